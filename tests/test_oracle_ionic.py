@@ -1,0 +1,166 @@
+"""Pins of the oracle's ionic models and exponential Euler step (Sec. 2, 4.1, Table 2)."""
+
+import os
+
+import numpy as np
+import pytest
+from scipy.integrate import solve_ivp
+
+from oracle.emrkc import Monodomain, OracleRun
+from oracle.ionic import HHModel, PassiveModel, TTP06Model, _x_over_expm1
+from oracle.power import compute_rho, start_vector
+from workloads import make_workload
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            rows.append(line.split())
+    return rows
+
+
+def test_hh_rest_gates_golden():
+    y0 = HHModel().y0()
+    vals = dict(zip(HHModel.names, y0))
+    for name, value, tol in _read("hh_rest_gates.txt"):
+        assert vals[name] == pytest.approx(float(value), abs=float(tol))
+
+
+def test_hh_rest_current_vanishes():
+    hh = HHModel()
+    y0 = hh.y0()
+    I = hh.I_ion(np.array([y0[0]]), y0[1:, None], np.zeros((0, 1)))
+    # E_L = V_rest + 10.613 is quoted to 3 decimals: |I| is a few 1e-3 uA/cm^2
+    assert abs(I[0]) < 1e-2
+
+
+def test_hh_removable_singularities():
+    hh = HHModel()
+    # alpha_m at v = 25 and alpha_n at v = 10 are 0/0 with limits 1.0 and 0.1
+    for v, k, lim in [(25.0, 0, 1.0), (10.0, 2, 0.1)]:
+        a, _ = hh.rates(np.array([hh.V_rest + v, hh.V_rest + v + 1e-6, hh.V_rest + v - 1e-6]))
+        assert a[k, 0] == pytest.approx(lim, rel=1e-12)
+        assert a[k, 1] == pytest.approx(lim, rel=1e-6)
+        assert a[k, 2] == pytest.approx(lim, rel=1e-6)
+    x = np.array([0.0, 1e-9, -1e-9, 1e-3, -2.0, 30.0])
+    ref = np.array([1.0, 1 - 5e-10, 1 + 5e-10, 1e-3 / np.expm1(1e-3), -2.0 / np.expm1(-2.0),
+                    30.0 / np.expm1(30.0)])
+    np.testing.assert_allclose(_x_over_expm1(x), ref, rtol=1e-14)
+
+
+@pytest.mark.parametrize("model_id,V", [(2, -75.0), (2, -20.0), (2, 30.0), (3, -85.0), (3, -10.0), (3, 25.0)])
+def test_rush_larsen_exact_for_frozen_V(model_id, V):
+    """Exponential Euler with V frozen equals the exact solution of the gate ODE
+    dz/dt = Lambda (z - z_inf), here integrated independently by a high-accuracy
+    ODE solver in the alpha/beta (or tau) form of Eq. (monodomain_gate)."""
+    w = make_workload(f"line2_{'hh' if model_id == 2 else 'ttp'}", length=0.001)
+    prob = Monodomain.from_workload(w)
+    Y = prob.initial_state()
+    Y[0] = V
+    eta = 0.37
+    YE = prob.exponential_euler(Y, eta)
+    Vv, zE, zS = prob.parts(Y)
+    lam, zinf = prob.model.gating(Vv, zE, zS)
+    if model_id == 2:
+        a, b = prob.model.rates(Vv)
+
+        def rhs(t, z):  # Eq. (monodomain_gate): alpha (1 - z) - beta z
+            return a[:, 0] * (1 - z) - b[:, 0] * z
+    else:
+        tau = -1.0 / lam[:, 0]
+
+        def rhs(t, z):
+            return (zinf[:, 0] - z) / tau
+    sol = solve_ivp(rhs, (0.0, eta), zE[:, 0], method="Radau", rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(YE[1:1 + prob.nE, 0], sol.y[:, -1], rtol=2e-9, atol=1e-12)
+    # V and z_S are untouched by the exponential step
+    assert YE[0, 0] == Y[0, 0]
+    np.testing.assert_array_equal(YE[1 + prob.nE:], Y[1 + prob.nE:])
+
+
+def test_table2_hh_stiffness():
+    """rho_S of HH over an action potential peaks near Table 2's rho_max = 40."""
+    rows = {r[0]: (int(r[1]), float(r[2])) for r in _read("table2_stiffness.txt")}
+    N, rho_max = rows["hh"]
+    assert HHModel.nE + HHModel.nS == N
+    w = make_workload("line2_hh", length=0.001)
+    w.stim_mask[:] = 1
+    prob = Monodomain.from_workload(w)
+    r = OracleRun(prob, rho_every=1, safety=1.0)
+    for _ in range(300):
+        r.step(0.02)
+    peak = max(l[3] for l in r.log)
+    assert 0.85 * rho_max <= peak <= 1.2 * rho_max
+
+
+def test_table2_ttp_stiffness():
+    """The full right-hand side Jacobian of TTP06 at rest has spectral radius
+    near Table 2's rho_max = 1000 (set by the fast m gate)."""
+    rows = {r[0]: (int(r[1]), float(r[2])) for r in _read("table2_stiffness.txt")}
+    N, rho_max = rows["ttp06_epi"]
+    assert TTP06Model.nE + TTP06Model.nS == N
+    w = make_workload("line2_ttp", length=0.001)
+    prob = Monodomain.from_workload(w)
+    Y = prob.initial_state()
+
+    def f(t, y):
+        YY = y.reshape(prob.N, -1)
+        return (prob.f_S(t, YY) + prob.f_E(t, YY)).ravel()
+
+    _, rho, _ = compute_rho(0.0, Y.ravel(), f, start_vector(11, Y.size), 0.0, tol=1e-6, max_iter=500)
+    assert 0.8 * rho_max <= rho <= 1.2 * rho_max
+
+
+def test_ttp_rest_state_nearly_stationary():
+    m = TTP06Model()
+    y0 = m.y0()
+    V = np.array([y0[0]])
+    zE = y0[1:13, None]
+    zS = y0[13:, None]
+    assert abs(m.I_ion(V, zE, zS)[0]) < 0.01  # pA/pF, vs ~ -50 at the upstroke
+    gS = m.g_S(V, zE, zS)[:, 0]
+    assert np.all(np.abs(gS) < 1e-3)
+    lam, zinf = m.gating(V, zE, zS)
+    assert np.all(np.abs(lam[:, 0] * (zE[:, 0] - zinf[:, 0])) < 0.01)
+
+
+@pytest.mark.slow
+def test_ttp_single_cell_action_potential():
+    """Published TTP06 epicardial characteristics: rest near -85 mV, upstroke
+    velocity of a few hundred mV/ms, APD90 near 300 ms (parity of the model
+    beyond these features is unpinned)."""
+    w = make_workload("line2_ttp", length=0.001)
+    w.stim_mask[:] = 1
+    w.stim_amp = 52.0
+    w.t_off = 1.0
+    prob = Monodomain.from_workload(w)
+    r = OracleRun(prob, rho_every=1)
+    dt = 0.1
+    V = []
+    for _ in range(4000):
+        r.step(dt)
+        V.append(r.Y[0, 0])
+    V = np.array(V)
+    t = dt * np.arange(1, V.size + 1)
+    assert -87.0 < V[-1] < -83.0
+    assert 10.0 < V.max() < 80.0
+    dVdt = np.diff(np.concatenate([[-85.23], V])) / dt
+    assert 150.0 < dVdt.max() < 600.0
+    amp = V.max() + 85.23
+    after = (t > t[V.argmax()]) & (V < -85.23 + 0.1 * amp)
+    apd90 = t[np.nonzero(after)[0][0]]
+    assert 240.0 < apd90 < 360.0
+
+
+def test_passive_model_linear():
+    m = PassiveModel()
+    V = np.array([1.0, -2.0])
+    assert np.allclose(m.I_ion(V, None, None), m.g_p * V)
+    lam, zinf = m.gating(V, None, None)
+    assert np.allclose(lam, -(m.a_w + m.b_w))
+    assert np.allclose(zinf, m.a_w / (m.a_w + m.b_w))

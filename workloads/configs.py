@@ -1,0 +1,150 @@
+"""Named synthetic workloads with the shapes of the paper's experiments.
+
+The paper's geometries (Sec. 5.2-5.4) are not shipped with it; these seeded
+synthetic problems stand in for them:
+
+  square65_hh  65 x 65 P1 triangles on [0,1]^2 cm, sigma = 1 mS/cm, HH,
+               50 uA/cm^2 for t <= 1 ms on the 0.1 cm corner, dt 0.05, T 20 ms.
+  slab_ttp     201 x 71 x 31 Kuhn tets on a 2.0 x 0.7 x 0.3 cm slab,
+               D = diag(1.33, 0.18, 0.18) mS/cm (fibres along x), TTP06 epi,
+               50 uA/cm^2 for t <= 2 ms on the 0.15 cm corner cube, dt 0.05,
+               T 50 ms (the 3-D cuboid of Sec. 5.3 at 0.1 mm).
+  shell_ttp    32 x 256 x 512 parametric prolate-ellipsoid shell (~4.2 M
+               nodes), fibre angle +60 deg (endo) -> -60 deg (epi), TTP06,
+               apical stimulus, dt 0.05, T 100 ms.
+
+Tissue constants follow Table 1 in centimetres: chi = 1400 /cm, Cm = 1 uF/cm^2.
+Ionic model ids: 0 none (pure diffusion), 1 passive test model, 2 Hodgkin-
+Huxley, 3 ten Tusscher-Panfilov 2006 epicardial.
+"""
+
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .fields import axis_D, corner_mask, fibre_D, isotropic_D, radius_mask
+from .meshes import line_mesh, shell_tet_mesh, slab_tet_mesh, square_tri_mesh
+
+MODEL_NONE, MODEL_PASSIVE, MODEL_HH, MODEL_TTP06 = 0, 1, 2, 3
+MODEL_NAMES = {0: "none", 1: "passive", 2: "hh", 3: "ttp06_epi"}
+
+
+@dataclass
+class Workload:
+    name: str
+    coords: np.ndarray
+    cells: np.ndarray
+    D: np.ndarray  # (n_cells, dim, dim) mS/cm
+    model: int
+    stim_mask: np.ndarray  # uint8 per node
+    stim_amp: float = 50.0  # uA/cm^2
+    t_on: float = 0.0
+    t_off: float = 1.0
+    dt: float = 0.05
+    T: float = 20.0
+    chi: float = 1400.0
+    Cm: float = 1.0
+    rho_every: int = 1  # 0 = once at start
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return self.coords.shape[0]
+
+    @property
+    def dim(self) -> int:
+        return self.coords.shape[1]
+
+    @property
+    def steps(self) -> int:
+        return int(round(self.T / self.dt))
+
+
+def _square(nx, ny, lx, ly, model, sigma=1.0, corner=0.1, t_off=1.0, dt=0.05, T=20.0, name=None):
+    coords, cells = square_tri_mesh(nx, ny, lx, ly)
+    D = isotropic_D(cells.shape[0], 2, sigma)
+    return Workload(name or f"square{nx}x{ny}", coords, cells, D, model,
+                    corner_mask(coords, corner), t_off=t_off, dt=dt, T=T)
+
+
+def _slab(nx, ny, nz, lx, ly, lz, model, sig=(1.33, 0.18, 0.18), corner=0.15,
+          t_off=2.0, dt=0.05, T=50.0, name=None):
+    coords, cells = slab_tet_mesh(nx, ny, nz, lx, ly, lz)
+    D = axis_D(cells.shape[0], sig)
+    return Workload(name or f"slab{nx}x{ny}x{nz}", coords, cells, D, model,
+                    corner_mask(coords, corner), t_off=t_off, dt=dt, T=T, rho_every=0)
+
+
+def shell_fibres(coords, cells, param):
+    """Cell fibre vectors: angle +60 deg at r=0 (endo) to -60 deg at r=1 (epi)
+    in the (e_phi, e_theta) tangent plane, evaluated at the cell centroid."""
+    pr, pt, pph, rs_in, rl_in, thick, z_top, nt, nphi = param
+    c = coords[cells].mean(axis=1)
+    rc = pr[cells].mean(axis=1)
+    phi = np.arctan2(c[:, 1], c[:, 0])
+    e_phi = np.stack([-np.sin(phi), np.cos(phi), np.zeros_like(phi)], axis=1)
+    # e_theta: derivative of the surface point along theta at fixed r, normalised
+    rs = rs_in + thick * rc
+    rl = rl_in + thick * rc
+    rho_xy = np.hypot(c[:, 0], c[:, 1])
+    sin_t = np.clip(rho_xy / rs, 0.0, 1.0)
+    cos_t = np.clip(c[:, 2] / rl, -1.0, 1.0)
+    e_th = np.stack([rs * cos_t * np.cos(phi), rs * cos_t * np.sin(phi), -rl * sin_t], axis=1)
+    e_th /= np.linalg.norm(e_th, axis=1, keepdims=True)
+    alpha = np.deg2rad(60.0 * (1.0 - rc) - 60.0 * rc)
+    return np.cos(alpha)[:, None] * e_phi + np.sin(alpha)[:, None] * e_th
+
+
+def make_workload(name: str, **kw) -> Workload:
+    """Build a named workload; keyword arguments override the defaults."""
+    if name == "square65_hh":
+        w = _square(65, 65, 1.0, 1.0, MODEL_HH, name=name)
+        w.rho_every = 1
+    elif name == "slab_ttp":
+        w = _slab(201, 71, 31, 2.0, 0.7, 0.3, MODEL_TTP06, name=name)
+    elif name == "slab_hh":
+        w = _slab(201, 71, 31, 2.0, 0.7, 0.3, MODEL_HH, name=name)
+    elif name == "shell_ttp":
+        nr = kw.pop("nr", 32)
+        nt = kw.pop("ntheta", 256)
+        nphi = kw.pop("nphi", 512)
+        coords, cells, param = shell_tet_mesh(nr, nt, nphi, return_param=True)
+        a_l = shell_fibres(coords, cells, param)
+        D = fibre_D(a_l, 1.33, 0.18)
+        rl_out = param[4] + param[5]
+        w = Workload(name, coords, cells, D, MODEL_TTP06,
+                     radius_mask(coords, (0.0, 0.0, -rl_out), 0.3),
+                     t_off=2.0, dt=0.05, T=100.0, rho_every=0)
+    elif name.startswith("square"):
+        # squareNxM_model, e.g. square17x17_hh on [0, (N-1)h] with h from kw
+        dims, model = name[len("square"):].split("_")
+        nx, ny = (int(v) for v in dims.split("x"))
+        h = kw.pop("h", 1.0 / 64)
+        mid = {"hh": MODEL_HH, "ttp": MODEL_TTP06, "none": MODEL_NONE, "passive": MODEL_PASSIVE}[model]
+        w = _square(nx, ny, (nx - 1) * h, (ny - 1) * h, mid, name=name)
+    elif name.startswith("slab"):
+        dims, model = name[len("slab"):].split("_")
+        nx, ny, nz = (int(v) for v in dims.split("x"))
+        h = kw.pop("h", 0.01)
+        mid = {"hh": MODEL_HH, "ttp": MODEL_TTP06, "none": MODEL_NONE, "passive": MODEL_PASSIVE}[model]
+        w = _slab(nx, ny, nz, (nx - 1) * h, (ny - 1) * h, (nz - 1) * h, mid, name=name)
+    elif name.startswith("line"):
+        n, model = name[len("line"):].split("_")
+        n = int(n)
+        length = kw.pop("length", 1.0)
+        coords, cells = line_mesh(n, length)
+        mid = {"hh": MODEL_HH, "ttp": MODEL_TTP06, "none": MODEL_NONE, "passive": MODEL_PASSIVE}[model]
+        w = Workload(name, coords, cells, isotropic_D(cells.shape[0], 1, 1.0), mid,
+                     corner_mask(coords, 0.1 * length))
+    else:
+        raise KeyError(f"unknown workload {name!r}")
+    for k, v in kw.items():
+        if not hasattr(w, k):
+            raise KeyError(f"unknown workload field {k!r}")
+        setattr(w, k, v)
+    return w
+
+
+WORKLOADS = ("square65_hh", "slab_ttp", "shell_ttp")
