@@ -1,0 +1,218 @@
+/*
+ * emrkc.h - C ABI of the GB300 (sm_103a) emRKC monodomain solver.
+ *
+ * One emRKC time step (Algorithm 3 of "Explicit stabilized multirate methods
+ * for the monodomain model in cardiac electrophysiology", arXiv 2401.01745)
+ * of the P1 finite-element monodomain system with lumped mass (Sec. 2.1,
+ * Eq. sd_sys), split as in Eq. (mono_in_FSE):
+ *   f_F(y)    = ((chi Cm M)^-1 A V, 0, 0)            A = -K (stiffness K >= 0)
+ *   f_S(t, y) = (Cm^-1 (I_stim(t) - I_ion(y)), 0, g_S(y))
+ *   f_E(y)    = (0, Lambda_E(y) (z_E - z_inf(y)), 0)
+ * The gating variables z_E take the exponential (Rush-Larsen) step of
+ * Sec. 4.1-4.2, the outer RKC iteration runs over the averaged force with
+ * s stages, and the inner RKC iteration runs over the diffusion SpMV with
+ * m stages (Algorithm 1).  Spectral radii rho_F and rho_S, which set s and
+ * m, come from the nonlinear power iteration of Algorithm 5 (App. A).
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns an int status: EMRKC_OK (0) or an EMRKC_ERR_*
+ *    code.  A human-readable message is available from emrkc_last_error().
+ *  - Host pointers passed in are read during the call only; the library
+ *    copies what it keeps (ownership stays with the caller).  Host output
+ *    buffers are allocated by the caller.
+ *  - The solver owns all device memory it allocates and frees it in
+ *    emrkc_destroy().  All device work is ordered on the solver's CUDA
+ *    stream (options.cuda_stream, or a stream the solver creates).
+ *  - Units: cm, ms, mV, mS/cm, uF/cm^2, uA/cm^2.
+ *  - The state is structure-of-arrays: variable 0 is V, variables 1..nE the
+ *    gating variables z_E, the remaining ones z_S (see emrkc_num_vars()).
+ *  - No CPU fallback exists: without a usable CUDA device every call that
+ *    needs one fails with EMRKC_ERR_CUDA.
+ */
+#ifndef EMRKC_H
+#define EMRKC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define EMRKC_OK 0
+#define EMRKC_ERR_ARG 1       /* invalid argument (null pointer, size, range) */
+#define EMRKC_ERR_CUDA 2      /* CUDA runtime error or no device              */
+#define EMRKC_ERR_OOM 3       /* device or host allocation failed             */
+#define EMRKC_ERR_NONFINITE 4 /* a NaN/Inf appeared in V during a step        */
+#define EMRKC_ERR_TIMEOUT 5   /* a bounded device wait gave up                */
+#define EMRKC_ERR_STATE 6     /* call not valid in the object's current state */
+
+/* ---- ionic models (Sec. 2 and Sec. 5, Table 2) ------------------------- */
+#define EMRKC_MODEL_NONE 0      /* pure diffusion, N = 1                      */
+#define EMRKC_MODEL_PASSIVE 1   /* linear test model (V, w, c), N = 3         */
+#define EMRKC_MODEL_HH 2        /* Hodgkin-Huxley 1952, N = 4 (V, m, h, n)    */
+#define EMRKC_MODEL_TTP06_EPI 3 /* ten Tusscher-Panfilov 2006 epi, N = 19     */
+
+/* ---- precision modes ---------------------------------------------------- */
+#define EMRKC_PREC_FP64 0  /* every operation in FP64                          */
+#define EMRKC_PREC_MIXED 1 /* z, SpMV, ionic model and gating in FP32; V, the
+                              stage coefficients and rho in FP64               */
+
+/* ---- spectral-radius policy (Sec. 5 setup; App. A) --------------------- */
+#define EMRKC_RHO_ONCE 0   /* power iteration before the first step only   */
+/* rho_every >= 1: power iteration every rho_every-th step (warm started)   */
+#define EMRKC_RHO_FIXED -1 /* use options.rho_F / rho_S as given            */
+
+typedef struct emrkc_solver emrkc_solver; /* opaque; owns device memory */
+
+/* Sparse P1 stiffness in CSR and the row-sum lumped mass (Sec. 2.1).
+ * K_ij = sum_T int_T D grad(phi_j) . grad(phi_i): symmetric, row sums 0,
+ * so the paper's A = -K.  Column indices must be in [0, n).  Entries whose
+ * magnitude is at most 1e-14 |K_ii| are dropped when the solver is built. */
+typedef struct {
+  int64_t n;                  /* number of nodes                           */
+  int64_t nnz;                /* stored entries                            */
+  const int64_t* row_ptr;     /* n + 1 host entries                        */
+  const int32_t* col;         /* nnz host entries                          */
+  const double* K;            /* nnz host entries                          */
+  const double* lumped_mass;  /* n host entries, all > 0                   */
+} emrkc_matrix;
+
+/* Matrix produced by emrkc_assemble_p1(); free with emrkc_free_matrix(). */
+typedef struct {
+  int64_t n, nnz;
+  int64_t* row_ptr;
+  int32_t* col;
+  double* K;
+  double* lumped_mass;
+} emrkc_owned_matrix;
+
+/* Tissue constants of Eq. (monodomain): chi (1/cm) and Cm (uF/cm^2). */
+typedef struct {
+  double chi;
+  double Cm;
+} emrkc_tissue;
+
+/* Nodal stimulus (Eq. sd_sys, linear interpolation of I_stim):
+ * I_stim(t, x_i) = amplitude if node_mask[i] != 0 and t_on <= t <= t_off. */
+typedef struct {
+  const uint8_t* node_mask; /* n host entries, or NULL for no stimulus */
+  double amplitude;         /* uA/cm^2 */
+  double t_on, t_off;       /* ms, inclusive */
+} emrkc_stimulus;
+
+typedef struct {
+  int precision;      /* EMRKC_PREC_*                                      */
+  int rho_every;      /* EMRKC_RHO_ONCE, EMRKC_RHO_FIXED or k >= 1          */
+  double rho_F, rho_S;/* used when rho_every == EMRKC_RHO_FIXED (1/ms)     */
+  double eps;         /* RKC damping, 0.05 (Algorithm 1)                    */
+  double safety;      /* factor on power-iteration rho, 1.05 (App. A)       */
+  double pow_tol;     /* relative tolerance of Algorithm 5, 1e-2            */
+  double pow_eps;     /* perturbation size of Algorithm 5, 1e-8             */
+  int pow_max_iter;   /* iteration cap of Algorithm 5, 50                   */
+  uint64_t seed;      /* start vectors: SplitMix64(seed ^ i) for rho_F and
+                         SplitMix64(~seed ^ k) for rho_S (k = var*n + node) */
+  double act_threshold; /* activation threshold in mV (-20); NaN disables  */
+  void* cuda_stream;  /* cudaStream_t to order work on, or NULL            */
+  int device;         /* CUDA device ordinal                                */
+  int profile;        /* 1: time every kernel class with CUDA events        */
+  int use_graphs;     /* 1: replay each fixed (s, m) step as a CUDA graph  */
+} emrkc_options;
+
+/* Kernel classes reported in emrkc_stats.phase_ms / phase_launches. */
+#define EMRKC_PHASE_STAGE 0   /* fused RL + ionic + first SpMV + outer update */
+#define EMRKC_PHASE_INNER 1   /* inner RKC SpMV stage                         */
+#define EMRKC_PHASE_POWER_F 2 /* power iteration on f_F                       */
+#define EMRKC_PHASE_POWER_S 3 /* power iteration on f_S                       */
+#define EMRKC_PHASE_OTHER 4   /* norms, start vectors, f_S(y)                 */
+#define EMRKC_NUM_PHASES 5
+
+typedef struct {
+  double t;              /* current time (ms)                          */
+  int64_t steps;         /* steps taken                                */
+  int s, m;              /* stage counts of the last step              */
+  double eta;            /* inner step of the last step                */
+  double rho_F, rho_S;   /* values used by the last step (with safety) */
+  int pow_iters_F, pow_iters_S; /* iterations of the last power call   */
+  int64_t total_pow_iters;
+  int64_t launches;      /* kernels launched since create              */
+  double phase_ms[EMRKC_NUM_PHASES];       /* needs options.profile    */
+  int64_t phase_launches[EMRKC_NUM_PHASES];
+} emrkc_stats;
+
+/* Fill *opt with the defaults listed above (FP64, rho every step, seed 0,
+ * threshold -20 mV, NULL stream, device 0, no profiling, graphs on). */
+int emrkc_default_options(emrkc_options* opt);
+
+/* Number of state variables N (V included) of an ionic model, or -1. */
+int emrkc_num_vars(int ionic_model);
+/* Number of gating variables nE of an ionic model, or -1. */
+int emrkc_num_gates(int ionic_model);
+
+/* P1 stiffness K and row-sum lumped mass of a simplex mesh (Sec. 2.1).
+ * dim in {1, 2, 3}; xyz: n_nodes*dim doubles (node-major); cells:
+ * n_cells*(dim+1) node indices; D_per_cell: n_cells*dim*dim doubles, the
+ * conductivity tensor of Eq. (def_D) per cell (row-major).  Host routine;
+ * on success *out owns malloc'd arrays (free with emrkc_free_matrix).
+ * Errors: EMRKC_ERR_ARG for bad sizes/indices or a zero-volume cell. */
+int emrkc_assemble_p1(int dim, int64_t n_nodes, const double* xyz, int64_t n_cells,
+                      const int64_t* cells, const double* D_per_cell,
+                      emrkc_owned_matrix* out);
+void emrkc_free_matrix(emrkc_owned_matrix* m);
+
+/* Build a solver: validates and copies the CSR, drops near-zero entries,
+ * prescales L = -(chi Cm M)^-1 K into a sliced-ELL device matrix, allocates
+ * the SoA state and sets every node to the model's rest state (Sec. 5).
+ * opt may be NULL (defaults).  On failure *out is NULL. */
+int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_model,
+                 const emrkc_stimulus* stim, const emrkc_options* opt, emrkc_solver** out);
+
+/* One emRKC step of size dt (ms) from the current state (Algorithm 3),
+ * preceded by the power iteration when the rho policy asks for it.  The
+ * step is enqueued on the solver's stream; the call synchronises only for
+ * the power iteration.  Returns EMRKC_ERR_NONFINITE if a previously
+ * enqueued step produced a non-finite V (checked at every synchronisation). */
+int emrkc_step(emrkc_solver* s, double dt);
+
+/* round(T/dt) steps; EMRKC_ERR_ARG if T/dt is not an integer within 1e-9.
+ * Synchronises at the end and reports non-finite values. */
+int emrkc_run(emrkc_solver* s, double T, double dt);
+
+/* Wait for all enqueued work; returns EMRKC_ERR_NONFINITE if any step
+ * produced a non-finite V since the last check. */
+int emrkc_sync(emrkc_solver* s);
+
+/* Copy variable var (0..N-1) or the whole state (var = -1, SoA: var-major,
+ * N*n doubles) to/from host memory; len must equal n or N*n.  FP32-stored
+ * variables (mixed precision) are converted.  Synchronous. */
+int emrkc_get_state(emrkc_solver* s, int var, double* host_out, int64_t len);
+int emrkc_set_state(emrkc_solver* s, int var, const double* host_in, int64_t len);
+
+/* Same as get/set_state with device pointers (len doubles, on this device). */
+int emrkc_get_state_device(emrkc_solver* s, int var, double* dev_out, int64_t len);
+int emrkc_set_state_device(emrkc_solver* s, int var, const double* dev_in, int64_t len);
+
+/* Activation times (first upward crossing of options.act_threshold,
+ * linear interpolation between step ends; NaN = never).  n doubles. */
+int emrkc_get_activation_times(emrkc_solver* s, double* host_out, int64_t n);
+
+/* Run Algorithm 5 now on the current state (warm started) and return the
+ * raw estimates (without the safety factor) and iteration counts. */
+int emrkc_estimate_rho(emrkc_solver* s, double* rho_F, double* rho_S, int* it_F, int* it_S);
+
+/* Set the time and step counter (checkpoint/resume together with set_state). */
+int emrkc_set_time(emrkc_solver* s, double t, int64_t steps);
+
+int emrkc_get_stats(emrkc_solver* s, emrkc_stats* out);
+
+/* Message of the last error on this solver, or of the last failed create
+ * on this thread when s is NULL.  Never NULL. */
+const char* emrkc_last_error(const emrkc_solver* s);
+
+void emrkc_destroy(emrkc_solver* s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EMRKC_H */

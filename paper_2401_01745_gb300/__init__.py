@@ -1,0 +1,197 @@
+"""GB300-native emRKC solver for the P1 monodomain model (Python binding).
+
+Thin wrapper over the C ABI in include/emrkc.h: it marshals numpy arrays and
+CUDA stream handles; every step of the method runs in the library's CUDA
+kernels.  There is no CPU fallback: if the library is missing or no CUDA
+device is usable, the calls raise.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _ffi
+from ._ffi import Matrix, Options, OwnedMatrix, Stats, Stimulus, Tissue
+
+MODEL_NONE, MODEL_PASSIVE, MODEL_HH, MODEL_TTP06 = 0, 1, 2, 3
+PREC_FP64, PREC_MIXED = 0, 1
+RHO_ONCE, RHO_FIXED = 0, -1
+
+
+class EmrkcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ffi.ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def build(verbose=False, force=False):
+    from .build import build as _b
+    return _b(verbose=verbose, force=force)
+
+
+def lib():
+    return _ffi.load()
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def num_vars(model: int) -> int:
+    return lib().emrkc_num_vars(model)
+
+
+def num_gates(model: int) -> int:
+    return lib().emrkc_num_gates(model)
+
+
+def assemble_p1(coords, cells, D):
+    """P1 stiffness K (CSR arrays) and lumped mass by the library's host assembler."""
+    coords = np.ascontiguousarray(coords, dtype=np.float64)
+    cells = np.ascontiguousarray(cells, dtype=np.int64)
+    D = np.ascontiguousarray(D, dtype=np.float64)
+    n, dim = coords.shape
+    out = OwnedMatrix()
+    rc = lib().emrkc_assemble_p1(dim, n, _dp(coords), cells.shape[0],
+                                 cells.ctypes.data_as(C.POINTER(C.c_int64)), _dp(D), C.byref(out))
+    if rc != 0:
+        raise EmrkcError(rc, "assembly failed")
+    try:
+        rp = np.ctypeslib.as_array(out.row_ptr, shape=(out.n + 1,)).copy()
+        col = np.ctypeslib.as_array(out.col, shape=(max(out.nnz, 1),))[:out.nnz].copy()
+        K = np.ctypeslib.as_array(out.K, shape=(max(out.nnz, 1),))[:out.nnz].copy()
+        M = np.ctypeslib.as_array(out.lumped_mass, shape=(out.n,)).copy()
+    finally:
+        lib().emrkc_free_matrix(C.byref(out))
+    return rp, col, K, M
+
+
+def default_options() -> Options:
+    o = Options()
+    lib().emrkc_default_options(C.byref(o))
+    return o
+
+
+class Solver:
+    """One monodomain problem advanced by emRKC on the GPU."""
+
+    def __init__(self, row_ptr, col, K, M, *, chi=1400.0, Cm=1.0, model=MODEL_HH, mask=None,
+                 amplitude=50.0, t_on=0.0, t_off=1.0, precision=PREC_FP64, rho_every=1,
+                 rho_F=0.0, rho_S=0.0, seed=0, act_threshold=-20.0, stream=None, device=0,
+                 profile=False, use_graphs=True, pow_tol=1e-2, pow_max_iter=50, safety=1.05):
+        self._lib = lib()
+        self._h = C.c_void_p()
+        self.row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        self.col = np.ascontiguousarray(col, dtype=np.int32)
+        self.K = np.ascontiguousarray(K, dtype=np.float64)
+        self.M = np.ascontiguousarray(M, dtype=np.float64)
+        self.n = self.M.size
+        self.model = model
+        self.N = num_vars(model)
+        mat = Matrix(self.n, self.K.size, self.row_ptr.ctypes.data_as(C.POINTER(C.c_int64)),
+                     self.col.ctypes.data_as(C.POINTER(C.c_int32)), _dp(self.K), _dp(self.M))
+        tis = Tissue(chi, Cm)
+        stim = Stimulus()
+        if mask is not None:
+            self._mask = np.ascontiguousarray(mask, dtype=np.uint8)
+            stim.node_mask = self._mask.ctypes.data_as(C.POINTER(C.c_uint8))
+        stim.amplitude = amplitude
+        stim.t_on = t_on
+        stim.t_off = t_off
+        o = default_options()
+        o.precision = precision
+        o.rho_every = rho_every
+        o.rho_F = rho_F
+        o.rho_S = rho_S
+        o.seed = seed
+        o.act_threshold = act_threshold
+        o.cuda_stream = stream
+        o.device = device
+        o.profile = int(profile)
+        o.use_graphs = int(use_graphs)
+        o.pow_tol = pow_tol
+        o.pow_max_iter = pow_max_iter
+        o.safety = safety
+        rc = self._lib.emrkc_create(C.byref(mat), C.byref(tis), model, C.byref(stim), C.byref(o),
+                                    C.byref(self._h))
+        if rc != 0:
+            raise EmrkcError(rc, self._lib.emrkc_last_error(None).decode())
+
+    @classmethod
+    def from_workload(cls, w, **kw):
+        rp, col, K, M = assemble_p1(w.coords, w.cells, w.D)
+        return cls(rp, col, K, M, chi=w.chi, Cm=w.Cm, model=w.model, mask=w.stim_mask,
+                   amplitude=w.stim_amp, t_on=w.t_on, t_off=w.t_off,
+                   rho_every=kw.pop("rho_every", w.rho_every), **kw)
+
+    def _check(self, rc):
+        if rc != 0:
+            raise EmrkcError(rc, self._lib.emrkc_last_error(self._h).decode())
+
+    def step(self, dt):
+        self._check(self._lib.emrkc_step(self._h, dt))
+
+    def run(self, T, dt):
+        self._check(self._lib.emrkc_run(self._h, T, dt))
+
+    def sync(self):
+        self._check(self._lib.emrkc_sync(self._h))
+
+    def get_state(self, var=-1, out=None):
+        shape = (self.N, self.n) if var == -1 else (self.n,)
+        if out is None:
+            out = np.empty(shape, dtype=np.float64)
+        self._check(self._lib.emrkc_get_state(self._h, var, _dp(out), out.size))
+        return out
+
+    def set_state(self, values, var=-1):
+        values = np.ascontiguousarray(values, dtype=np.float64)
+        self._check(self._lib.emrkc_set_state(self._h, var, _dp(values), values.size))
+
+    def get_state_device(self, ptr, var, length):
+        self._check(self._lib.emrkc_get_state_device(self._h, var, C.c_void_p(ptr), length))
+
+    def set_state_device(self, ptr, var, length):
+        self._check(self._lib.emrkc_set_state_device(self._h, var, C.c_void_p(ptr), length))
+
+    def activation_times(self):
+        out = np.empty(self.n)
+        self._check(self._lib.emrkc_get_activation_times(self._h, _dp(out), self.n))
+        return out
+
+    def estimate_rho(self):
+        rf, rs = C.c_double(), C.c_double()
+        itf, its = C.c_int(), C.c_int()
+        self._check(self._lib.emrkc_estimate_rho(self._h, C.byref(rf), C.byref(rs), C.byref(itf),
+                                                 C.byref(its)))
+        return rf.value, rs.value, itf.value, its.value
+
+    def set_time(self, t, steps):
+        self._check(self._lib.emrkc_set_time(self._h, t, steps))
+
+    def stats(self) -> dict:
+        st = Stats()
+        self._check(self._lib.emrkc_get_stats(self._h, C.byref(st)))
+        d = {k: getattr(st, k) for k, _ in Stats._fields_ if k not in ("phase_ms", "phase_launches")}
+        d["phase_ms"] = dict(zip(_ffi.PHASES, list(st.phase_ms)))
+        d["phase_launches"] = dict(zip(_ffi.PHASES, list(st.phase_launches)))
+        return d
+
+    def close(self):
+        if self._h:
+            self._lib.emrkc_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,102 @@
+"""ctypes declarations of the C ABI in include/emrkc.h (argument marshalling only)."""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libemrkc.so")
+
+EMRKC_OK = 0
+ERRORS = {1: "EMRKC_ERR_ARG", 2: "EMRKC_ERR_CUDA", 3: "EMRKC_ERR_OOM", 4: "EMRKC_ERR_NONFINITE",
+          5: "EMRKC_ERR_TIMEOUT", 6: "EMRKC_ERR_STATE"}
+NUM_PHASES = 5
+PHASES = ("stage", "inner", "power_F", "power_S", "other")
+
+
+class Matrix(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.POINTER(C.c_int64)),
+                ("col", C.POINTER(C.c_int32)), ("K", C.POINTER(C.c_double)),
+                ("lumped_mass", C.POINTER(C.c_double))]
+
+
+class OwnedMatrix(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.POINTER(C.c_int64)),
+                ("col", C.POINTER(C.c_int32)), ("K", C.POINTER(C.c_double)),
+                ("lumped_mass", C.POINTER(C.c_double))]
+
+
+class Tissue(C.Structure):
+    _fields_ = [("chi", C.c_double), ("Cm", C.c_double)]
+
+
+class Stimulus(C.Structure):
+    _fields_ = [("node_mask", C.POINTER(C.c_uint8)), ("amplitude", C.c_double),
+                ("t_on", C.c_double), ("t_off", C.c_double)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("rho_every", C.c_int), ("rho_F", C.c_double),
+                ("rho_S", C.c_double), ("eps", C.c_double), ("safety", C.c_double),
+                ("pow_tol", C.c_double), ("pow_eps", C.c_double), ("pow_max_iter", C.c_int),
+                ("seed", C.c_uint64), ("act_threshold", C.c_double), ("cuda_stream", C.c_void_p),
+                ("device", C.c_int), ("profile", C.c_int), ("use_graphs", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("t", C.c_double), ("steps", C.c_int64), ("s", C.c_int), ("m", C.c_int),
+                ("eta", C.c_double), ("rho_F", C.c_double), ("rho_S", C.c_double),
+                ("pow_iters_F", C.c_int), ("pow_iters_S", C.c_int), ("total_pow_iters", C.c_int64),
+                ("launches", C.c_int64), ("phase_ms", C.c_double * NUM_PHASES),
+                ("phase_launches", C.c_int64 * NUM_PHASES)]
+
+
+_P = C.c_void_p
+_PD = C.POINTER(C.c_double)
+
+SIGNATURES = {
+    "emrkc_default_options": (C.c_int, [C.POINTER(Options)]),
+    "emrkc_num_vars": (C.c_int, [C.c_int]),
+    "emrkc_num_gates": (C.c_int, [C.c_int]),
+    "emrkc_assemble_p1": (C.c_int, [C.c_int, C.c_int64, _PD, C.c_int64, C.POINTER(C.c_int64), _PD,
+                                    C.POINTER(OwnedMatrix)]),
+    "emrkc_free_matrix": (None, [C.POINTER(OwnedMatrix)]),
+    "emrkc_create": (C.c_int, [C.POINTER(Matrix), C.POINTER(Tissue), C.c_int, C.POINTER(Stimulus),
+                               C.POINTER(Options), C.POINTER(_P)]),
+    "emrkc_step": (C.c_int, [_P, C.c_double]),
+    "emrkc_run": (C.c_int, [_P, C.c_double, C.c_double]),
+    "emrkc_sync": (C.c_int, [_P]),
+    "emrkc_get_state": (C.c_int, [_P, C.c_int, _PD, C.c_int64]),
+    "emrkc_set_state": (C.c_int, [_P, C.c_int, _PD, C.c_int64]),
+    "emrkc_get_state_device": (C.c_int, [_P, C.c_int, C.c_void_p, C.c_int64]),
+    "emrkc_set_state_device": (C.c_int, [_P, C.c_int, C.c_void_p, C.c_int64]),
+    "emrkc_get_activation_times": (C.c_int, [_P, _PD, C.c_int64]),
+    "emrkc_estimate_rho": (C.c_int, [_P, _PD, _PD, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "emrkc_set_time": (C.c_int, [_P, C.c_double, C.c_int64]),
+    "emrkc_get_stats": (C.c_int, [_P, C.POINTER(Stats)]),
+    "emrkc_last_error": (C.c_char_p, [_P]),
+    "emrkc_destroy": (None, [_P]),
+}
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load the shared library; raises if it has not been built."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"the emRKC CUDA library is not built ({p}); run paper_2401_01745_gb300.build()")
+    lib = C.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        if not hasattr(lib, name):
+            continue
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib

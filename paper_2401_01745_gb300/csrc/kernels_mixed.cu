@@ -1,0 +1,17 @@
+// Mixed-precision instantiations: z, the ionic model, the gating exponentials
+// and the SpMV in FP32; V, its stage recurrence and the power iteration in FP64.
+#include "kernels.cuh"
+
+namespace emrkc {
+
+bool get_kernels_mixed(int model, KernelSet* ks) {
+  switch (model) {
+    case 0: Kernels<ModelNone<double>, ModelNone<float>, float, float, true>::fill(ks, model); return true;
+    case 1: Kernels<ModelPassive<double>, ModelPassive<float>, float, float, true>::fill(ks, model); return true;
+    case 2: Kernels<ModelHH<double>, ModelHH<float>, float, float, true>::fill(ks, model); return true;
+    case 3: Kernels<ModelTTP06<double>, ModelTTP06<float>, float, float, true>::fill(ks, model); return true;
+    default: return false;
+  }
+}
+
+}  // namespace emrkc

@@ -1,0 +1,138 @@
+// Internal interface between the host runtime (solver.cpp) and the CUDA
+// kernels (kernels_fp64.cu, kernels_mixed.cu).  Plain structs of device
+// pointers and scalars; no CUDA types leak into the host runtime beyond
+// cudaStream_t.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace emrkc {
+
+// Sliced ELL: slices of 32 consecutive rows; slice b stores width[b]
+// entries per row at slice_ptr[b] + k*32 + (row % 32), k < width[b].
+// Padding entries have col = the row itself and val = 0.
+struct Ell {
+  int64_t n = 0;
+  int64_t n_slices = 0;
+  const int64_t* slice_ptr = nullptr;
+  const int32_t* width = nullptr;
+  const int32_t* col = nullptr;
+  const double* val = nullptr;  // FP64 mode: L including the diagonal
+  const float* val32 = nullptr; // mixed mode: off-diagonal L only
+};
+
+// Deterministic two-level reduction scratch: per-block partial sums, a
+// ticket counter and result slots.
+struct ReduceScratch {
+  double* partials = nullptr;   // >= kReduceMaxBlocks entries
+  unsigned int* ticket = nullptr;
+  double* result = nullptr;     // result slots (device)
+};
+constexpr int kReduceBlock = 256;
+constexpr int kReduceMaxBlocks = 1024;
+
+// One outer stage j of the emRKC step (Algorithm 3): exponential Euler of
+// the gates at g_{j-1}, f_S at y_E, the first inner RKC stage (needs one
+// SpMV of V_{j-1}) and the z-part of g_j.
+struct StageArgs {
+  int64_t n = 0, ld = 0;
+  const double* Vm1 = nullptr;  // V of g_{j-1}
+  const void* Zm1 = nullptr;    // z block of g_{j-1} ((N-1) x ld, Z type)
+  const double* Vm2 = nullptr;  // g_{j-2} (j >= 2 only)
+  const void* Zm2 = nullptr;
+  double* Vout = nullptr;       // V of g_j (written when m == 1)
+  void* Zout = nullptr;         // z block of g_j
+  double nu = 1, kappa = 0, mu_dt = 0;  // outer coefficients of stage j
+  double eta = 0;               // inner step
+  double cm_inner = 1;          // c_m of the inner iteration
+  double mu1_eta = 0;           // mu'_1 * eta (inner first stage)
+  int m = 1;                    // inner stage count
+  double* U1 = nullptr;         // u_1 of the inner iteration (m >= 2)
+  void* F = nullptr;            // frozen forcing (I_stim - I_ion)/Cm (m >= 2; R type)
+  const uint8_t* mask = nullptr;
+  double stim = 0;              // stimulus amplitude at this stage's time
+  double inv_Cm = 1, Cm = 1;
+  // epilogue of the last kernel of a step
+  int final_stage = 0;
+  const double* Vn = nullptr;   // V at the start of the step
+  double* act = nullptr;        // activation times (nullptr: off)
+  double t_n = 0, dt = 0, threshold = -20;
+  int* flags = nullptr;         // bit 0: non-finite V
+  double* Vn_copy = nullptr;    // if set: store V_n (first stage when s >= 2)
+};
+
+// Inner RKC stage k >= 2 over f_u(u) = L u + F:
+// u_k = nu'_k u_{k-1} + kappa'_k u_{k-2} + mu'_k eta (L u_{k-1} + F).
+// When last: f_bar_V = (u_m - V_{j-1})/eta and V_j = nu V_{j-1} + kappa V_{j-2} + mu dt f_bar_V.
+struct InnerArgs {
+  int64_t n = 0;
+  const double* u1 = nullptr;   // u_{k-1}
+  const double* u2 = nullptr;   // u_{k-2}
+  double* uk = nullptr;         // u_k (when not last)
+  const void* F = nullptr;
+  double nu = 0, kappa = 0, mu_eta = 0;
+  int last = 0;
+  const double* Vm1 = nullptr;
+  const double* Vm2 = nullptr;
+  double* Vout = nullptr;
+  double onu = 1, okappa = 0, omu_dt = 0, eta = 1;
+  int final_stage = 0;
+  const double* Vn = nullptr;
+  double* act = nullptr;
+  double t_n = 0, dt = 0, threshold = -20;
+  int* flags = nullptr;
+};
+
+// Power iteration (Algorithm 5) kernels.
+struct PowerFArgs {
+  int64_t n = 0;
+  const double* V = nullptr;
+  const double* v_old = nullptr;
+  double* v_new = nullptr;
+  double q = 0;
+  int slot = 0;  // result slot for the sum of squares of v_new
+};
+
+struct PowerSArgs {
+  int64_t n = 0, ld = 0;
+  const double* V = nullptr;
+  const void* Z = nullptr;      // state z block (Z type)
+  const double* v_old = nullptr;  // N x ld
+  double* v_new = nullptr;        // N x ld
+  const double* fy = nullptr;     // f_S(y), N x ld
+  double q = 0;
+  const uint8_t* mask = nullptr;
+  double stim = 0, Cm = 1;
+  int slot = 0;
+};
+
+struct Launchers;  // per precision mode
+
+// Kernel launchers, implemented per precision (FP64 / mixed) and per model.
+struct KernelSet {
+  int model = 0;
+  int N = 1, nE = 0, nS = 0;
+  void (*stage)(const StageArgs&, const Ell&, int has_m2, cudaStream_t) = nullptr;
+  void (*inner)(const InnerArgs&, const Ell&, cudaStream_t) = nullptr;
+  void (*power_F)(const PowerFArgs&, const Ell&, const ReduceScratch&, cudaStream_t) = nullptr;
+  void (*power_S)(const PowerSArgs&, const ReduceScratch&, cudaStream_t) = nullptr;
+  void (*fS_eval)(const PowerSArgs&, double* out, cudaStream_t) = nullptr;  // fy = f_S(y)
+  void (*state_sumsq)(int64_t n, int64_t ld, int nz, const double* V, const void* Z,
+                      const ReduceScratch&, int slot, cudaStream_t) = nullptr;
+  void (*convert_z)(int64_t count, const void* src, double* dst, int to_double, cudaStream_t) = nullptr;
+};
+
+// Defined in kernels_fp64.cu / kernels_mixed.cu.
+bool get_kernels_fp64(int model, KernelSet* ks);
+bool get_kernels_mixed(int model, KernelSet* ks);
+
+// Precision-independent kernels (kernels_fp64.cu).
+void launch_sumsq(int64_t count, const double* x, const ReduceScratch& rs, int slot, cudaStream_t st);
+void launch_start_vector(uint64_t key, int64_t n, int64_t ld, int rows, double* v, cudaStream_t st);
+void launch_fill(double* x, int64_t count, double value, cudaStream_t st);
+void launch_fill_rows(void* z, int zsize, int64_t n, int64_t ld, int rows, const double* values,
+                      cudaStream_t st);
+
+}  // namespace emrkc

@@ -1,0 +1,254 @@
+// Ionic models in Hodgkin-Huxley form for the CUDA path (Sec. 2, Eq. monodomain).
+//
+// Each model exposes, per node and templated on the arithmetic type R
+// (double for the FP64 path, float for the mixed path):
+//   gating(V, zE, zS, lam, zinf)  : Lambda_E (<= 0) and z_inf of every gate, so
+//                                   that g_E = Lambda_E (zE - z_inf).  Gates in
+//                                   alpha/beta form use Lambda = -(alpha+beta),
+//                                   z_inf = alpha/(alpha+beta); tau-form gates use
+//                                   Lambda = -1/tau.
+//   currents(V, zE, zS, Iion, gS) : total ionic current (uA/cm^2 at 1 uF/cm^2) and
+//                                   the right-hand side g_S of the non-gating
+//                                   variables (Eq. mono_in_FSE).
+// The exponential (Rush-Larsen) step itself is applied by the stage kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace emrkc {
+
+template <typename R> struct Math;
+
+template <> struct Math<double> {
+  static __device__ __forceinline__ double ex(double x) { return exp(x); }
+  static __device__ __forceinline__ double em1(double x) { return expm1(x); }
+  static __device__ __forceinline__ double ln(double x) { return log(x); }
+  static __device__ __forceinline__ double sq(double x) { return sqrt(x); }
+  static __device__ __forceinline__ double dv(double a, double b) { return a / b; }
+  // x / (e^x - 1) with the removable singularity at 0 (1 - x/2 for |x| < 1e-7)
+  static __device__ __forceinline__ double x_em1(double x) {
+    return fabs(x) < 1e-7 ? 1.0 - 0.5 * x : x / expm1(x);
+  }
+};
+
+template <> struct Math<float> {
+  static __device__ __forceinline__ float ex(float x) { return __expf(x); }
+  static __device__ __forceinline__ float em1(float x) { return expm1f(x); }
+  static __device__ __forceinline__ float ln(float x) { return __logf(x); }
+  static __device__ __forceinline__ float sq(float x) { return sqrtf(x); }
+  static __device__ __forceinline__ float dv(float a, float b) { return __fdividef(a, b); }
+  static __device__ __forceinline__ float x_em1(float x) {
+    return fabsf(x) < 1e-4f ? 1.0f - 0.5f * x : __fdividef(x, expm1f(x));
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Pure diffusion: V only.
+template <typename R> struct ModelNone {
+  static constexpr int NE = 0, NS = 0;
+  static __device__ __forceinline__ void gating(R, const R*, const R*, R*, R*) {}
+  static __device__ __forceinline__ void currents(R, const R*, const R*, R& I, R*) { I = R(0); }
+  static __host__ __device__ constexpr double rest(int) { return 0.0; }
+};
+
+// ---------------------------------------------------------------------------
+// Linear passive test model: I_ion = g_p V, one gate w with constant rates,
+// one auxiliary c with g_S = -k_c c.  All three components are decoupled.
+template <typename R> struct ModelPassive {
+  static constexpr int NE = 1, NS = 1;
+  static __device__ __forceinline__ void gating(R, const R*, const R*, R* lam, R* zinf) {
+    lam[0] = -(R(20) + R(30));
+    zinf[0] = R(20) / (R(20) + R(30));
+  }
+  static __device__ __forceinline__ void currents(R V, const R*, const R* zS, R& I, R* gS) {
+    I = R(0.5) * V;
+    gS[0] = -R(2) * zS[0];
+  }
+  static __host__ __device__ constexpr double rest(int k) {
+    return k == 0 ? 0.0 : 1.0;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Hodgkin-Huxley 1952 (modern sign convention, V_rest = -75 mV).
+// Rates in v = V - V_rest; reversal potentials V_rest + 115, V_rest - 12,
+// V_rest + 10.613; conductances 120, 36, 0.3 mS/cm^2.
+template <typename R> struct ModelHH {
+  static constexpr int NE = 3, NS = 0;
+  using M = Math<R>;
+  static __device__ __forceinline__ void rates(R V, R* a, R* b) {
+    const R v = V - R(-75.0);
+    a[0] = M::x_em1((R(25.0) - v) / R(10.0));      // alpha_m = 0.1(25-v)/(e^{(25-v)/10}-1)
+    b[0] = R(4.0) * M::ex(-v / R(18.0));            // beta_m
+    a[1] = R(0.07) * M::ex(-v / R(20.0));           // alpha_h
+    b[1] = R(1.0) / (M::ex((R(30.0) - v) / R(10.0)) + R(1.0));  // beta_h
+    a[2] = R(0.1) * M::x_em1((R(10.0) - v) / R(10.0));  // alpha_n = 0.01(10-v)/(e^{(10-v)/10}-1)
+    b[2] = R(0.125) * M::ex(-v / R(80.0));          // beta_n
+  }
+  static __device__ __forceinline__ void gating(R V, const R*, const R*, R* lam, R* zinf) {
+    R a[3], b[3];
+    rates(V, a, b);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      lam[k] = -(a[k] + b[k]);
+      zinf[k] = a[k] / (a[k] + b[k]);
+    }
+  }
+  static __device__ __forceinline__ void currents(R V, const R* zE, const R*, R& I, R*) {
+    const R m = zE[0], h = zE[1], n = zE[2];
+    const R n2 = n * n;
+    I = R(120.0) * (m * m * m) * h * (V - R(-75.0 + 115.0)) +
+        R(36.0) * (n2 * n2) * (V - R(-75.0 - 12.0)) + R(0.3) * (V - R(-75.0 + 10.613));
+  }
+};
+
+// ---------------------------------------------------------------------------
+// ten Tusscher & Panfilov 2006, epicardial cell.
+// Gates z_E: m h j xr1 xr2 xs r s d f f2 fCass; z_S: Rbar Ki Nai Cai CaSR CaSS.
+// Currents in pA/pF, time in ms, concentrations in mM; free calcium is the
+// state and fast buffering enters through beta = 1/(1 + B K/(c + K)^2).
+template <typename R> struct ModelTTP06 {
+  static constexpr int NE = 12, NS = 6;
+  using M = Math<R>;
+  // physical constants (R in mJ/(K mol), F in C/mol), cell geometry
+  static constexpr double Rgas = 8314.472, Temp = 310.0, Far = 96485.3415;
+  static constexpr double Cap = 0.185, Vc = 0.016404, Vsr = 0.001094, Vss = 0.00005468;
+  static constexpr double Ko = 5.4, Nao = 140.0, Cao = 2.0;
+
+  static __device__ __forceinline__ R sig(R x) { return R(1) / (R(1) + M::ex(x)); }
+
+  static __device__ __forceinline__ void gating(R V, const R*, const R* zS, R* lam, R* zinf) {
+    const R CaSS = zS[5];
+    // I_Na gates
+    {
+      const R s = sig((R(-56.86) - V) / R(9.03));
+      zinf[0] = s * s;
+      const R am = sig((R(-60.0) - V) / R(5.0));
+      const R bm = R(0.1) * sig((V + R(35.0)) / R(5.0)) + R(0.10) * sig((V - R(50.0)) / R(200.0));
+      lam[0] = -R(1) / (am * bm);
+    }
+    const R hs = sig((V + R(71.55)) / R(7.43));
+    zinf[1] = hs * hs;
+    zinf[2] = hs * hs;
+    if (V >= R(-40.0)) {
+      const R bh = R(0.77) / (R(0.13) * (R(1) + M::ex(-(V + R(10.66)) / R(11.1))));
+      lam[1] = -bh;  // alpha_h = 0
+      const R bj = R(0.6) * M::ex(R(0.057) * V) / (R(1) + M::ex(R(-0.1) * (V + R(32.0))));
+      lam[2] = -bj;  // alpha_j = 0
+    } else {
+      const R ah = R(0.057) * M::ex(-(V + R(80.0)) / R(6.8));
+      const R bh = R(2.7) * M::ex(R(0.079) * V) + R(3.1e5) * M::ex(R(0.3485) * V);
+      lam[1] = -(ah + bh);
+      const R aj = (R(-2.5428e4) * M::ex(R(0.2444) * V) - R(6.948e-6) * M::ex(R(-0.04391) * V)) *
+                   (V + R(37.78)) / (R(1) + M::ex(R(0.311) * (V + R(79.23))));
+      const R bj = R(0.02424) * M::ex(R(-0.01052) * V) / (R(1) + M::ex(R(-0.1378) * (V + R(40.14))));
+      lam[2] = -(aj + bj);
+    }
+    // I_Kr gates
+    zinf[3] = sig((R(-26.0) - V) / R(7.0));
+    lam[3] = -R(1) / ((R(450.0) * sig((R(-45.0) - V) / R(10.0))) * (R(6.0) * sig((V + R(30.0)) / R(11.5))));
+    zinf[4] = sig((V + R(88.0)) / R(24.0));
+    lam[4] = -R(1) / ((R(3.0) * sig((R(-60.0) - V) / R(20.0))) * (R(1.12) * sig((V - R(60.0)) / R(20.0))));
+    // I_Ks gate
+    zinf[5] = sig((R(-5.0) - V) / R(14.0));
+    lam[5] = -R(1) / ((R(1400.0) / M::sq(R(1) + M::ex((R(5.0) - V) / R(6.0)))) * sig((V - R(35.0)) / R(15.0)) +
+                      R(80.0));
+    // I_to gates (epicardial s)
+    zinf[6] = sig((R(20.0) - V) / R(6.0));
+    {
+      const R d40 = V + R(40.0);
+      lam[6] = -R(1) / (R(9.5) * M::ex(-(d40 * d40) / R(1800.0)) + R(0.8));
+    }
+    zinf[7] = sig((V + R(20.0)) / R(5.0));
+    {
+      const R d45 = V + R(45.0);
+      lam[7] = -R(1) / (R(85.0) * M::ex(-(d45 * d45) / R(320.0)) + R(5.0) * sig((V - R(20.0)) / R(5.0)) + R(3.0));
+    }
+    // I_CaL gates
+    zinf[8] = sig((R(-8.0) - V) / R(7.5));
+    lam[8] = -R(1) / ((R(1.4) * sig((R(-35.0) - V) / R(13.0)) + R(0.25)) * (R(1.4) * sig((V + R(5.0)) / R(5.0))) +
+                      sig((R(50.0) - V) / R(20.0)));
+    zinf[9] = sig((V + R(20.0)) / R(7.0));
+    {
+      const R d27 = V + R(27.0);
+      lam[9] = -R(1) / (R(1102.5) * M::ex(-(d27 * d27) / R(225.0)) + R(200.0) * sig((R(13.0) - V) / R(10.0)) +
+                        R(180.0) * sig((V + R(30.0)) / R(10.0)) + R(20.0));
+    }
+    zinf[10] = R(0.67) * sig((V + R(35.0)) / R(7.0)) + R(0.33);
+    {
+      const R d25 = V + R(25.0);
+      lam[10] = -R(1) / (R(600.0) * M::ex(-(d25 * d25) / R(170.0)) + R(31.0) * sig((R(25.0) - V) / R(10.0)) +
+                         R(16.0) * sig((V + R(30.0)) / R(10.0)));
+    }
+    {
+      const R c = CaSS / R(0.05);
+      const R q = R(1) + c * c;
+      zinf[11] = R(0.6) / q + R(0.4);
+      lam[11] = -R(1) / (R(80.0) / q + R(2.0));
+    }
+  }
+
+  static __device__ __forceinline__ void currents(R V, const R* zE, const R* zS, R& Iion, R* gS) {
+    const R m = zE[0], h = zE[1], j = zE[2], xr1 = zE[3], xr2 = zE[4], xs = zE[5];
+    const R r = zE[6], s = zE[7], d = zE[8], f = zE[9], f2 = zE[10], fcass = zE[11];
+    const R Rbar = zS[0], Ki = zS[1], Nai = zS[2], Cai = zS[3], CaSR = zS[4], CaSS = zS[5];
+    const R RTF = R(Rgas * Temp / Far);
+    const R iRTF = R(1) / RTF;
+    const R E_K = RTF * M::ln(R(Ko) / Ki);
+    const R E_Na = RTF * M::ln(R(Nao) / Nai);
+    const R E_Ks = RTF * M::ln((R(Ko) + R(0.03) * R(Nao)) / (Ki + R(0.03) * Nai));
+    const R E_Ca = R(0.5) * RTF * M::ln(R(Cao) / Cai);
+    const R sqko = M::sq(R(Ko) / R(5.4));
+    const R VK = V - E_K;
+    const R aK1 = R(0.1) / (R(1) + M::ex(R(0.06) * (VK - R(200.0))));
+    const R bK1 = (R(3.0) * M::ex(R(0.0002) * (VK + R(100.0))) + M::ex(R(0.1) * (VK - R(10.0)))) /
+                  (R(1) + M::ex(R(-0.5) * VK));
+    const R I_K1 = R(5.405) * sqko * (aK1 / (aK1 + bK1)) * VK;
+    const R I_to = R(0.294) * r * s * VK;
+    const R I_Kr = R(0.153) * sqko * xr1 * xr2 * VK;
+    const R I_Ks = R(0.392) * xs * xs * (V - E_Ks);
+    const R I_Na = R(14.838) * (m * m * m) * h * j * (V - E_Na);
+    const R I_bNa = R(0.00029) * (V - E_Na);
+    const R u = R(2.0) * (V - R(15.0)) * iRTF;
+    const R I_CaL = R(3.980e-5) * d * f * f2 * fcass * R(2.0 * Far) * M::x_em1(u) *
+                    (R(0.25) * CaSS * M::ex(u) - R(Cao));
+    const R I_bCa = R(0.000592) * (V - E_Ca);
+    const R e1 = M::ex(R(0.35) * V * iRTF);
+    const R e2 = M::ex(R(0.35 - 1.0) * V * iRTF);
+    const R Nai3 = Nai * Nai * Nai;
+    const R I_NaCa = R(1000.0) * (e1 * Nai3 * R(Cao) - e2 * R(Nao * Nao * Nao) * Cai * R(2.5)) /
+                     (R((87.5 * 87.5 * 87.5 + Nao * Nao * Nao) * (1.38 + Cao)) * (R(1) + R(0.1) * e2));
+    const R I_NaK = R(2.724) * R(Ko / (Ko + 1.0)) * Nai / (Nai + R(40.0)) /
+                    (R(1) + R(0.1245) * M::ex(R(-0.1) * V * iRTF) + R(0.0353) * M::ex(-V * iRTF));
+    const R I_pCa = R(0.1238) * Cai / (R(0.0005) + Cai);
+    const R I_pK = R(0.0146) * VK / (R(1) + M::ex((R(25.0) - V) / R(5.98)));
+    Iion = I_Kr + I_Ks + I_K1 + I_to + I_Na + I_bNa + I_CaL + I_bCa + I_NaK + I_NaCa + I_pCa + I_pK;
+
+    // calcium dynamics
+    const R rs = R(1) + (R(1.5) / CaSR) * (R(1.5) / CaSR);
+    const R kcasr = R(2.5) - R(2.5 - 1.0) / rs;
+    const R k1 = R(0.15) / kcasr;
+    const R k2 = R(0.045) * kcasr;
+    const R CaSS2 = CaSS * CaSS;
+    const R O = k1 * CaSS2 * Rbar / (R(0.060) + k1 * CaSS2);
+    const R I_rel = R(0.102) * O * (CaSR - CaSS);
+    const R kc = R(0.00025) / Cai;
+    const R I_up = R(0.006375) / (R(1) + kc * kc);
+    const R I_leak = R(0.00036) * (CaSR - Cai);
+    const R I_xfer = R(0.0038) * (CaSS - Cai);
+    const R ci = Cai + R(0.001), csr = CaSR + R(0.3), css = CaSS + R(0.00025);
+    const R b_c = R(1) / (R(1) + R(0.2 * 0.001) / (ci * ci));
+    const R b_sr = R(1) / (R(1) + R(10.0 * 0.3) / (csr * csr));
+    const R b_ss = R(1) / (R(1) + R(0.4 * 0.00025) / (css * css));
+    const R capF = R(Cap / (Vc * Far));
+    gS[0] = -k2 * CaSS * Rbar + R(0.005) * (R(1) - Rbar);
+    gS[1] = -(I_K1 + I_to + I_Kr + I_Ks - R(2) * I_NaK + I_pK) * capF;
+    gS[2] = -(I_Na + I_bNa + R(3) * I_NaK + R(3) * I_NaCa) * capF;
+    gS[3] = b_c * ((I_leak - I_up) * R(Vsr / Vc) + I_xfer - (I_bCa + I_pCa - R(2) * I_NaCa) * R(0.5) * capF);
+    gS[4] = b_sr * (I_up - I_rel - I_leak);
+    gS[5] = b_ss * (-I_CaL * R(Cap / (2.0 * Vss * Far)) + I_rel * R(Vsr / Vss) - I_xfer * R(Vc / Vss));
+  }
+};
+
+}  // namespace emrkc

@@ -1,0 +1,913 @@
+// Host runtime of the emRKC solver: the C ABI of include/emrkc.h.
+//
+// Per step (Algorithm 3):
+//   rho policy -> power iteration (Algorithm 5, device kernels + host loop)
+//   s = get_stages(dt, rho_S), eta = 2 dt / l_s, m = get_stages(eta, rho_F)
+//   for j = 1..s: stage kernel (exponential Euler, f_S, first inner stage,
+//                 z-part of g_j), then inner kernels k = 2..m (SpMV stages;
+//                 the last one writes the V-part of g_j)
+// Three rotating state buffers hold g_{j-2}, g_{j-1}, g_j (Sec. 3.1); three
+// rotating V-sized buffers hold the inner stages u_{k-2}, u_{k-1}, u_k.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "emrkc.h"
+#include "launch.h"
+
+using namespace emrkc;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// ---- Algorithm 1 on the host (FP64) -----------------------------------------
+// get_stages: smallest s >= 1 with beta s^2 >= dt rho, beta = 2 - 4 eps / 3.
+int stages_for(double dt, double rho, double eps, double* l_s) {
+  const double beta = 2.0 - 4.0 * eps / 3.0;
+  double s_real = std::ceil(std::sqrt(dt * rho / beta));
+  int s = (s_real < 1.0 || !(s_real == s_real)) ? 1 : (int)s_real;
+  if (s < 1) s = 1;
+  if (l_s) *l_s = beta * (double)s * (double)s;
+  return s;
+}
+
+// get_coeffs: Chebyshev T_j(w0) by the three-term recurrence and
+// T_s'(w0) = s U_{s-1}(w0) with U by its own recurrence.
+struct Coeffs {
+  std::vector<double> mu, nu, kappa, c;
+};
+
+Coeffs make_coeffs(int s, double eps) {
+  Coeffs co;
+  co.mu.assign(s + 1, 0.0);
+  co.nu.assign(s + 1, 0.0);
+  co.kappa.assign(s + 1, 0.0);
+  co.c.assign(s + 1, 0.0);
+  const double w0 = 1.0 + eps / ((double)s * (double)s);
+  std::vector<double> T(s + 1), U(s + 1);
+  T[0] = 1.0;
+  U[0] = 1.0;
+  if (s >= 1) {
+    T[1] = w0;
+    U[1] = 2.0 * w0;
+  }
+  for (int j = 1; j < s; ++j) {
+    T[j + 1] = 2.0 * w0 * T[j] - T[j - 1];
+    U[j + 1] = 2.0 * w0 * U[j] - U[j - 1];
+  }
+  const double dTs = (double)s * U[s - 1];
+  const double w1 = T[s] / dTs;
+  co.mu[1] = w1 / w0;
+  co.c[1] = co.mu[1];
+  for (int j = 2; j <= s; ++j) {
+    // b_j = 1 / T_j(w0)
+    co.mu[j] = 2.0 * w1 * T[j - 1] / T[j];
+    co.nu[j] = 2.0 * w0 * T[j - 1] / T[j];
+    co.kappa[j] = -T[j - 2] / T[j];
+    co.c[j] = co.nu[j] * co.c[j - 1] + co.kappa[j] * co.c[j - 2] + co.mu[j];
+  }
+  return co;
+}
+
+
+// Rest states (Sec. 5: "provided by the ionic model's definition").
+std::vector<double> rest_state(int model) {
+  switch (model) {
+    case EMRKC_MODEL_NONE:
+      return {0.0};
+    case EMRKC_MODEL_PASSIVE:
+      return {0.0, 1.0, 1.0};
+    case EMRKC_MODEL_HH: {
+      // gates at z_inf(V_rest), rates at v = 0
+      const double am = 2.5 / std::expm1(2.5), bm = 4.0;
+      const double ah = 0.07, bh = 1.0 / (std::exp(3.0) + 1.0);
+      const double an = 0.1 * 1.0 / std::expm1(1.0), bn = 0.125;
+      return {-75.0, am / (am + bm), ah / (ah + bh), an / (an + bn)};
+    }
+    case EMRKC_MODEL_TTP06_EPI:
+      // V; m h j xr1 xr2 xs r s d f f2 fCass; Rbar Ki Nai Cai CaSR CaSS
+      return {-85.23, 0.00172, 0.7444,  0.7045, 0.00621, 0.4712, 0.0095,   2.42e-8, 0.999998, 3.373e-5,
+              0.7888, 0.9755,  0.9953,  0.9073, 136.89,  8.604,  0.000126, 3.64,    0.00036};
+    default:
+      return {};
+  }
+}
+
+struct Timing {
+  int cls;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct emrkc_solver {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  emrkc_options opt{};
+  int model = 0, N = 1, nE = 0, nS = 0, precision = 0;
+  size_t zsize = 8;   // bytes per stored z value
+  size_t rsize = 8;   // bytes per forcing value (compute type)
+  int64_t n = 0, ld = 0;
+  KernelSet ks{};
+  Ell ell{};
+  // device buffers
+  int64_t* d_slice_ptr = nullptr;
+  int32_t* d_width = nullptr;
+  int32_t* d_col = nullptr;
+  double* d_val = nullptr;
+  float* d_val32 = nullptr;
+  double* d_V[3] = {nullptr, nullptr, nullptr};
+  void* d_Z[3] = {nullptr, nullptr, nullptr};
+  double* d_U[3] = {nullptr, nullptr, nullptr};
+  void* d_F = nullptr;
+  uint8_t* d_mask = nullptr;
+  double* d_vF = nullptr;
+  double* d_vF2 = nullptr;
+  double* d_vS = nullptr;
+  double* d_vS2 = nullptr;
+  double* d_fy = nullptr;
+  double* d_act = nullptr;
+  double* d_Vn = nullptr;
+  double* d_tmp = nullptr;
+  double* d_rest = nullptr;
+  int* d_flags = nullptr;
+  ReduceScratch rs{};
+  double* h_pin = nullptr;  // pinned: [0..7] results, [8] flags
+  int cur = 0;
+  double amp = 0, t_on = 0, t_off = -1, chi = 1, Cm = 1;
+  double rhoF_raw = 0, rhoS_raw = 0;
+  bool rho_done = false;
+  double t = 0;
+  int64_t steps = 0;
+  int last_s = 0, last_m = 0;
+  double last_eta = 0, last_rhoF = 0, last_rhoS = 0;
+  int itF = 0, itS = 0;
+  int64_t total_it = 0, launches = 0;
+  bool act_on = false;
+  double phase_ms[EMRKC_NUM_PHASES] = {0};
+  int64_t phase_launches[EMRKC_NUM_PHASES] = {0};
+  std::vector<Timing> pending;
+  std::vector<cudaEvent_t> event_pool;
+  std::map<int, Coeffs> coeff_cache;
+  std::string err;
+
+  int fail(int code, const std::string& msg) {
+    err = msg;
+    return code;
+  }
+  int cuda_fail(cudaError_t e, const char* what) {
+    err = std::string(what) + ": " + cudaGetErrorString(e);
+    return EMRKC_ERR_CUDA;
+  }
+  const Coeffs& coeffs(int s) {
+    auto it = coeff_cache.find(s);
+    if (it == coeff_cache.end()) it = coeff_cache.emplace(s, make_coeffs(s, opt.eps)).first;
+    return it->second;
+  }
+  cudaEvent_t get_event() {
+    if (!event_pool.empty()) {
+      cudaEvent_t e = event_pool.back();
+      event_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  // Bracket one kernel launch with events when profiling.
+  template <class Fn>
+  void launch(int cls, Fn&& fn) {
+    if (opt.profile) {
+      Timing tm{cls, get_event(), get_event()};
+      cudaEventRecord(tm.a, stream);
+      fn();
+      cudaEventRecord(tm.b, stream);
+      pending.push_back(tm);
+    } else {
+      fn();
+    }
+    ++launches;
+    ++phase_launches[cls];
+  }
+  void harvest() {
+    for (auto& tm : pending) {
+      float ms = 0.f;
+      cudaEventSynchronize(tm.b);
+      cudaEventElapsedTime(&ms, tm.a, tm.b);
+      phase_ms[tm.cls] += ms;
+      event_pool.push_back(tm.a);
+      event_pool.push_back(tm.b);
+    }
+    pending.clear();
+  }
+  void* zrow(int buf, int k) const { return (char*)d_Z[buf] + (size_t)k * ld * zsize; }
+};
+
+namespace {
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+void free_all(emrkc_solver* s) {
+  if (!s) return;
+  cudaSetDevice(s->device);
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  s->harvest();
+  void* ptrs[] = {s->d_slice_ptr, s->d_width, s->d_col, s->d_val, s->d_val32, s->d_V[0], s->d_V[1], s->d_V[2],
+                  s->d_Z[0], s->d_Z[1], s->d_Z[2], s->d_U[0], s->d_U[1], s->d_U[2], s->d_F, s->d_mask, s->d_vF,
+                  s->d_vF2, s->d_vS, s->d_vS2, s->d_fy, s->d_act, s->d_Vn, s->d_tmp, s->d_rest, s->d_flags,
+                  s->rs.partials, s->rs.ticket, s->rs.result};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (s->h_pin) cudaFreeHost(s->h_pin);
+  for (cudaEvent_t e : s->event_pool) cudaEventDestroy(e);
+  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+}
+
+// Read back reduction results [first, first+count) and the flags word.
+int read_results(emrkc_solver* s, int first, int count) {
+  cudaError_t e = cudaMemcpyAsync(s->h_pin + first, s->rs.result + first, count * sizeof(double),
+                                  cudaMemcpyDeviceToHost, s->stream);
+  if (e != cudaSuccess) return s->cuda_fail(e, "copy of reduction results");
+  e = cudaMemcpyAsync(s->h_pin + 8, s->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+  if (e != cudaSuccess) return s->cuda_fail(e, "copy of flags");
+  e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return s->cuda_fail(e, "stream synchronisation");
+  return EMRKC_OK;
+}
+
+int check_flags(emrkc_solver* s) {
+  int flags = 0;
+  std::memcpy(&flags, s->h_pin + 8, sizeof(int));
+  if (flags & 1) {
+    int zero = 0;
+    cudaMemcpyAsync(s->d_flags, &zero, sizeof(int), cudaMemcpyHostToDevice, s->stream);
+    cudaStreamSynchronize(s->stream);
+    return s->fail(EMRKC_ERR_NONFINITE, "non-finite transmembrane potential produced by a step");
+  }
+  return EMRKC_OK;
+}
+
+double stim_at(const emrkc_solver* s, double t) {
+  return (s->d_mask != nullptr && s->t_on <= t && t <= s->t_off) ? s->amp : 0.0;
+}
+
+// Algorithm 5 on f_F (V block only).
+int power_F(emrkc_solver* s) {
+  double* V = s->d_V[s->cur];
+  s->launch(EMRKC_PHASE_OTHER, [&] { launch_sumsq(s->n, V, s->rs, 0, s->stream); });
+  s->launch(EMRKC_PHASE_OTHER, [&] { launch_sumsq(s->n, s->d_vF, s->rs, 1, s->stream); });
+  int rc = read_results(s, 0, 2);
+  if (rc) return rc;
+  if ((rc = check_flags(s))) return rc;
+  const double ny = std::sqrt(s->h_pin[0]);
+  double nv = std::sqrt(s->h_pin[1]);
+  const double delta = ny > 0.0 ? ny * s->opt.pow_eps : s->opt.pow_eps;
+  int it = 0;
+  double rho = s->rhoF_raw;
+  if (nv == 0.0) {
+    s->rhoF_raw = 0.0;
+    s->itF = 0;
+    return EMRKC_OK;
+  }
+  double q = delta / nv, rho_old = 0.0;
+  while (std::fabs(rho - rho_old) >= s->opt.pow_tol * rho && it < s->opt.pow_max_iter) {
+    rho_old = rho;
+    PowerFArgs a;
+    a.n = s->n;
+    a.V = V;
+    a.v_old = s->d_vF;
+    a.v_new = s->d_vF2;
+    a.q = q;
+    a.slot = 2;
+    s->launch(EMRKC_PHASE_POWER_F, [&] { s->ks.power_F(a, s->ell, s->rs, s->stream); });
+    if ((rc = read_results(s, 2, 1))) return rc;
+    std::swap(s->d_vF, s->d_vF2);
+    ++it;
+    nv = std::sqrt(s->h_pin[2]);
+    if (nv == 0.0) {
+      rho = 0.0;
+      break;
+    }
+    q = delta / nv;
+    rho = nv / delta;
+  }
+  s->rhoF_raw = rho;
+  s->itF = it;
+  s->total_it += it;
+  return EMRKC_OK;
+}
+
+// Algorithm 5 on f_S (full state), evaluated in FP64.
+int power_S(emrkc_solver* s) {
+  double* V = s->d_V[s->cur];
+  const int64_t rows = s->N;
+  PowerSArgs a;
+  a.n = s->n;
+  a.ld = s->ld;
+  a.V = V;
+  a.Z = s->d_Z[s->cur];
+  a.mask = s->d_mask;
+  a.stim = stim_at(s, s->t);
+  a.Cm = s->Cm;
+  s->launch(EMRKC_PHASE_OTHER, [&] { s->ks.state_sumsq(s->n, s->ld, s->N - 1, V, s->d_Z[s->cur], s->rs, 0, s->stream); });
+  s->launch(EMRKC_PHASE_OTHER, [&] { launch_sumsq(rows * s->ld, s->d_vS, s->rs, 1, s->stream); });
+  s->launch(EMRKC_PHASE_OTHER, [&] { s->ks.fS_eval(a, s->d_fy, s->stream); });
+  int rc = read_results(s, 0, 2);
+  if (rc) return rc;
+  if ((rc = check_flags(s))) return rc;
+  const double ny = std::sqrt(s->h_pin[0]);
+  double nv = std::sqrt(s->h_pin[1]);
+  const double delta = ny > 0.0 ? ny * s->opt.pow_eps : s->opt.pow_eps;
+  int it = 0;
+  double rho = s->rhoS_raw;
+  if (nv == 0.0) {
+    s->rhoS_raw = 0.0;
+    s->itS = 0;
+    return EMRKC_OK;
+  }
+  double q = delta / nv, rho_old = 0.0;
+  while (std::fabs(rho - rho_old) >= s->opt.pow_tol * rho && it < s->opt.pow_max_iter) {
+    rho_old = rho;
+    a.v_old = s->d_vS;
+    a.v_new = s->d_vS2;
+    a.fy = s->d_fy;
+    a.q = q;
+    a.slot = 3;
+    s->launch(EMRKC_PHASE_POWER_S, [&] { s->ks.power_S(a, s->rs, s->stream); });
+    if ((rc = read_results(s, 3, 1))) return rc;
+    std::swap(s->d_vS, s->d_vS2);
+    ++it;
+    nv = std::sqrt(s->h_pin[3]);
+    if (nv == 0.0) {
+      rho = 0.0;
+      break;
+    }
+    q = delta / nv;
+    rho = nv / delta;
+  }
+  s->rhoS_raw = rho;
+  s->itS = it;
+  s->total_it += it;
+  return EMRKC_OK;
+}
+
+int do_step(emrkc_solver* s, double dt) {
+  int rc;
+  double rhoF, rhoS;
+  s->itF = s->itS = 0;
+  if (s->opt.rho_every == EMRKC_RHO_FIXED) {
+    rhoF = s->opt.rho_F;
+    rhoS = s->opt.rho_S;
+  } else {
+    const bool due = (s->opt.rho_every == EMRKC_RHO_ONCE) ? !s->rho_done : (s->steps % s->opt.rho_every == 0);
+    if (due) {
+      if ((rc = power_F(s))) return rc;
+      if ((rc = power_S(s))) return rc;
+      s->rho_done = true;
+    }
+    rhoF = s->opt.safety * s->rhoF_raw;
+    rhoS = s->opt.safety * s->rhoS_raw;
+  }
+  double l_s = 0.0;
+  const int S = stages_for(dt, rhoS, s->opt.eps, &l_s);
+  const double eta = 2.0 * dt / l_s;
+  const int Mi = stages_for(eta, rhoF, s->opt.eps, nullptr);
+  const Coeffs co = s->coeffs(S);
+  const Coeffs ci = s->coeffs(Mi);
+  const int b0 = s->cur;
+  const double* Vn = (S == 1) ? s->d_V[b0] : s->d_Vn;
+  for (int j = 1; j <= S; ++j) {
+    const int bm1 = (b0 + j - 1) % 3, bm2 = (b0 + j - 2 + 3) % 3, bo = (b0 + j) % 3;
+    StageArgs a;
+    a.n = s->n;
+    a.ld = s->ld;
+    a.Vm1 = s->d_V[bm1];
+    a.Zm1 = s->d_Z[bm1];
+    a.Vm2 = j >= 2 ? s->d_V[bm2] : nullptr;
+    a.Zm2 = j >= 2 ? s->d_Z[bm2] : nullptr;
+    a.Vout = s->d_V[bo];
+    a.Zout = s->d_Z[bo];
+    a.nu = j >= 2 ? co.nu[j] : 1.0;
+    a.kappa = j >= 2 ? co.kappa[j] : 0.0;
+    a.mu_dt = co.mu[j] * dt;
+    a.eta = eta;
+    a.cm_inner = ci.c[Mi];
+    a.mu1_eta = ci.mu[1] * eta;
+    a.m = Mi;
+    a.U1 = s->d_U[0];
+    a.F = s->d_F;
+    a.mask = s->d_mask;
+    a.stim = stim_at(s, s->t + co.c[j - 1] * dt);
+    a.Cm = s->Cm;
+    a.inv_Cm = 1.0 / s->Cm;
+    a.final_stage = (j == S && Mi == 1) ? 1 : 0;
+    a.Vn = Vn;
+    a.act = s->act_on ? s->d_act : nullptr;
+    a.t_n = s->t;
+    a.dt = dt;
+    a.threshold = s->opt.act_threshold;
+    a.flags = s->d_flags;
+    a.Vn_copy = (j == 1 && S >= 2) ? s->d_Vn : nullptr;
+    s->launch(EMRKC_PHASE_STAGE, [&] { s->ks.stage(a, s->ell, j >= 2, s->stream); });
+    for (int k = 2; k <= Mi; ++k) {
+      InnerArgs b;
+      b.n = s->n;
+      b.u1 = (k - 1 == 0) ? s->d_V[bm1] : s->d_U[(k - 2) % 3];
+      b.u2 = (k - 2 == 0) ? s->d_V[bm1] : s->d_U[(k - 3) % 3];
+      b.uk = s->d_U[(k - 1) % 3];
+      b.F = s->d_F;
+      b.nu = ci.nu[k];
+      b.kappa = ci.kappa[k];
+      b.mu_eta = ci.mu[k] * eta;
+      b.last = (k == Mi) ? 1 : 0;
+      b.Vm1 = s->d_V[bm1];
+      b.Vm2 = j >= 2 ? s->d_V[bm2] : nullptr;
+      b.Vout = s->d_V[bo];
+      b.onu = a.nu;
+      b.okappa = a.kappa;
+      b.omu_dt = a.mu_dt;
+      b.eta = eta;
+      b.final_stage = (j == S && k == Mi) ? 1 : 0;
+      b.Vn = Vn;
+      b.act = a.act;
+      b.t_n = s->t;
+      b.dt = dt;
+      b.threshold = s->opt.act_threshold;
+      b.flags = s->d_flags;
+      s->launch(EMRKC_PHASE_INNER, [&] { s->ks.inner(b, s->ell, s->stream); });
+    }
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return s->cuda_fail(e, "kernel launch");
+  s->cur = (b0 + S) % 3;
+  s->t += dt;
+  s->steps += 1;
+  s->last_s = S;
+  s->last_m = Mi;
+  s->last_eta = eta;
+  s->last_rhoF = rhoF;
+  s->last_rhoS = rhoS;
+  return EMRKC_OK;
+}
+
+int sync_and_check(emrkc_solver* s) {
+  cudaError_t e = cudaMemcpyAsync(s->h_pin + 8, s->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+  if (e != cudaSuccess) return s->cuda_fail(e, "copy of flags");
+  e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return s->cuda_fail(e, "stream synchronisation");
+  return check_flags(s);
+}
+
+// Build the device matrices from the CSR input.
+int build_matrix(emrkc_solver* s, const emrkc_matrix* m) {
+  const int64_t n = m->n;
+  const bool mixed = s->precision == EMRKC_PREC_MIXED;
+  std::vector<std::vector<std::pair<int32_t, double>>> rows(n);
+  for (int64_t i = 0; i < n; ++i) {
+    double kii = 0.0;
+    for (int64_t p = m->row_ptr[i]; p < m->row_ptr[i + 1]; ++p)
+      if (m->col[p] == i) kii += m->K[p];
+    const double scale = -1.0 / (s->chi * s->Cm * m->lumped_mass[i]);
+    const double drop = 1e-14 * std::fabs(kii);
+    for (int64_t p = m->row_ptr[i]; p < m->row_ptr[i + 1]; ++p) {
+      const int32_t c = m->col[p];
+      const double k = m->K[p];
+      if (c != i && std::fabs(k) <= drop) continue;
+      if (mixed && c == i) continue;
+      rows[i].push_back({c, k * scale});
+    }
+  }
+  const int64_t ns = (n + 31) / 32;
+  std::vector<int64_t> sptr(ns + 1, 0);
+  std::vector<int32_t> width(ns, 0);
+  for (int64_t b = 0; b < ns; ++b) {
+    int w = 0;
+    for (int64_t i = b * 32; i < std::min<int64_t>(n, b * 32 + 32); ++i) w = std::max<int>(w, (int)rows[i].size());
+    width[b] = w;
+    sptr[b + 1] = sptr[b] + (int64_t)w * 32;
+  }
+  const int64_t total = sptr[ns];
+  std::vector<int32_t> col(std::max<int64_t>(total, 1), 0);
+  std::vector<double> val(mixed ? 0 : std::max<int64_t>(total, 1), 0.0);
+  std::vector<float> val32(mixed ? std::max<int64_t>(total, 1) : 0, 0.0f);
+  for (int64_t b = 0; b < ns; ++b) {
+    for (int l = 0; l < 32; ++l) {
+      const int64_t i = b * 32 + l;
+      const int32_t pad_col = (int32_t)std::min<int64_t>(i, n - 1);
+      for (int k = 0; k < width[b]; ++k) {
+        const int64_t p = sptr[b] + (int64_t)k * 32 + l;
+        if (i < n && k < (int)rows[i].size()) {
+          col[p] = rows[i][k].first;
+          if (mixed) val32[p] = (float)rows[i][k].second;
+          else val[p] = rows[i][k].second;
+        } else {
+          col[p] = pad_col;
+        }
+      }
+    }
+  }
+  cudaError_t e;
+  if ((e = dalloc(&s->d_slice_ptr, ns + 1)) != cudaSuccess) return s->fail(EMRKC_ERR_OOM, "device allocation (matrix)");
+  if ((e = dalloc(&s->d_width, ns)) != cudaSuccess) return s->fail(EMRKC_ERR_OOM, "device allocation (matrix)");
+  if ((e = dalloc(&s->d_col, col.size())) != cudaSuccess) return s->fail(EMRKC_ERR_OOM, "device allocation (matrix)");
+  cudaMemcpy(s->d_slice_ptr, sptr.data(), sptr.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+  if (ns) cudaMemcpy(s->d_width, width.data(), width.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  cudaMemcpy(s->d_col, col.data(), col.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (mixed) {
+    if ((e = dalloc(&s->d_val32, val32.size())) != cudaSuccess) return s->fail(EMRKC_ERR_OOM, "device allocation (matrix)");
+    cudaMemcpy(s->d_val32, val32.data(), val32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  } else {
+    if ((e = dalloc(&s->d_val, val.size())) != cudaSuccess) return s->fail(EMRKC_ERR_OOM, "device allocation (matrix)");
+    cudaMemcpy(s->d_val, val.data(), val.size() * sizeof(double), cudaMemcpyHostToDevice);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return s->cuda_fail(e, "matrix upload");
+  s->ell.n = n;
+  s->ell.n_slices = ns;
+  s->ell.slice_ptr = s->d_slice_ptr;
+  s->ell.width = s->d_width;
+  s->ell.col = s->d_col;
+  s->ell.val = s->d_val;
+  s->ell.val32 = s->d_val32;
+  return EMRKC_OK;
+}
+
+int validate_matrix(const emrkc_matrix* m, std::string* why) {
+  if (!m || m->n <= 0 || m->nnz < 0 || !m->row_ptr || (m->nnz > 0 && (!m->col || !m->K)) || !m->lumped_mass) {
+    *why = "matrix: null pointer or non-positive size";
+    return EMRKC_ERR_ARG;
+  }
+  if (m->n > (int64_t)INT32_MAX - 64) {
+    *why = "matrix: more than 2^31 - 64 rows";
+    return EMRKC_ERR_ARG;
+  }
+  if (m->row_ptr[0] != 0 || m->row_ptr[m->n] != m->nnz) {
+    *why = "matrix: row_ptr[0] must be 0 and row_ptr[n] must equal nnz";
+    return EMRKC_ERR_ARG;
+  }
+  for (int64_t i = 0; i < m->n; ++i) {
+    if (m->row_ptr[i + 1] < m->row_ptr[i]) {
+      *why = "matrix: row_ptr is not monotone";
+      return EMRKC_ERR_ARG;
+    }
+    if (!(m->lumped_mass[i] > 0.0) || !std::isfinite(m->lumped_mass[i])) {
+      *why = "matrix: lumped mass must be positive and finite";
+      return EMRKC_ERR_ARG;
+    }
+  }
+  for (int64_t p = 0; p < m->nnz; ++p) {
+    if (m->col[p] < 0 || m->col[p] >= m->n) {
+      *why = "matrix: column index out of range";
+      return EMRKC_ERR_ARG;
+    }
+    if (!std::isfinite(m->K[p])) {
+      *why = "matrix: non-finite entry";
+      return EMRKC_ERR_ARG;
+    }
+  }
+  return EMRKC_OK;
+}
+
+int state_copy(emrkc_solver* s, int var, double* buf, int64_t len, bool to_host, bool dev_ptr) {
+  if (!s) return EMRKC_ERR_ARG;
+  cudaSetDevice(s->device);
+  if (!buf) return s->fail(EMRKC_ERR_ARG, "null buffer");
+  if (var < -1 || var >= s->N) return s->fail(EMRKC_ERR_ARG, "variable index out of range");
+  const int64_t need = (var == -1) ? (int64_t)s->N * s->n : s->n;
+  if (len != need) return s->fail(EMRKC_ERR_STATE, "buffer length does not match the state size");
+  const int first = var == -1 ? 0 : var;
+  const int last = var == -1 ? s->N - 1 : var;
+  const cudaMemcpyKind kind_out = dev_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const cudaMemcpyKind kind_in = dev_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaError_t e = cudaSuccess;
+  for (int v = first; v <= last; ++v) {
+    double* hb = buf + (int64_t)(v - first) * s->n;
+    if (v == 0) {
+      e = to_host ? cudaMemcpyAsync(hb, s->d_V[s->cur], s->n * sizeof(double), kind_out, s->stream)
+                  : cudaMemcpyAsync(s->d_V[s->cur], hb, s->n * sizeof(double), kind_in, s->stream);
+    } else if (s->zsize == 8) {
+      double* zr = (double*)s->zrow(s->cur, v - 1);
+      e = to_host ? cudaMemcpyAsync(hb, zr, s->n * sizeof(double), kind_out, s->stream)
+                  : cudaMemcpyAsync(zr, hb, s->n * sizeof(double), kind_in, s->stream);
+    } else {
+      void* zr = s->zrow(s->cur, v - 1);
+      if (to_host) {
+        s->ks.convert_z(s->n, zr, s->d_tmp, 1, s->stream);
+        e = cudaMemcpyAsync(hb, s->d_tmp, s->n * sizeof(double), kind_out, s->stream);
+      } else {
+        e = cudaMemcpyAsync(s->d_tmp, hb, s->n * sizeof(double), kind_in, s->stream);
+        if (e == cudaSuccess) s->ks.convert_z(s->n, zr, s->d_tmp, 0, s->stream);
+      }
+    }
+    if (e != cudaSuccess) return s->cuda_fail(e, "state copy");
+    // d_tmp is reused by the next variable: order the copies
+    if (s->zsize != 8) {
+      e = cudaStreamSynchronize(s->stream);
+      if (e != cudaSuccess) return s->cuda_fail(e, "state copy");
+    }
+  }
+  e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return s->cuda_fail(e, "state copy");
+  return EMRKC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int emrkc_default_options(emrkc_options* o) {
+  if (!o) return EMRKC_ERR_ARG;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = EMRKC_PREC_FP64;
+  o->rho_every = 1;
+  o->rho_F = 0.0;
+  o->rho_S = 0.0;
+  o->eps = 0.05;
+  o->safety = 1.05;
+  o->pow_tol = 1e-2;
+  o->pow_eps = 1e-8;
+  o->pow_max_iter = 50;
+  o->seed = 0;
+  o->act_threshold = -20.0;
+  o->cuda_stream = nullptr;
+  o->device = 0;
+  o->profile = 0;
+  o->use_graphs = 1;
+  return EMRKC_OK;
+}
+
+int emrkc_num_vars(int model) {
+  const auto r = rest_state(model);
+  return r.empty() ? -1 : (int)r.size();
+}
+
+int emrkc_num_gates(int model) {
+  switch (model) {
+    case EMRKC_MODEL_NONE: return 0;
+    case EMRKC_MODEL_PASSIVE: return 1;
+    case EMRKC_MODEL_HH: return 3;
+    case EMRKC_MODEL_TTP06_EPI: return 12;
+    default: return -1;
+  }
+}
+
+int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_model, const emrkc_stimulus* stim,
+                 const emrkc_options* opt, emrkc_solver** out) {
+  if (!out) {
+    g_create_error = "out is NULL";
+    return EMRKC_ERR_ARG;
+  }
+  *out = nullptr;
+  std::string why;
+  int rc = validate_matrix(mat, &why);
+  if (rc) {
+    g_create_error = why;
+    return rc;
+  }
+  if (!tissue || !(tissue->chi > 0) || !(tissue->Cm > 0)) {
+    g_create_error = "tissue: chi and Cm must be positive";
+    return EMRKC_ERR_ARG;
+  }
+  if (emrkc_num_vars(ionic_model) < 0) {
+    g_create_error = "unknown ionic model";
+    return EMRKC_ERR_ARG;
+  }
+  emrkc_options o;
+  if (opt) o = *opt;
+  else emrkc_default_options(&o);
+  if (o.precision != EMRKC_PREC_FP64 && o.precision != EMRKC_PREC_MIXED) {
+    g_create_error = "unknown precision mode";
+    return EMRKC_ERR_ARG;
+  }
+  if (o.rho_every < EMRKC_RHO_FIXED || !(o.eps > 0) || !(o.safety > 0) || !(o.pow_tol > 0) || !(o.pow_eps > 0) ||
+      o.pow_max_iter < 1) {
+    g_create_error = "options: invalid rho policy or power-iteration parameters";
+    return EMRKC_ERR_ARG;
+  }
+  if (o.rho_every == EMRKC_RHO_FIXED && (!(o.rho_F >= 0) || !(o.rho_S >= 0))) {
+    g_create_error = "options: fixed rho values must be >= 0";
+    return EMRKC_ERR_ARG;
+  }
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev <= o.device || o.device < 0) {
+    g_create_error = std::string("no usable CUDA device: ") + (e != cudaSuccess ? cudaGetErrorString(e) : "ordinal");
+    return EMRKC_ERR_CUDA;
+  }
+  auto* s = new emrkc_solver();
+  s->opt = o;
+  s->device = o.device;
+  cudaSetDevice(s->device);
+  s->model = ionic_model;
+  s->precision = o.precision;
+  const bool ok = (s->precision == EMRKC_PREC_FP64) ? get_kernels_fp64(ionic_model, &s->ks)
+                                                    : get_kernels_mixed(ionic_model, &s->ks);
+  if (!ok) {
+    g_create_error = "no kernels for this model";
+    delete s;
+    return EMRKC_ERR_ARG;
+  }
+  s->N = s->ks.N;
+  s->nE = s->ks.nE;
+  s->nS = s->ks.nS;
+  s->zsize = s->precision == EMRKC_PREC_FP64 ? 8 : 4;
+  s->rsize = s->zsize;
+  s->n = mat->n;
+  s->ld = (mat->n + 63) / 64 * 64;
+  s->chi = tissue->chi;
+  s->Cm = tissue->Cm;
+  s->act_on = !std::isnan(o.act_threshold);
+  auto bail = [&](int code, const std::string& msg) {
+    g_create_error = msg.empty() ? s->err : msg;
+    free_all(s);
+    delete s;
+    return code;
+  };
+  if (o.cuda_stream) {
+    s->stream = (cudaStream_t)o.cuda_stream;
+  } else {
+    if ((e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)) != cudaSuccess)
+      return bail(EMRKC_ERR_CUDA, std::string("stream creation: ") + cudaGetErrorString(e));
+    s->own_stream = true;
+  }
+  if ((rc = build_matrix(s, mat))) return bail(rc, "");
+  const int64_t ld = s->ld, nz = s->N - 1;
+  bool fail = false;
+  for (int b = 0; b < 3; ++b) {
+    fail |= dalloc(&s->d_V[b], ld) != cudaSuccess;
+    fail |= cudaMalloc(&s->d_Z[b], std::max<int64_t>(nz * ld, 1) * s->zsize) != cudaSuccess;
+    fail |= dalloc(&s->d_U[b], ld) != cudaSuccess;
+  }
+  fail |= cudaMalloc(&s->d_F, ld * s->rsize) != cudaSuccess;
+  fail |= dalloc(&s->d_vF, ld) != cudaSuccess;
+  fail |= dalloc(&s->d_vF2, ld) != cudaSuccess;
+  fail |= dalloc(&s->d_vS, (int64_t)s->N * ld) != cudaSuccess;
+  fail |= dalloc(&s->d_vS2, (int64_t)s->N * ld) != cudaSuccess;
+  fail |= dalloc(&s->d_fy, (int64_t)s->N * ld) != cudaSuccess;
+  fail |= dalloc(&s->d_act, ld) != cudaSuccess;
+  fail |= dalloc(&s->d_Vn, ld) != cudaSuccess;
+  fail |= dalloc(&s->d_tmp, ld) != cudaSuccess;
+  fail |= dalloc(&s->d_rest, 64) != cudaSuccess;
+  fail |= dalloc(&s->d_flags, 4) != cudaSuccess;
+  fail |= dalloc(&s->rs.partials, kReduceMaxBlocks) != cudaSuccess;
+  fail |= dalloc(&s->rs.ticket, 4) != cudaSuccess;
+  fail |= dalloc(&s->rs.result, 16) != cudaSuccess;
+  if (fail) return bail(EMRKC_ERR_OOM, "device allocation failed");
+  if ((e = cudaMallocHost(&s->h_pin, 16 * sizeof(double))) != cudaSuccess) return bail(EMRKC_ERR_OOM, "pinned allocation failed");
+  std::memset(s->h_pin, 0, 16 * sizeof(double));
+  if (stim && stim->node_mask) {
+    if ((e = dalloc(&s->d_mask, s->n)) != cudaSuccess) return bail(EMRKC_ERR_OOM, "device allocation failed");
+    cudaMemcpy(s->d_mask, stim->node_mask, s->n, cudaMemcpyHostToDevice);
+    s->amp = stim->amplitude;
+    s->t_on = stim->t_on;
+    s->t_off = stim->t_off;
+  }
+  cudaMemsetAsync(s->d_flags, 0, 4 * sizeof(int), s->stream);
+  cudaMemsetAsync(s->rs.ticket, 0, 4 * sizeof(unsigned int), s->stream);
+  cudaMemsetAsync(s->rs.result, 0, 16 * sizeof(double), s->stream);
+  for (int b = 0; b < 3; ++b) cudaMemsetAsync(s->d_U[b], 0, ld * sizeof(double), s->stream);
+  // rest state in every buffer
+  const auto rest = rest_state(ionic_model);
+  cudaMemcpy(s->d_rest, rest.data(), rest.size() * sizeof(double), cudaMemcpyHostToDevice);
+  for (int b = 0; b < 3; ++b) {
+    launch_fill(s->d_V[b], ld, rest[0], s->stream);
+    if (nz > 0) launch_fill_rows(s->d_Z[b], (int)s->zsize, s->n, ld, (int)nz, s->d_rest + 1, s->stream);
+  }
+  launch_fill(s->d_act, ld, std::nan(""), s->stream);
+  launch_start_vector(o.seed, s->n, ld, 1, s->d_vF, s->stream);
+  launch_start_vector(~o.seed, s->n, ld, s->N, s->d_vS, s->stream);
+  if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess)
+    return bail(EMRKC_ERR_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));
+  if ((e = cudaGetLastError()) != cudaSuccess)
+    return bail(EMRKC_ERR_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));
+  *out = s;
+  return EMRKC_OK;
+}
+
+int emrkc_step(emrkc_solver* s, double dt) {
+  if (!s) return EMRKC_ERR_ARG;
+  if (!(dt > 0) || !std::isfinite(dt)) return s->fail(EMRKC_ERR_ARG, "dt must be positive and finite");
+  cudaSetDevice(s->device);
+  return do_step(s, dt);
+}
+
+int emrkc_run(emrkc_solver* s, double T, double dt) {
+  if (!s) return EMRKC_ERR_ARG;
+  if (!(dt > 0) || !(T >= 0) || !std::isfinite(T) || !std::isfinite(dt))
+    return s->fail(EMRKC_ERR_ARG, "T and dt must be finite, dt > 0, T >= 0");
+  const double r = T / dt;
+  const int64_t steps = (int64_t)std::llround(r);
+  if (std::fabs((double)steps * dt - T) > 1e-9 * std::max(1.0, std::fabs(T)))
+    return s->fail(EMRKC_ERR_ARG, "T is not an integer multiple of dt");
+  cudaSetDevice(s->device);
+  for (int64_t k = 0; k < steps; ++k) {
+    int rc = do_step(s, dt);
+    if (rc) return rc;
+  }
+  return sync_and_check(s);
+}
+
+int emrkc_sync(emrkc_solver* s) {
+  if (!s) return EMRKC_ERR_ARG;
+  cudaSetDevice(s->device);
+  int rc = sync_and_check(s);
+  s->harvest();
+  return rc;
+}
+
+int emrkc_get_state(emrkc_solver* s, int var, double* host_out, int64_t len) {
+  return state_copy(s, var, host_out, len, true, false);
+}
+
+int emrkc_set_state(emrkc_solver* s, int var, const double* host_in, int64_t len) {
+  return state_copy(s, var, const_cast<double*>(host_in), len, false, false);
+}
+
+int emrkc_get_state_device(emrkc_solver* s, int var, double* dev_out, int64_t len) {
+  return state_copy(s, var, dev_out, len, true, true);
+}
+
+int emrkc_set_state_device(emrkc_solver* s, int var, const double* dev_in, int64_t len) {
+  return state_copy(s, var, const_cast<double*>(dev_in), len, false, true);
+}
+
+int emrkc_get_activation_times(emrkc_solver* s, double* host_out, int64_t n) {
+  if (!s) return EMRKC_ERR_ARG;
+  if (!host_out) return s->fail(EMRKC_ERR_ARG, "null buffer");
+  if (n != s->n) return s->fail(EMRKC_ERR_STATE, "length must equal the number of nodes");
+  cudaSetDevice(s->device);
+  cudaError_t e = cudaMemcpyAsync(host_out, s->d_act, s->n * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return s->cuda_fail(e, "activation copy");
+  return EMRKC_OK;
+}
+
+int emrkc_estimate_rho(emrkc_solver* s, double* rho_F, double* rho_S, int* it_F, int* it_S) {
+  if (!s) return EMRKC_ERR_ARG;
+  cudaSetDevice(s->device);
+  int rc = power_F(s);
+  if (!rc) rc = power_S(s);
+  if (rc) return rc;
+  if (rho_F) *rho_F = s->rhoF_raw;
+  if (rho_S) *rho_S = s->rhoS_raw;
+  if (it_F) *it_F = s->itF;
+  if (it_S) *it_S = s->itS;
+  return EMRKC_OK;
+}
+
+int emrkc_set_time(emrkc_solver* s, double t, int64_t steps) {
+  if (!s) return EMRKC_ERR_ARG;
+  if (!std::isfinite(t) || steps < 0) return s->fail(EMRKC_ERR_ARG, "invalid time or step count");
+  s->t = t;
+  s->steps = steps;
+  return EMRKC_OK;
+}
+
+int emrkc_get_stats(emrkc_solver* s, emrkc_stats* out) {
+  if (!s || !out) return EMRKC_ERR_ARG;
+  cudaSetDevice(s->device);
+  s->harvest();
+  std::memset(out, 0, sizeof(*out));
+  out->t = s->t;
+  out->steps = s->steps;
+  out->s = s->last_s;
+  out->m = s->last_m;
+  out->eta = s->last_eta;
+  out->rho_F = s->last_rhoF;
+  out->rho_S = s->last_rhoS;
+  out->pow_iters_F = s->itF;
+  out->pow_iters_S = s->itS;
+  out->total_pow_iters = s->total_it;
+  out->launches = s->launches;
+  for (int k = 0; k < EMRKC_NUM_PHASES; ++k) {
+    out->phase_ms[k] = s->phase_ms[k];
+    out->phase_launches[k] = s->phase_launches[k];
+  }
+  return EMRKC_OK;
+}
+
+const char* emrkc_last_error(const emrkc_solver* s) {
+  if (!s) return g_create_error.c_str();
+  return s->err.c_str();
+}
+
+void emrkc_destroy(emrkc_solver* s) {
+  if (!s) return;
+  free_all(s);
+  delete s;
+}
+
+}  // extern "C"

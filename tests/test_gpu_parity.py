@@ -1,0 +1,241 @@
+"""GPU parity of the CUDA emRKC path against the FP64 CPU oracle.
+
+Both sides receive the same seeded inputs (workloads package) and run the
+same number of steps from the model's rest state; the oracle follows
+Algorithm 3 / Algorithm 5 literally, the GPU runs the fused kernels through
+the C ABI.  Tolerances:
+  FP64 path : relative L2 (lumped mass) error in V <= 1e-10 (the FP64 target),
+              every other state variable within 1e-9 of its scale,
+              activation times within 1e-8 ms;
+  mixed path: relative L2 error in V <= 1e-3 and activation times within
+              0.05 ms of the FP64 GPU path.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import paper_2401_01745_gb300 as pkg
+from oracle.emrkc import Monodomain, OracleRun
+from workloads import make_workload
+
+pytestmark = pytest.mark.gpu
+
+TOL_V = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    pkg.build()
+
+
+def _run_pair(w, steps, rho_every=1, fixed=None, precision=pkg.PREC_FP64, seed=0, oracle=True):
+    kw = dict(rho_every=rho_every, seed=seed, precision=precision)
+    if fixed is not None:
+        kw.update(rho_every=pkg.RHO_FIXED, rho_F=fixed[0], rho_S=fixed[1])
+    sol = pkg.Solver.from_workload(w, **kw)
+    log = []
+    for _ in range(steps):
+        sol.step(w.dt)
+        st = sol.stats()
+        log.append((st["s"], st["m"]))
+    sol.sync()
+    Y = sol.get_state()
+    act = sol.activation_times()
+    stats = sol.stats()
+    sol.close()
+    if not oracle:
+        return Y, act, log, stats, None, None, None
+    prob = Monodomain.from_workload(w)
+    ref = OracleRun(prob, rho_every=rho_every if fixed is None else 1, fixed_rho=fixed, seed=seed)
+    for _ in range(steps):
+        ref.step(w.dt)
+    return Y, act, log, stats, prob, ref, [(l[0], l[1]) for l in ref.log]
+
+
+def _assert_parity(Y, act, prob, ref, tol_v=TOL_V):
+    err = prob.l2_norm(Y[0] - ref.Y[0]) / prob.l2_norm(ref.Y[0])
+    assert err <= tol_v, f"rel L2 error in V {err:.3e}"
+    for k in range(1, prob.N):
+        scale = max(np.max(np.abs(ref.Y[k])), 1e-12)
+        d = np.max(np.abs(Y[k] - ref.Y[k])) / scale
+        assert d <= 1e-9, f"variable {k}: max rel diff {d:.3e}"
+    a_gpu, a_ref = act, ref.act
+    assert np.array_equal(np.isnan(a_gpu), np.isnan(a_ref))
+    fin = np.isfinite(a_ref)
+    if fin.any():
+        assert np.max(np.abs(a_gpu[fin] - a_ref[fin])) <= 1e-8
+    return err
+
+
+@pytest.mark.parametrize("name,dt,steps,h", [
+    ("square33x29_hh", 0.05, 120, 1.0 / 64),   # ragged n = 957, through the upstroke
+    ("square33x29_hh", 0.02, 250, 1.0 / 64),
+    ("slab23x9x5_ttp", 0.05, 60, 0.01),        # n = 1035, s = 1, m = 2
+    ("slab23x9x5_hh", 0.05, 60, 0.01),
+    ("square40x3_ttp", 0.25, 20, 1.0 / 128),   # large dt: s >= 2
+])
+def test_fp64_parity_rho_every_step(name, dt, steps, h):
+    w = make_workload(name, h=h)
+    w.dt = dt
+    Y, act, log, st, prob, ref, rlog = _run_pair(w, steps)
+    assert log == rlog, "stage counts (s, m) differ from the oracle"
+    _assert_parity(Y, act, prob, ref)
+
+
+@pytest.mark.parametrize("fixed", [(900.0, 60.0), (5000.0, 300.0), (40.0, 0.0)])
+def test_fp64_parity_fixed_rho_many_stages(fixed):
+    """Fixed rho forces s > 1 and m > 1 (three-term recurrences on both levels)."""
+    w = make_workload("slab13x7x5_ttp", h=0.01)
+    w.dt = 0.1
+    Y, act, log, st, prob, ref, rlog = _run_pair(w, 25, fixed=fixed)
+    assert log == rlog
+    s, m = log[-1]
+    if fixed[0] > 1000:
+        assert s >= 3 and m >= 3
+    _assert_parity(Y, act, prob, ref)
+
+
+def test_fp64_parity_rho_once():
+    w = make_workload("slab23x9x5_ttp", h=0.01)
+    Y, act, log, st, prob, ref, rlog = _run_pair(w, 50, rho_every=pkg.RHO_ONCE)
+    assert log == rlog
+    _assert_parity(Y, act, prob, ref)
+
+
+def test_power_iteration_matches_oracle():
+    from oracle.power import compute_rho, start_vector
+    w = make_workload("slab23x9x5_ttp", h=0.01)
+    sol = pkg.Solver.from_workload(w, seed=1234)
+    rF, rS, itF, itS = sol.estimate_rho()
+    prob = Monodomain.from_workload(w)
+    Y = prob.initial_state()
+    vF, rFo, itFo = compute_rho(0.0, Y[0], prob.rho_F_fn, start_vector(1234, prob.n), 0.0)
+    vS, rSo, itSo = compute_rho(0.0, Y.ravel(), prob.rho_S_fn,
+                                start_vector(~1234 & 0xFFFFFFFFFFFFFFFF, prob.N * prob.n), 0.0)
+    assert (itF, itS) == (itFo, itSo)
+    assert rF == pytest.approx(rFo, rel=1e-6)
+    assert rS == pytest.approx(rSo, rel=1e-6)
+    # warm start: a second call converges in very few iterations
+    rF2, rS2, itF2, itS2 = sol.estimate_rho()
+    assert itF2 <= 3 and itS2 <= 3
+    sol.close()
+
+
+def test_passive_model_closed_form_on_gpu():
+    """Sec. 4.4 amplification on a 1-D cosine eigenvector, evaluated on the GPU."""
+    from numpy.polynomial import chebyshev as C
+
+    def P(m, z):
+        w0 = 1.0 + 0.05 / m ** 2
+        T = [0] * m + [1]
+        w1 = C.chebval(w0, T) / C.chebval(w0, C.chebder(T))
+        return C.chebval(w0 + w1 * z, T) / C.chebval(w0, T)
+
+    n, L, k = 40, 0.39, 7
+    w = make_workload(f"line{n}_passive", length=L)
+    w.stim_mask[:] = 0
+    dt, rhoF, rhoS = 0.2, 3000.0, 40.0
+    sol = pkg.Solver.from_workload(w, rho_every=pkg.RHO_FIXED, rho_F=rhoF, rho_S=rhoS)
+    x = w.coords[:, 0]
+    Y0 = np.stack([np.cos(k * np.pi * x / L), np.full(n, 0.9), np.full(n, -0.7)])
+    sol.set_state(Y0)
+    sol.step(dt)
+    Y1 = sol.get_state()
+    st = sol.stats()
+    sol.close()
+    s, m, eta = st["s"], st["m"], st["eta"]
+    assert s >= 2 and m >= 2
+    h = L / (n - 1)
+    lamF = -(4.0 / (h * h * 1400.0)) * math.sin(k * math.pi / (2 * (n - 1))) ** 2
+    Phi = (P(m, eta * lamF) - 1.0) / (eta * lamF)
+    np.testing.assert_allclose(Y1[0], P(s, dt * Phi * (lamF - 0.5)) * Y0[0], rtol=1e-11, atol=1e-12)
+    lamE = -50.0
+    phiE = math.expm1(eta * lamE) / (eta * lamE)
+    np.testing.assert_allclose(Y1[1] - 0.4, P(s, dt * phiE * lamE) * 0.5, rtol=1e-11)
+    np.testing.assert_allclose(Y1[2], P(s, -dt * 2.0) * -0.7, rtol=1e-11)
+
+
+def test_conservation_pure_diffusion_gpu():
+    w = make_workload("square31x23_none", h=1.0 / 30)
+    w.stim_mask[:] = 0
+    sol = pkg.Solver.from_workload(w, rho_every=pkg.RHO_FIXED, rho_F=4000.0, rho_S=1.0)
+    rng = np.random.default_rng(4)
+    V0 = rng.normal(size=w.n)
+    sol.set_state(V0, var=0)
+    sol.run(20.0, 0.2)
+    V = sol.get_state(var=0)
+    rp, col, K, M = pkg.assemble_p1(w.coords, w.cells, w.D)
+    sol.close()
+    assert abs(np.sum(M * V) - np.sum(M * V0)) <= 1e-11 * np.sum(M * np.abs(V0))
+    assert np.linalg.norm(V - V0) > 0.5 * np.linalg.norm(V0 - V0.mean())
+
+
+def test_full_size_square65_hh_parity():
+    """The 65 x 65 HH square at dt = 0.05 ms, rho every step, T = 20 ms (all 400 steps)."""
+    w = make_workload("square65_hh")
+    Y, act, log, st, prob, ref, rlog = _run_pair(w, w.steps)
+    assert log == rlog
+    _assert_parity(Y, act, prob, ref)
+
+
+def test_full_size_slab_ttp_parity_first_steps():
+    """The 201 x 71 x 31 TTP06 slab (442,401 nodes) in the launch configuration of the
+    benchmark, compared with the oracle over its first steps (rho every step)."""
+    w = make_workload("slab_ttp")
+    Y, act, log, st, prob, ref, rlog = _run_pair(w, 4)
+    assert log == rlog
+    _assert_parity(Y, act, prob, ref)
+
+
+@pytest.mark.parametrize("name,dt,steps,h", [
+    ("slab41x15x7_ttp", 0.05, 300, 0.01),
+    ("square33x33_hh", 0.02, 300, 1.0 / 64),
+])
+def test_mixed_precision_vs_fp64(name, dt, steps, h):
+    w = make_workload(name, h=h)
+    w.dt = dt
+    Y64, a64, log64, *_ = _run_pair(w, steps, oracle=False)
+    Y32, a32, log32, *_ = _run_pair(w, steps, precision=pkg.PREC_MIXED, oracle=False)
+    prob = Monodomain.from_workload(w)
+    err = prob.l2_norm(Y32[0] - Y64[0]) / prob.l2_norm(Y64[0])
+    assert err <= 1e-3, f"mixed vs FP64 rel L2 error in V {err:.3e}"
+    fin = np.isfinite(a64) & np.isfinite(a32)
+    assert np.array_equal(np.isfinite(a64), np.isfinite(a32))
+    assert fin.any()
+    assert np.max(np.abs(a64[fin] - a32[fin])) <= 0.05
+
+
+def test_state_roundtrip_and_errors():
+    w = make_workload("square9x7_ttp", h=0.01)
+    sol = pkg.Solver.from_workload(w)
+    Y = sol.get_state()
+    assert Y.shape == (19, w.n)
+    np.testing.assert_allclose(Y[:, 0], Monodomain.from_workload(w).initial_state()[:, 0])
+    Y[5] += 1e-3
+    sol.set_state(Y)
+    np.testing.assert_array_equal(sol.get_state(), Y)
+    with pytest.raises(pkg.EmrkcError) as ei:
+        sol.run(1.0, 0.3)  # not an integer number of steps
+    assert ei.value.code == 1
+    with pytest.raises(pkg.EmrkcError) as ei:
+        sol.set_state(np.zeros(w.n + 1), var=0)
+    assert ei.value.code == 6
+    # a NaN injected through set_state is reported after the next step
+    V = sol.get_state(var=0)
+    V[3] = np.nan
+    sol.set_state(V, var=0)
+    with pytest.raises(pkg.EmrkcError) as ei:
+        sol.step(0.05)
+        sol.sync()
+    assert ei.value.code == 4
+    sol.close()
+
+
+def test_tiny_meshes():
+    for name in ["line2_hh", "line3_ttp", "square2x2_hh"]:
+        w = make_workload(name)
+        Y, act, log, st, prob, ref, rlog = _run_pair(w, 30)
+        assert log == rlog
+        _assert_parity(Y, act, prob, ref)
