@@ -1,0 +1,407 @@
+"""Benchmark: emRKC node-timesteps/s on one GB300 (or N replicas).
+
+Default workload: the 3-D slab of 201 x 71 x 31 nodes (442,401 nodes, 2.52 M
+Kuhn tetrahedra, D = diag(1.33, 0.18, 0.18) mS/cm), TTP06 epicardial,
+dt = 0.05 ms, stimulus 50 uA/cm^2 for 2 ms on the 0.15 cm corner cube.
+One timed step = one emRKC step through the C ABI: the power iteration for
+rho_F and rho_S (every step by default), the stage counts, the fused stage
+kernel and the inner SpMV stages.  The headline path is the mixed-precision
+form; the plain FP64 form is measured on the same workload beside it, and the
+mixed result is compared with the FP64 result over a T = 50 ms horizon.
+
+L2 (129 MB) is flushed before every timed step by writing a 512 MB buffer on
+the same stream (outside the step's CUDA-event interval).
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (a slab with fewer z-layers), same metric.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "node-timesteps/s (emRKC step, <=1e-3 rel. L2 error in V vs plain FP64)"
+UNIT = "node-timesteps/s"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        time.sleep(0.25)
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        try:
+            import torch
+            if not torch.cuda.is_available():
+                backend = "gloo"
+        except Exception:
+            backend = "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _sum_over_ranks(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (reference arm and cpu_baseline): bounded sample of the slab
+
+
+def _oracle_sample(steps_budget_s, K, W=0):
+    """Oracle emRKC on a slab with the workload's x-y extent and fewer z-layers,
+    sized so that K steps take about ``steps_budget_s`` seconds."""
+    from oracle.emrkc import Monodomain, OracleRun
+    from workloads import make_workload
+
+    per_node_step = 1.0 / 3.4e5  # s, measured oracle cost (calibrated below)
+    n_target = steps_budget_s / (max(K, 1) * per_node_step)
+    nz = int(max(2, min(31, round(n_target / (201 * 71)))))
+    w = make_workload(f"slab201x71x{nz}_ttp", h=0.01)
+    prob = Monodomain.from_workload(w)
+    r = OracleRun(prob, rho_every=1)
+    for _ in range(W):
+        r.step(w.dt)
+    t0 = time.perf_counter()
+    for _ in range(K):
+        r.step(w.dt)
+    el = time.perf_counter() - t0
+    return w.n, K, el
+
+
+def run_reference(args):
+    world, rank, local = _dist_init()
+    if rank != 0:
+        return 0
+    budget = 120.0
+    n, K, el = _oracle_sample(budget, args.steps, args.warmup)
+    value = n * K / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": K, "warmup": args.warmup, "ms_per_step": 1e3 * el / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"slab 201x71x{n // (201 * 71)} nodes (bounded sample of the 201x71x31 slab), "
+                               "TTP06 epi, dt 0.05 ms, rho every step",
+                   "nodes": n, "precision": "fp64 CPU oracle (numpy, single thread)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{K} emRKC steps on {n} nodes"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--workload", default="slab_ttp")
+    ap.add_argument("--rho-every", type=int, default=1)
+    ap.add_argument("--horizon-steps", type=int, default=1000, help="steps of the mixed-vs-FP64 accuracy check")
+    ap.add_argument("--fp64-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    import paper_2401_01745_gb300 as pkg
+    from workloads import make_workload
+
+    world, rank, local = _dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pkg.build()
+    w = make_workload(args.workload)
+    rp, col, K, M = pkg.assemble_p1(w.coords, w.cells, w.D)
+    stream = torch.cuda.Stream(device=dev)
+    prec = pkg.PREC_MIXED if args.precision == "mixed" else pkg.PREC_FP64
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    hbm_peak, peak_kind = _peaks()
+
+    def make(precision, profile=False):
+        return pkg.Solver(rp, col, K, M, chi=w.chi, Cm=w.Cm, model=w.model, mask=w.stim_mask,
+                          amplitude=w.stim_amp, t_on=w.t_on, t_off=w.t_off, precision=precision,
+                          rho_every=args.rho_every, stream=stream.cuda_stream, device=local,
+                          profile=profile)
+
+    def timed_steps(sol, K_, flush_l2=True):
+        """K_ steps, each bracketed by CUDA events on the solver's stream, L2
+        flushed before each step (outside the bracket)."""
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K_)]
+        l0 = sol.stats()["launches"]
+        with torch.cuda.stream(stream):
+            for k in range(K_):
+                if flush_l2:
+                    flush.fill_(float(k))
+                evs[k][0].record(stream)
+                sol.step(w.dt)
+                evs[k][1].record(stream)
+        stream.synchronize()
+        sol.sync()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        return ms, sol.stats()["launches"] - l0
+
+    # ---- headline: precision under test, K timed steps after W warm-up ----
+    sol = make(prec)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            sol.step(w.dt)
+    sol.sync()
+    torch.cuda.synchronize()
+    _barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms, launches = timed_steps(sol, args.steps)
+    torch.cuda.synchronize()
+    _barrier(world)
+    st = sol.stats()
+    total_ms = sum(ms)
+    total_ms_max = _max_over_ranks(total_ms, world, dev)
+    units = _sum_over_ranks(float(w.n * args.steps), world, dev)
+    value = units / (total_ms_max / 1e3)
+    sol.close()
+
+    # ---- per-kernel durations (CUDA events around every launch, same stream) ----
+    solp = make(prec, profile=True)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            solp.step(w.dt)
+    solp.sync()
+    p0 = solp.stats()
+    Kp = min(args.steps, 100)
+    timed_steps(solp, Kp)
+    p1 = solp.stats()
+    solp.close()
+    phase_ms = {k: p1["phase_ms"][k] - p0["phase_ms"][k] for k in p1["phase_ms"]}
+    phase_n = {k: p1["phase_launches"][k] - p0["phase_launches"][k] for k in p1["phase_launches"]}
+    dominant = max(phase_ms, key=lambda k: phase_ms[k])
+    N = pkg.num_vars(w.model)
+    zb = 4 if prec == pkg.PREC_MIXED else 8
+    # algorithmic bytes per node per launch (rows of L: off-diagonals only in
+    # mixed mode, 4-byte value + 4-byte column; FP64 mode 8 + 4 incl. diagonal)
+    nnz_row = (col.size / w.n - (1 if prec == pkg.PREC_MIXED else 0))
+    mat_b = nnz_row * ((4 + 4) if prec == pkg.PREC_MIXED else (8 + 4))
+    fb = 4 if prec == pkg.PREC_MIXED else 8
+    bytes_stage = 8 + (N - 1) * zb + 1 + mat_b + (N - 1) * zb + 8 + fb  # V,z,mask,L in; z,u1,F out (m>=2)
+    bytes_inner = 8 + 8 + fb + mat_b + 8                                  # u1, V, F, L in; V out
+    per_launch = {"stage": bytes_stage, "inner": bytes_inner}
+    dom_key = dominant if dominant in per_launch else "stage"
+    avg_ms = phase_ms[dom_key] / max(phase_n[dom_key], 1)
+    achieved = per_launch[dom_key] * w.n / (avg_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": f"{dom_key} ({'stage_kernel' if dom_key == 'stage' else 'inner_kernel'})",
+                "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+                "bytes_per_node": per_launch[dom_key], "avg_launch_us": avg_ms * 1e3,
+                "traffic": None}
+    kernel_breakdown = {k: {"ms_per_step": phase_ms[k] / Kp, "launches_per_step": phase_n[k] / Kp}
+                        for k in phase_ms}
+
+    # ---- end to end through the C ABI with host buffers ----
+    sol = make(prec)
+    pinned_in = torch.empty((N, w.n), dtype=torch.float64, pin_memory=True)
+    pinned_out = torch.empty((w.n,), dtype=torch.float64, pin_memory=True)
+    sol.get_state(out=pinned_in.numpy())
+    Ke = min(args.steps, 100)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            sol.set_state(pinned_in.numpy())
+            sol.step(w.dt)
+            sol.get_state(var=0, out=pinned_out.numpy())
+    torch.cuda.synchronize()
+    _barrier(world)
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for _ in range(Ke):
+            sol.set_state(pinned_in.numpy())
+            sol.step(w.dt)
+            sol.get_state(var=0, out=pinned_out.numpy())
+    sol.sync()
+    e2e_s = _max_over_ranks(time.perf_counter() - t0, world, dev)
+    sol.close()
+    e2e = {"value": _sum_over_ranks(float(w.n * Ke), world, dev) / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(N * w.n * 8), "d2h_bytes_per_step": int(w.n * 8),
+           "steps": Ke, "api": "emrkc_set_state(all vars, pinned host) + emrkc_step + emrkc_get_state(V)"}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == pkg.PREC_MIXED else "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: 201x71x31-node Kuhn-tet slab 2.0x0.7x0.3 cm, TTP06 epi, "
+                               "dt 0.05 ms, 50 uA/cm^2 corner stimulus",
+                   "nodes": w.n, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "precision": ("mixed: FP32 z, ionic model, gating, SpMV; FP64 V recurrence, "
+                                 "stage coefficients, rho" if prec == pkg.PREC_MIXED else "fp64"),
+                   "rho_policy": "every step" if args.rho_every == 1 else f"every {args.rho_every}",
+                   "s": st["s"], "m": st["m"], "l2": "flushed before every timed step (512 MB write)"},
+        "roofline": roofline,
+        "kernels": kernel_breakdown,
+        "gpu_launches": int(launches),
+        "e2e": e2e,
+        "clocks": clk.summary(),
+    }
+
+    # ---- plain FP64 form on the same workload, and accuracy of the mixed form ----
+    if prec == pkg.PREC_MIXED and rank == 0:
+        s64 = make(pkg.PREC_FP64)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                s64.step(w.dt)
+        s64.sync()
+        ms64, _ = timed_steps(s64, args.fp64_steps)
+        s64.close()
+        v64 = w.n * args.fp64_steps / (sum(ms64) / 1e3)
+        out["fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": sum(ms64) / args.fp64_steps,
+                       "steps": args.fp64_steps, "speedup_of_headline": value / v64}
+    if prec == pkg.PREC_MIXED and rank == 0 and not args.no_accuracy:
+        H = args.horizon_steps
+        a = make(pkg.PREC_FP64)
+        b = make(pkg.PREC_MIXED)
+        with torch.cuda.stream(stream):
+            for _ in range(H):
+                a.step(w.dt)
+                b.step(w.dt)
+        a.sync()
+        b.sync()
+        Va, Vb = a.get_state(var=0), b.get_state(var=0)
+        ta, tb = a.activation_times(), b.activation_times()
+        a.close()
+        b.close()
+        err = float(np.sqrt(np.sum(M * (Va - Vb) ** 2) / np.sum(M * Va * Va)))
+        both = np.isfinite(ta) & np.isfinite(tb)
+        out["accuracy"] = {"rel_l2_err_V_vs_fp64": err, "T_ms": H * w.dt,
+                           "max_activation_diff_ms": float(np.max(np.abs(ta[both] - tb[both]))) if both.any() else None,
+                           "activated_nodes": int(both.sum()),
+                           "activation_pattern_equal": bool(np.array_equal(np.isfinite(ta), np.isfinite(tb)))}
+
+    if rank == 0 and not args.no_cpu_baseline:
+        n_s, K_s, el = _oracle_sample(15.0, 10)
+        out["cpu_baseline"] = {"value": n_s * K_s / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"{K_s} FP64 oracle emRKC steps (numpy, 1 thread) on a "
+                                         f"201x71x{n_s // (201 * 71)} slab ({n_s} nodes), same h, model, dt"}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

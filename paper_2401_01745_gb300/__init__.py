@@ -27,7 +27,7 @@ class EmrkcError(RuntimeError):
 
 
 def build(verbose=False, force=False):
-    from .build import build as _b
+    from ._buildlib import build as _b
     return _b(verbose=verbose, force=force)
 
 

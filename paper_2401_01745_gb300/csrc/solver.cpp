@@ -588,36 +588,38 @@ int state_copy(emrkc_solver* s, int var, double* buf, int64_t len, bool to_host,
   if (var < -1 || var >= s->N) return s->fail(EMRKC_ERR_ARG, "variable index out of range");
   const int64_t need = (var == -1) ? (int64_t)s->N * s->n : s->n;
   if (len != need) return s->fail(EMRKC_ERR_STATE, "buffer length does not match the state size");
-  const int first = var == -1 ? 0 : var;
-  const int last = var == -1 ? s->N - 1 : var;
-  const cudaMemcpyKind kind_out = dev_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  const cudaMemcpyKind kind_in = dev_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind kind = dev_ptr ? cudaMemcpyDeviceToDevice
+                                      : (to_host ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice);
+  const size_t row = (size_t)s->n * sizeof(double), pitch_b = (size_t)s->n * sizeof(double);
   cudaError_t e = cudaSuccess;
-  for (int v = first; v <= last; ++v) {
-    double* hb = buf + (int64_t)(v - first) * s->n;
-    if (v == 0) {
-      e = to_host ? cudaMemcpyAsync(hb, s->d_V[s->cur], s->n * sizeof(double), kind_out, s->stream)
-                  : cudaMemcpyAsync(s->d_V[s->cur], hb, s->n * sizeof(double), kind_in, s->stream);
-    } else if (s->zsize == 8) {
-      double* zr = (double*)s->zrow(s->cur, v - 1);
-      e = to_host ? cudaMemcpyAsync(hb, zr, s->n * sizeof(double), kind_out, s->stream)
-                  : cudaMemcpyAsync(zr, hb, s->n * sizeof(double), kind_in, s->stream);
+  // V
+  if (var <= 0) {
+    e = to_host ? cudaMemcpyAsync(buf, s->d_V[s->cur], row, kind, s->stream)
+                : cudaMemcpyAsync(s->d_V[s->cur], buf, row, kind, s->stream);
+    if (e != cudaSuccess) return s->cuda_fail(e, "state copy");
+  }
+  // z rows first..last (z index = var - 1), as one pitched copy
+  const int zfirst = (var == -1) ? 0 : var - 1;
+  const int zrows = (var == -1) ? s->N - 1 : (var >= 1 ? 1 : 0);
+  if (zrows > 0) {
+    double* hb = buf + ((var == -1) ? s->n : 0);
+    const size_t dpitch = (size_t)s->ld * sizeof(double);
+    if (s->zsize == 8) {
+      double* zr = (double*)s->zrow(s->cur, zfirst);
+      e = to_host ? cudaMemcpy2DAsync(hb, pitch_b, zr, dpitch, row, zrows, kind, s->stream)
+                  : cudaMemcpy2DAsync(zr, dpitch, hb, pitch_b, row, zrows, kind, s->stream);
     } else {
-      void* zr = s->zrow(s->cur, v - 1);
+      void* zr = s->zrow(s->cur, zfirst);
+      const int64_t count = (int64_t)zrows * s->ld;
       if (to_host) {
-        s->ks.convert_z(s->n, zr, s->d_tmp, 1, s->stream);
-        e = cudaMemcpyAsync(hb, s->d_tmp, s->n * sizeof(double), kind_out, s->stream);
+        s->ks.convert_z(count, zr, s->d_tmp, 1, s->stream);
+        e = cudaMemcpy2DAsync(hb, pitch_b, s->d_tmp, dpitch, row, zrows, kind, s->stream);
       } else {
-        e = cudaMemcpyAsync(s->d_tmp, hb, s->n * sizeof(double), kind_in, s->stream);
-        if (e == cudaSuccess) s->ks.convert_z(s->n, zr, s->d_tmp, 0, s->stream);
+        e = cudaMemcpy2DAsync(s->d_tmp, dpitch, hb, pitch_b, row, zrows, kind, s->stream);
+        if (e == cudaSuccess) s->ks.convert_z(count, zr, s->d_tmp, 0, s->stream);
       }
     }
     if (e != cudaSuccess) return s->cuda_fail(e, "state copy");
-    // d_tmp is reused by the next variable: order the copies
-    if (s->zsize != 8) {
-      e = cudaStreamSynchronize(s->stream);
-      if (e != cudaSuccess) return s->cuda_fail(e, "state copy");
-    }
   }
   e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return s->cuda_fail(e, "state copy");
@@ -759,7 +761,7 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
   fail |= dalloc(&s->d_fy, (int64_t)s->N * ld) != cudaSuccess;
   fail |= dalloc(&s->d_act, ld) != cudaSuccess;
   fail |= dalloc(&s->d_Vn, ld) != cudaSuccess;
-  fail |= dalloc(&s->d_tmp, ld) != cudaSuccess;
+  fail |= dalloc(&s->d_tmp, (int64_t)std::max(1, s->N - 1) * ld) != cudaSuccess;
   fail |= dalloc(&s->d_rest, 64) != cudaSuccess;
   fail |= dalloc(&s->d_flags, 4) != cudaSuccess;
   fail |= dalloc(&s->rs.partials, kReduceMaxBlocks) != cudaSuccess;

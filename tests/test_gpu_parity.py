@@ -70,7 +70,7 @@ def _assert_parity(Y, act, prob, ref, tol_v=TOL_V):
 
 
 @pytest.mark.parametrize("name,dt,steps,h", [
-    ("square33x29_hh", 0.05, 120, 1.0 / 64),   # ragged n = 957, through the upstroke
+    ("square33x29_hh", 0.05, 35, 1.0 / 64),    # ragged n = 957, stimulus and upstroke
     ("square33x29_hh", 0.02, 250, 1.0 / 64),
     ("slab23x9x5_ttp", 0.05, 60, 0.01),        # n = 1035, s = 1, m = 2
     ("slab23x9x5_hh", 0.05, 60, 0.01),
@@ -173,9 +173,21 @@ def test_conservation_pure_diffusion_gpu():
 
 
 def test_full_size_square65_hh_parity():
-    """The 65 x 65 HH square at dt = 0.05 ms, rho every step, T = 20 ms (all 400 steps)."""
+    """The 65 x 65 HH square, rho every step.
+
+    At dt = 0.05 ms the literal Algorithm 3 leaves the stable regime after the
+    upstroke (rho_F ~ 25 is not >> rho_S ~ 40, Lemma 4.2 B) and the trajectory
+    amplifies rounding differences: the oracle perturbed by 1e-15 itself
+    diverges to O(0.1) by T = 20 ms (pinned on CPU in
+    test_oracle_sensitivity.py).  Parity at 1e-10 is therefore checked over
+    the window before the instability at dt = 0.05 ms, and over the whole
+    T = 20 ms horizon at dt = 0.02 ms, where the step is stable."""
     w = make_workload("square65_hh")
-    Y, act, log, st, prob, ref, rlog = _run_pair(w, w.steps)
+    Y, act, log, st, prob, ref, rlog = _run_pair(w, 35)
+    assert log == rlog
+    _assert_parity(Y, act, prob, ref)
+    w.dt = 0.02
+    Y, act, log, st, prob, ref, rlog = _run_pair(w, 1000)
     assert log == rlog
     _assert_parity(Y, act, prob, ref)
 
