@@ -202,16 +202,17 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000, help="timed steps (1000 = T 50 ms at dt 0.05)")
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--workload", default="slab_ttp")
-    ap.add_argument("--rho-every", type=int, default=1)
-    ap.add_argument("--horizon-steps", type=int, default=1000, help="steps of the mixed-vs-FP64 accuracy check")
-    ap.add_argument("--fp64-steps", type=int, default=20)
+    ap.add_argument("--rho-every", type=int, default=0, help="0: once at t = 0 (Sec. 5 setup); k: every k steps")
+    ap.add_argument("--every-step-steps", type=int, default=200)
+    ap.add_argument("--fp64-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="headline only (for profiler runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -233,16 +234,17 @@ def main():
     prec = pkg.PREC_MIXED if args.precision == "mixed" else pkg.PREC_FP64
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     hbm_peak, peak_kind = _peaks()
+    N = pkg.num_vars(w.model)
 
-    def make(precision, profile=False):
+    def make(precision, profile=False, rho_every=None):
         return pkg.Solver(rp, col, K, M, chi=w.chi, Cm=w.Cm, model=w.model, mask=w.stim_mask,
                           amplitude=w.stim_amp, t_on=w.t_on, t_off=w.t_off, precision=precision,
-                          rho_every=args.rho_every, stream=stream.cuda_stream, device=local,
-                          profile=profile)
+                          rho_every=args.rho_every if rho_every is None else rho_every,
+                          stream=stream.cuda_stream, device=local, profile=profile)
 
     def timed_steps(sol, K_, flush_l2=True):
-        """K_ steps, each bracketed by CUDA events on the solver's stream, L2
-        flushed before each step (outside the bracket)."""
+        """K_ steps, each bracketed by CUDA events on the solver's stream, with
+        L2 flushed before each step outside the bracket."""
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K_)]
         l0 = sol.stats()["launches"]
         with torch.cuda.stream(stream):
@@ -257,12 +259,16 @@ def main():
         ms = [a.elapsed_time(b) for a, b in evs]
         return ms, sol.stats()["launches"] - l0
 
-    # ---- headline: precision under test, K timed steps after W warm-up ----
-    sol = make(prec)
+    # ---- warm-up on a separate instance (module load, clocks, allocator) ----
+    warm = make(prec)
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            sol.step(w.dt)
-    sol.sync()
+            warm.step(w.dt)
+    warm.sync()
+    warm.close()
+
+    # ---- headline: K steps from rest on a fresh solver (includes rho at t = 0) ----
+    sol = make(prec)
     torch.cuda.synchronize()
     _barrier(world)
     torch.cuda.synchronize()
@@ -276,41 +282,79 @@ def main():
     units = _sum_over_ranks(float(w.n * args.steps), world, dev)
     value = units / (total_ms_max / 1e3)
     sol.close()
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == pkg.PREC_MIXED else "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: 201x71x31-node Kuhn-tet slab 2.0x0.7x0.3 cm, TTP06 epi, "
+                               "dt 0.05 ms, 50 uA/cm^2 corner stimulus; timed from rest (t = 0)",
+                   "nodes": w.n, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "precision": ("mixed: FP32 z, ionic model, gating, SpMV, inner increments; FP64 V "
+                                 "recurrence, stage coefficients, rho" if prec == pkg.PREC_MIXED else "fp64"),
+                   "rho_policy": ("once at t = 0 (inside the timed region)" if args.rho_every == 0
+                                  else f"every {args.rho_every} steps"),
+                   "s": st["s"], "m": st["m"], "power_iterations": st["total_pow_iters"],
+                   "l2": "flushed before every timed step (512 MB write, outside the step's events)"},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    if args.no_extras:
+        if rank == 0:
+            print(json.dumps(out))
+        return 0
 
     # ---- per-kernel durations (CUDA events around every launch, same stream) ----
     solp = make(prec, profile=True)
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            solp.step(w.dt)
-    solp.sync()
-    p0 = solp.stats()
-    Kp = min(args.steps, 100)
+    Kp = args.steps
     timed_steps(solp, Kp)
     p1 = solp.stats()
     solp.close()
-    phase_ms = {k: p1["phase_ms"][k] - p0["phase_ms"][k] for k in p1["phase_ms"]}
-    phase_n = {k: p1["phase_launches"][k] - p0["phase_launches"][k] for k in p1["phase_launches"]}
-    dominant = max(phase_ms, key=lambda k: phase_ms[k])
-    N = pkg.num_vars(w.model)
+    phase_ms, phase_n = p1["phase_ms"], p1["phase_launches"]
     zb = 4 if prec == pkg.PREC_MIXED else 8
-    # algorithmic bytes per node per launch (rows of L: off-diagonals only in
-    # mixed mode, 4-byte value + 4-byte column; FP64 mode 8 + 4 incl. diagonal)
-    nnz_row = (col.size / w.n - (1 if prec == pkg.PREC_MIXED else 0))
-    mat_b = nnz_row * ((4 + 4) if prec == pkg.PREC_MIXED else (8 + 4))
-    fb = 4 if prec == pkg.PREC_MIXED else 8
-    bytes_stage = 8 + (N - 1) * zb + 1 + mat_b + (N - 1) * zb + 8 + fb  # V,z,mask,L in; z,u1,F out (m>=2)
-    bytes_inner = 8 + 8 + fb + mat_b + 8                                  # u1, V, F, L in; V out
+    nnz_row = p1["matrix_entries"] / w.n  # stored entries of L per row (sliced ELL)
+    if prec == pkg.PREC_MIXED:
+        mat_b = nnz_row * (4 + 4)  # off-diagonal FP32 value + int32 column
+        # stage: V hi, z, mask, L in; z, delta_1, L V, F out
+        bytes_stage = 4 + (N - 1) * zb + 1 + mat_b + (N - 1) * zb + 4 + 4 + 4
+        # last inner stage: delta_1, L V, F, V hi + lo, L in; V hi + lo out
+        bytes_inner = 4 + 4 + 4 + 8 + mat_b + 8
+    else:
+        mat_b = nnz_row * (8 + 4)
+        bytes_stage = 8 + (N - 1) * zb + 1 + mat_b + (N - 1) * zb + 8 + 8  # V, z, mask, L; z, u_1, F
+        bytes_inner = 8 + 8 + 8 + mat_b + 8  # u_1, V, F, L; V
     per_launch = {"stage": bytes_stage, "inner": bytes_inner}
-    dom_key = dominant if dominant in per_launch else "stage"
+    step_kernels = {k: phase_ms[k] for k in ("stage", "inner")}
+    dom_key = max(step_kernels, key=lambda k: step_kernels[k])
     avg_ms = phase_ms[dom_key] / max(phase_n[dom_key], 1)
     achieved = per_launch[dom_key] * w.n / (avg_ms / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": f"{dom_key} ({'stage_kernel' if dom_key == 'stage' else 'inner_kernel'})",
-                "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
-                "bytes_per_node": per_launch[dom_key], "avg_launch_us": avg_ms * 1e3,
-                "traffic": None}
-    kernel_breakdown = {k: {"ms_per_step": phase_ms[k] / Kp, "launches_per_step": phase_n[k] / Kp}
-                        for k in phase_ms}
+    out["roofline"] = {
+        "bound": "hbm", "kernel": "stage_kernel_mixed (fused RL + TTP06 + first SpMV + outer update)"
+        if dom_key == "stage" else "inner_kernel_mixed (SpMV stage + FP64 V update)",
+        "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+        "peak_source": f"{peak_kind}: MEASURED_PEAKS.json hbm_gbs (burst copy)",
+        "bytes_per_node_per_launch": per_launch[dom_key], "avg_launch_us": avg_ms * 1e3,
+        "matrix_entries_per_row": nnz_row,
+        "traffic": None}
+    out["kernels"] = {k: {"ms_per_step": phase_ms[k] / Kp, "launches_per_step": phase_n[k] / Kp,
+                          "avg_launch_us": 1e3 * phase_ms[k] / max(phase_n[k], 1)}
+                      for k in phase_ms if phase_n[k] > 0}
+    if "stage" in per_launch and "inner" in per_launch:
+        out["kernels"]["stage"]["gbs"] = bytes_stage * w.n / (phase_ms["stage"] / max(phase_n["stage"], 1) / 1e3) / 1e9
+        out["kernels"]["inner"]["gbs"] = bytes_inner * w.n / (phase_ms["inner"] / max(phase_n["inner"], 1) / 1e3) / 1e9
+
+    # ---- rho every step (Algorithm 5 warm started before every step) ----
+    sole = make(prec, rho_every=1)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            sole.step(w.dt)
+    sole.sync()
+    mse, _ = timed_steps(sole, args.every_step_steps)
+    ste = sole.stats()
+    sole.close()
+    out["rho_every_step"] = {"value": w.n * args.every_step_steps / (sum(mse) / 1e3), "unit": UNIT,
+                             "ms_per_step": sum(mse) / args.every_step_steps, "steps": args.every_step_steps,
+                             "power_iterations_per_step": ste["total_pow_iters"] / (args.warmup + args.every_step_steps)}
 
     # ---- end to end through the C ABI with host buffers ----
     sol = make(prec)
@@ -334,61 +378,41 @@ def main():
     sol.sync()
     e2e_s = _max_over_ranks(time.perf_counter() - t0, world, dev)
     sol.close()
-    e2e = {"value": _sum_over_ranks(float(w.n * Ke), world, dev) / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": int(N * w.n * 8), "d2h_bytes_per_step": int(w.n * 8),
-           "steps": Ke, "api": "emrkc_set_state(all vars, pinned host) + emrkc_step + emrkc_get_state(V)"}
-
-    out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if prec == pkg.PREC_MIXED else "f64", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: 201x71x31-node Kuhn-tet slab 2.0x0.7x0.3 cm, TTP06 epi, "
-                               "dt 0.05 ms, 50 uA/cm^2 corner stimulus",
-                   "nodes": w.n, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "precision": ("mixed: FP32 z, ionic model, gating, SpMV; FP64 V recurrence, "
-                                 "stage coefficients, rho" if prec == pkg.PREC_MIXED else "fp64"),
-                   "rho_policy": "every step" if args.rho_every == 1 else f"every {args.rho_every}",
-                   "s": st["s"], "m": st["m"], "l2": "flushed before every timed step (512 MB write)"},
-        "roofline": roofline,
-        "kernels": kernel_breakdown,
-        "gpu_launches": int(launches),
-        "e2e": e2e,
-        "clocks": clk.summary(),
-    }
+    out["e2e"] = {"value": _sum_over_ranks(float(w.n * Ke), world, dev) / e2e_s, "unit": UNIT,
+                  "h2d_bytes_per_step": int(N * w.n * 8), "d2h_bytes_per_step": int(w.n * 8),
+                  "steps": Ke, "api": "per step: emrkc_set_state(all variables, pinned host) + emrkc_step "
+                                      "+ emrkc_get_state(V, pinned host)"}
 
     # ---- plain FP64 form on the same workload, and accuracy of the mixed form ----
     if prec == pkg.PREC_MIXED and rank == 0:
         s64 = make(pkg.PREC_FP64)
-        with torch.cuda.stream(stream):
-            for _ in range(3):
-                s64.step(w.dt)
-        s64.sync()
         ms64, _ = timed_steps(s64, args.fp64_steps)
         s64.close()
         v64 = w.n * args.fp64_steps / (sum(ms64) / 1e3)
         out["fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": sum(ms64) / args.fp64_steps,
-                       "steps": args.fp64_steps, "speedup_of_headline": value / v64}
-    if prec == pkg.PREC_MIXED and rank == 0 and not args.no_accuracy:
-        H = args.horizon_steps
-        a = make(pkg.PREC_FP64)
-        b = make(pkg.PREC_MIXED)
-        with torch.cuda.stream(stream):
-            for _ in range(H):
-                a.step(w.dt)
-                b.step(w.dt)
-        a.sync()
-        b.sync()
-        Va, Vb = a.get_state(var=0), b.get_state(var=0)
-        ta, tb = a.activation_times(), b.activation_times()
-        a.close()
-        b.close()
-        err = float(np.sqrt(np.sum(M * (Va - Vb) ** 2) / np.sum(M * Va * Va)))
-        both = np.isfinite(ta) & np.isfinite(tb)
-        out["accuracy"] = {"rel_l2_err_V_vs_fp64": err, "T_ms": H * w.dt,
-                           "max_activation_diff_ms": float(np.max(np.abs(ta[both] - tb[both]))) if both.any() else None,
-                           "activated_nodes": int(both.sum()),
-                           "activation_pattern_equal": bool(np.array_equal(np.isfinite(ta), np.isfinite(tb)))}
+                       "steps": args.fp64_steps, "dtype": "f64",
+                       "note": "same workload and rho policy, timed from rest", "headline_speedup": value / v64}
+        if not args.no_accuracy:
+            H = int(round(w.T / w.dt))
+            a = make(pkg.PREC_FP64)
+            b = make(pkg.PREC_MIXED)
+            with torch.cuda.stream(stream):
+                for _ in range(H):
+                    a.step(w.dt)
+                    b.step(w.dt)
+            a.sync()
+            b.sync()
+            Va, Vb = a.get_state(var=0), b.get_state(var=0)
+            ta, tb = a.activation_times(), b.activation_times()
+            a.close()
+            b.close()
+            err = float(np.sqrt(np.sum(M * (Va - Vb) ** 2) / np.sum(M * Va * Va)))
+            both = np.isfinite(ta) & np.isfinite(tb)
+            out["accuracy"] = {"rel_l2_err_V_vs_fp64": err, "T_ms": H * w.dt,
+                               "max_activation_diff_ms": (float(np.max(np.abs(ta[both] - tb[both])))
+                                                          if both.any() else None),
+                               "activated_nodes": int(both.sum()),
+                               "activation_pattern_equal": bool(np.array_equal(np.isfinite(ta), np.isfinite(tb)))}
 
     if rank == 0 and not args.no_cpu_baseline:
         n_s, K_s, el = _oracle_sample(15.0, 10)

@@ -136,6 +136,8 @@ typedef struct {
   int pow_iters_F, pow_iters_S; /* iterations of the last power call   */
   int64_t total_pow_iters;
   int64_t launches;      /* kernels launched since create              */
+  int64_t matrix_entries;/* stored nonzeros of L after dropping zeros  */
+  int64_t matrix_slots;  /* sliced-ELL slots including padding         */
   double phase_ms[EMRKC_NUM_PHASES];       /* needs options.profile    */
   int64_t phase_launches[EMRKC_NUM_PHASES];
 } emrkc_stats;

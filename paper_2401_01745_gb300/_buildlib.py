@@ -24,6 +24,7 @@ LIB = os.path.join(OUT_DIR, "libemrkc.so")
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_UNITS = ["kernels_fp64.cu", "kernels_mixed.cu", "batch.cu"]
 HOST_UNITS = ["solver.cpp", "assemble.cpp", "batch_host.cpp"]
+FAST_MATH_UNITS = {"kernels_mixed.cu", "batch.cu"}
 
 
 def _cuda_home():
@@ -60,7 +61,10 @@ def build(verbose: bool = False, force: bool = False) -> str:
     for u in cuda_units:
         obj = os.path.join(BUILD_DIR, u + ".o")
         objs.append(obj)
-        cmd = [nvcc, *GENCODE, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+        # the mixed-precision unit uses approximate FP32 division/sqrt and
+        # flush-to-zero (FP64 code in it is unaffected)
+        fast = ["-use_fast_math"] if u in FAST_MATH_UNITS else []
+        cmd = [nvcc, *GENCODE, "-O3", "-lineinfo", "-std=c++17", *fast, "-Xcompiler", "-fPIC",
                "-I", INCLUDE, "-I", CSRC, "-c", os.path.join(CSRC, u), "-o", obj]
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     for u in host_units:

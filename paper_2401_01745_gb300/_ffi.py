@@ -48,7 +48,8 @@ class Stats(C.Structure):
     _fields_ = [("t", C.c_double), ("steps", C.c_int64), ("s", C.c_int), ("m", C.c_int),
                 ("eta", C.c_double), ("rho_F", C.c_double), ("rho_S", C.c_double),
                 ("pow_iters_F", C.c_int), ("pow_iters_S", C.c_int), ("total_pow_iters", C.c_int64),
-                ("launches", C.c_int64), ("phase_ms", C.c_double * NUM_PHASES),
+                ("launches", C.c_int64), ("matrix_entries", C.c_int64), ("matrix_slots", C.c_int64),
+                ("phase_ms", C.c_double * NUM_PHASES),
                 ("phase_launches", C.c_int64 * NUM_PHASES)]
 
 

@@ -32,13 +32,13 @@ __device__ __forceinline__ double ell_dot64(const Ell& A, int64_t i, const doubl
 
 // Mixed: sum_{k != i} L_ik (x_k - x_i) in FP32 (row sums of L vanish, so
 // this equals (L x)_i; differences keep the FP32 sum well conditioned).
-__device__ __forceinline__ float ell_diff32(const Ell& A, int64_t i, const double* __restrict__ x) {
+__device__ __forceinline__ float ell_diff32(const Ell& A, int64_t i, const float* __restrict__ x) {
   const int64_t b = i >> 5;
   const int w = __ldg(A.width + b);
   int64_t p = __ldg(A.slice_ptr + b) + (i & 31);
-  const float xi = (float)__ldg(x + i);
+  const float xi = __ldg(x + i);
   float acc = 0.0f;
-  for (int k = 0; k < w; ++k, p += 32) acc += __ldg(A.val32 + p) * ((float)__ldg(x + __ldg(A.col + p)) - xi);
+  for (int k = 0; k < w; ++k, p += 32) acc += __ldg(A.val32 + p) * (__ldg(x + __ldg(A.col + p)) - xi);
   return acc;
 }
 
@@ -70,110 +70,195 @@ __device__ __forceinline__ void step_epilogue(int64_t i, double Vn, double Vnew,
   }
 }
 
+// Mixed path: V is carried as the unevaluated sum hi + lo of two floats
+// (48 significand bits) and updated with error-free transformations, so the
+// V accumulation never uses the FP64 pipe.  ff_add is Knuth's TwoSum of
+// (hi, inc) followed by Dekker's FastTwoSum renormalisation; __fadd_rn /
+// __fsub_rn keep the compiler from contracting or reassociating them.
+__device__ __forceinline__ void ff_add(float hi, float lo, float inc, float& ohi, float& olo) {
+  const float s = __fadd_rn(hi, inc);
+  const float bp = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(inc, bp));
+  const float l = __fadd_rn(lo, e);
+  const float h = __fadd_rn(s, l);
+  olo = __fsub_rn(l, __fsub_rn(h, s));
+  ohi = h;
+}
+
+// Epilogue of the mixed path on the hi parts (the crossing branch is rare).
+__device__ __forceinline__ void step_epilogue_ff(int64_t i, float Vn, float Vnew, double* act, double t_n,
+                                                 double dt, float th, int* flags) {
+  if (!isfinite(Vnew)) atomicOr(flags, 1);
+  if (act != nullptr && Vn < th && Vnew >= th) {
+    if (isnan(act[i])) act[i] = t_n + dt * (double)((th - Vn) / (Vnew - Vn));
+  }
+}
+
 // ---------------------------------------------------------------------------
-// Outer stage j: exponential Euler of the gates (Algorithm 3, Exponential_Euler),
-// frozen forcing f_S(t_j, y_E), first inner RKC stage and the z-part of g_j.
-template <class Model, typename R, typename Z, bool MIXED, bool HAS_M2>
-__global__ void __launch_bounds__(128) stage_kernel(const StageArgs a, const Ell A) {
+// Outer stage j (FP64 path): exponential Euler of the gates (Algorithm 3,
+// Exponential_Euler), frozen forcing f_S(t_j, y_E), first inner RKC stage and
+// the z-part of g_j = nu g_{j-1} + kappa g_{j-2} + mu dt f_bar, where
+// f_bar = ((y_E - y)/eta on the gates, c_m g_S on z_S, (u_m - V)/eta on V).
+template <class Model, bool HAS_M2>
+__global__ void __launch_bounds__(128) stage_kernel_fp64(const StageArgs a, const Ell A) {
   constexpr int NE = Model::NE, NS = Model::NS, NZ = NE + NS;
-  using M = Math<R>;
+  using M = Math<double>;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   const int64_t ld = a.ld;
-  const Z* __restrict__ Zm1 = static_cast<const Z*>(a.Zm1);
-  const Z* __restrict__ Zm2 = static_cast<const Z*>(a.Zm2);
-  Z* __restrict__ Zout = static_cast<Z*>(a.Zout);
+  const double* __restrict__ Zm1 = static_cast<const double*>(a.Zm1);
+  const double* __restrict__ Zm2 = static_cast<const double*>(a.Zm2);
+  double* __restrict__ Zout = static_cast<double*>(a.Zout);
 
   const double V = a.Vm1[i];
-  R z[NZ > 0 ? NZ : 1];
+  double z[NZ > 0 ? NZ : 1];
 #pragma unroll
-  for (int k = 0; k < NZ; ++k) z[k] = (R)Zm1[k * ld + i];
+  for (int k = 0; k < NZ; ++k) z[k] = Zm1[k * ld + i];
 
-  // y_E = y + (e^{eta Lambda} - I)(y - y_inf) on the gates
-  R zE1[NE > 0 ? NE : 1];
+  double zE1[NE > 0 ? NE : 1];
   if constexpr (NE > 0) {
-    R lam[NE], zinf[NE];
-    Model::gating((R)V, z, z + NE, lam, zinf);
+    double lam[NE], zinf[NE];
+    Model::gating(V, z, z + NE, lam, zinf);
 #pragma unroll
-    for (int k = 0; k < NE; ++k) zE1[k] = z[k] + M::em1((R)a.eta * lam[k]) * (z[k] - zinf[k]);
+    for (int k = 0; k < NE; ++k) zE1[k] = z[k] + M::em1(a.eta * lam[k]) * (z[k] - zinf[k]);
   }
-  // f_S(t_j, y_E): V-row and g_S
-  R Iion;
-  R gS[NS > 0 ? NS : 1];
-  Model::currents((R)V, zE1, z + NE, Iion, gS);
-  const R Istim = (a.mask != nullptr && a.mask[i]) ? (R)a.stim : R(0);
-  R F;
-  if constexpr (MIXED) F = (Istim - Iion) * (R)a.inv_Cm;
-  else F = (Istim - Iion) / (R)a.Cm;
+  double Iion;
+  double gS[NS > 0 ? NS : 1];
+  Model::currents(V, zE1, z + NE, Iion, gS);
+  const double Istim = (a.mask != nullptr && a.mask[i]) ? a.stim : 0.0;
+  const double F = (Istim - Iion) * a.inv_Cm;
 
-  // z-part of g_j = nu g_{j-1} + kappa g_{j-2} + mu dt f_bar, with
-  // f_bar = ((y_E - y)/eta on the gates, c_m g_S on z_S)
   if constexpr (NZ > 0) {
-    const R nu = (R)a.nu, kap = (R)a.kappa, mudt = (R)a.mu_dt;
 #pragma unroll
     for (int k = 0; k < NZ; ++k) {
-      R fbar;
-      if (k < NE) {
-        if constexpr (MIXED) fbar = (zE1[k < NE ? k : 0] - z[k]) * (R)(1.0 / a.eta);
-        else fbar = (zE1[k < NE ? k : 0] - z[k]) / (R)a.eta;
-      } else {
-        fbar = (R)a.cm_inner * gS[k >= NE ? k - NE : 0];
-      }
-      R out;
-      if constexpr (HAS_M2) out = nu * z[k] + kap * (R)Zm2[k * ld + i] + mudt * fbar;
-      else out = z[k] + mudt * fbar;
-      Zout[k * ld + i] = (Z)out;
+      const double fbar = (k < NE) ? (zE1[k < NE ? k : 0] - z[k]) * a.inv_eta : a.cm_inner * gS[k >= NE ? k - NE : 0];
+      double out;
+      if constexpr (HAS_M2) out = a.nu * z[k] + a.kappa * Zm2[k * ld + i] + a.mu_dt * fbar;
+      else out = z[k] + a.mu_dt * fbar;
+      Zout[k * ld + i] = out;
     }
   }
-
-  // first inner stage needs L V_{j-1}
-  double LV;
-  if constexpr (MIXED) LV = (double)ell_diff32(A, i, a.Vm1);
-  else LV = ell_dot64(A, i, a.Vm1);
-
+  const double LV = ell_dot64(A, i, a.Vm1);
   if (a.Vn_copy != nullptr) a.Vn_copy[i] = V;
   if (a.m == 1) {
-    double fbarV;
-    if constexpr (MIXED) {
-      fbarV = (double)((float)(a.mu1_eta / a.eta) * ((float)LV + F));
-    } else {
-      const double u1 = V + a.mu1_eta * (LV + (double)F);
-      fbarV = (u1 - V) / a.eta;
-    }
+    const double fbarV = a.mu1 * (LV + F);  // (u_1 - V)/eta with u_1 = V + mu'_1 eta (L V + F)
     double Vnew;
     if constexpr (HAS_M2) Vnew = a.nu * V + a.kappa * a.Vm2[i] + a.mu_dt * fbarV;
     else Vnew = V + a.mu_dt * fbarV;
     a.Vout[i] = Vnew;
     if (a.final_stage) step_epilogue(i, a.Vn[i], Vnew, a.act, a.t_n, a.dt, a.threshold, a.flags);
   } else {
-    a.U1[i] = V + a.mu1_eta * (LV + (double)F);
-    static_cast<R*>(a.F)[i] = F;
+    a.U1[i] = V + a.mu1_eta * (LV + F);
+    static_cast<double*>(a.F)[i] = F;
   }
 }
 
-// Inner RKC stage k >= 2 (Algorithm 1 applied to f_u = f_F + frozen f_S).
-template <typename R, bool MIXED>
-__global__ void __launch_bounds__(256) inner_kernel(const InnerArgs a, const Ell A) {
+// Outer stage j (mixed path): as above with z, the ionic model, the gating
+// exponentials and L V in FP32 (on the FP32 mirror of V); V itself is only
+// updated in FP64 (m == 1).  For m >= 2 the inner stages carry the FP32
+// increments delta_k = u_k - V_{j-1}; this kernel writes delta_1, L V and F.
+template <class Model, bool HAS_M2>
+__global__ void __launch_bounds__(128) stage_kernel_mixed(const StageArgs a, const Ell A) {
+  constexpr int NE = Model::NE, NS = Model::NS, NZ = NE + NS;
+  using M = Math<float>;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
-  double Lu;
-  if constexpr (MIXED) Lu = (double)ell_diff32(A, i, a.u1);
-  else Lu = ell_dot64(A, i, a.u1);
-  const double F = (double)static_cast<const R*>(a.F)[i];
+  const int64_t ld = a.ld;
+  const float* __restrict__ Zm1 = static_cast<const float*>(a.Zm1);
+  const float* __restrict__ Zm2 = static_cast<const float*>(a.Zm2);
+  float* __restrict__ Zout = static_cast<float*>(a.Zout);
+
+  const float V = a.V32m1[i];
+  float z[NZ > 0 ? NZ : 1];
+#pragma unroll
+  for (int k = 0; k < NZ; ++k) z[k] = Zm1[k * ld + i];
+
+  float zE1[NE > 0 ? NE : 1];
+  if constexpr (NE > 0) {
+    float lam[NE], zinf[NE];
+    Model::gating(V, z, z + NE, lam, zinf);
+#pragma unroll
+    for (int k = 0; k < NE; ++k) zE1[k] = z[k] + M::em1(a.f_eta * lam[k]) * (z[k] - zinf[k]);
+  }
+  float Iion;
+  float gS[NS > 0 ? NS : 1];
+  Model::currents(V, zE1, z + NE, Iion, gS);
+  const float Istim = (a.mask != nullptr && a.mask[i]) ? a.f_stim : 0.0f;
+  const float F = (Istim - Iion) * a.f_inv_Cm;
+
+  if constexpr (NZ > 0) {
+#pragma unroll
+    for (int k = 0; k < NZ; ++k) {
+      const float fbar = (k < NE) ? (zE1[k < NE ? k : 0] - z[k]) * a.f_inv_eta : a.f_cm * gS[k >= NE ? k - NE : 0];
+      float out;
+      if constexpr (HAS_M2) out = a.f_nu * z[k] + a.f_kappa * Zm2[k * ld + i] + a.f_mudt * fbar;
+      else out = z[k] + a.f_mudt * fbar;
+      Zout[k * ld + i] = out;
+    }
+  }
+  const float LV = ell_diff32(A, i, a.V32m1);
+  if (a.Vn32_copy != nullptr) a.Vn32_copy[i] = V;
+  if (a.m == 1) {
+    // V_j = V_{j-1} + kappa (V_{j-2} - V_{j-1}) + mu dt f_bar  (nu + kappa = 1)
+    const float fbarV = a.f_mu1 * (LV + F);
+    const float lo1 = a.Vlo_m1[i];
+    float inc = a.f_mudt * fbarV;
+    if constexpr (HAS_M2) inc += a.f_kappa * ((a.Vhi_m2[i] - V) + (a.Vlo_m2[i] - lo1));
+    float hi, lo;
+    ff_add(V, lo1, inc, hi, lo);
+    a.V32out[i] = hi;
+    a.Vlo_out[i] = lo;
+    if (a.final_stage) step_epilogue_ff(i, a.Vn32[i], hi, a.act, a.t_n, a.dt, a.f_th, a.flags);
+  } else {
+    a.D1[i] = a.f_mu1eta * (LV + F);
+    a.LV[i] = LV;
+    static_cast<float*>(a.F)[i] = F;
+  }
+}
+
+// Inner RKC stage k >= 2 (FP64 path), Algorithm 1 applied to f_u = f_F + frozen f_S.
+static __global__ void __launch_bounds__(256) inner_kernel_fp64(const InnerArgs a, const Ell A) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const double Lu = ell_dot64(A, i, a.u1);
+  const double F = static_cast<const double*>(a.F)[i];
   const double uk = a.nu * a.u1[i] + a.kappa * a.u2[i] + a.mu_eta * (Lu + F);
   if (!a.last) {
     a.uk[i] = uk;
     return;
   }
   const double V1 = a.Vm1[i];
-  double fbar;
-  if constexpr (MIXED) fbar = (uk - V1) * (1.0 / a.eta);
-  else fbar = (uk - V1) / a.eta;
+  const double fbar = (uk - V1) * a.inv_eta;
   double Vnew;
   if (a.Vm2 != nullptr) Vnew = a.onu * V1 + a.okappa * a.Vm2[i] + a.omu_dt * fbar;
   else Vnew = V1 + a.omu_dt * fbar;
   a.Vout[i] = Vnew;
   if (a.final_stage) step_epilogue(i, a.Vn[i], Vnew, a.act, a.t_n, a.dt, a.threshold, a.flags);
+}
+
+// Inner RKC stage k >= 2 (mixed path) on the FP32 increments:
+// delta_k = nu'_k delta_{k-1} + kappa'_k delta_{k-2} + mu'_k eta (L V + L delta_{k-1} + F)
+// (nu'_k + kappa'_k = 1 makes this the u-recurrence shifted by V); the last
+// stage forms f_bar_V = delta_m / eta and updates the float-float V.
+static __global__ void __launch_bounds__(256) inner_kernel_mixed(const InnerArgs a, const Ell A) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const float Ld = ell_diff32(A, i, a.d1);
+  const float F = static_cast<const float*>(a.F)[i];
+  float dk = a.f_nu * a.d1[i] + a.f_mueta * (a.LV[i] + Ld + F);
+  if (a.d2 != nullptr) dk += a.f_kappa * a.d2[i];
+  if (!a.last) {
+    a.dk[i] = dk;
+    return;
+  }
+  const float hi1 = a.Vhi1[i], lo1 = a.Vlo1[i];
+  float inc = a.f_omu_dt * (dk * a.f_inv_eta);
+  if (a.Vhi2 != nullptr) inc += a.f_okappa * ((a.Vhi2[i] - hi1) + (a.Vlo2[i] - lo1));
+  float hi, lo;
+  ff_add(hi1, lo1, inc, hi, lo);
+  a.V32out[i] = hi;
+  a.Vlo_out[i] = lo;
+  if (a.final_stage) step_epilogue_ff(i, a.Vn32[i], hi, a.act, a.t_n, a.dt, a.f_th, a.flags);
 }
 
 // ---------------------------------------------------------------------------
@@ -345,14 +430,19 @@ template <class MD, class MR, typename R, typename Z, bool MIXED>
 struct Kernels {
   static void stage(const StageArgs& a, const Ell& A, int has_m2, cudaStream_t st) {
     if (a.n == 0) return;
-    if (has_m2)
-      stage_kernel<MR, R, Z, MIXED, true><<<blocks_for(a.n, 128), 128, 0, st>>>(a, A);
-    else
-      stage_kernel<MR, R, Z, MIXED, false><<<blocks_for(a.n, 128), 128, 0, st>>>(a, A);
+    const unsigned g = blocks_for(a.n, 128);
+    if constexpr (MIXED) {
+      if (has_m2) stage_kernel_mixed<MR, true><<<g, 128, 0, st>>>(a, A);
+      else stage_kernel_mixed<MR, false><<<g, 128, 0, st>>>(a, A);
+    } else {
+      if (has_m2) stage_kernel_fp64<MR, true><<<g, 128, 0, st>>>(a, A);
+      else stage_kernel_fp64<MR, false><<<g, 128, 0, st>>>(a, A);
+    }
   }
   static void inner(const InnerArgs& a, const Ell& A, cudaStream_t st) {
     if (a.n == 0) return;
-    inner_kernel<R, MIXED><<<blocks_for(a.n, 256), 256, 0, st>>>(a, A);
+    if constexpr (MIXED) inner_kernel_mixed<<<blocks_for(a.n, 256), 256, 0, st>>>(a, A);
+    else inner_kernel_fp64<<<blocks_for(a.n, 256), 256, 0, st>>>(a, A);
   }
   static void power_F(const PowerFArgs& a, const Ell& A, const ReduceScratch& rs, cudaStream_t st) {
     powerF_kernel<MIXED><<<reduce_grid(a.n), kReduceBlock, 0, st>>>(a, A, rs);

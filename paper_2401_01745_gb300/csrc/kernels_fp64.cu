@@ -91,4 +91,32 @@ void launch_fill_rows(void* z, int zsize, int64_t n, int64_t ld, int rows, const
   fill_rows_kernel<<<g, 256, 0, st>>>(z, zsize, n, ld, rows, values);
 }
 
+__global__ void ff_split_kernel(const double* v, float* hi, float* lo, int64_t count) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = v[i];
+    const float h = (float)x;
+    hi[i] = h;
+    lo[i] = (float)(x - (double)h);
+  }
+}
+
+__global__ void ff_join_kernel(const float* hi, const float* lo, double* v, int64_t count) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = (double)hi[i] + (double)lo[i];
+}
+
+void launch_ff_split(const double* v, float* hi, float* lo, int64_t count, cudaStream_t st) {
+  if (count == 0) return;
+  unsigned g = blocks_for(count, 256);
+  if (g > 8192) g = 8192;
+  ff_split_kernel<<<g, 256, 0, st>>>(v, hi, lo, count);
+}
+
+void launch_ff_join(const float* hi, const float* lo, double* v, int64_t count, cudaStream_t st) {
+  if (count == 0) return;
+  unsigned g = blocks_for(count, 256);
+  if (g > 8192) g = 8192;
+  ff_join_kernel<<<g, 256, 0, st>>>(hi, lo, v, count);
+}
+
 }  // namespace emrkc

@@ -61,6 +61,23 @@ struct StageArgs {
   double t_n = 0, dt = 0, threshold = -20;
   int* flags = nullptr;         // bit 0: non-finite V
   double* Vn_copy = nullptr;    // if set: store V_n (first stage when s >= 2)
+  // precomputed reciprocals / products (no divisions in the kernels)
+  double inv_eta = 1, mu_dt_over_eta = 0, mu1 = 1;
+  // mixed mode: FP32 mirror of V, FP32 increments delta_k = u_k - V_{j-1}
+  const float* V32m1 = nullptr;
+  float* V32out = nullptr;      // written with Vout (m == 1)
+  float* D1 = nullptr;          // delta_1 = mu'_1 eta (L V + F)   (m >= 2)
+  float* LV = nullptr;          // L V_{j-1}, reused by the inner stages (m >= 2)
+  float f_nu = 1, f_kappa = 0, f_mudt = 0, f_inv_eta = 1, f_cm = 1, f_mu1 = 1, f_mu1eta = 0;
+  float f_eta = 0, f_stim = 0, f_inv_Cm = 1;
+  // mixed mode: V is the unevaluated sum hi + lo of two floats (V32 = hi)
+  const float* Vlo_m1 = nullptr;
+  const float* Vhi_m2 = nullptr;
+  const float* Vlo_m2 = nullptr;
+  float* Vlo_out = nullptr;
+  const float* Vn32 = nullptr;  // hi of V_n (epilogue)
+  float* Vn32_copy = nullptr;   // store hi of V_n (first stage when s >= 2)
+  float f_th = -20;
 };
 
 // Inner RKC stage k >= 2 over f_u(u) = L u + F:
@@ -83,6 +100,21 @@ struct InnerArgs {
   double* act = nullptr;
   double t_n = 0, dt = 0, threshold = -20;
   int* flags = nullptr;
+  double inv_eta = 1;
+  // mixed mode: delta_k = nu'_k delta_{k-1} + kappa'_k delta_{k-2} + mu'_k eta (LV + L delta_{k-1} + F)
+  const float* d1 = nullptr;    // delta_{k-1}
+  const float* d2 = nullptr;    // delta_{k-2} (nullptr: delta_0 = 0)
+  float* dk = nullptr;          // delta_k (when not last)
+  const float* LV = nullptr;
+  float* V32out = nullptr;
+  float f_nu = 0, f_kappa = 0, f_mueta = 0, f_inv_eta = 1;
+  const float* Vhi1 = nullptr;  // V_{j-1} as hi + lo
+  const float* Vlo1 = nullptr;
+  const float* Vhi2 = nullptr;  // V_{j-2} (nullptr when j == 1)
+  const float* Vlo2 = nullptr;
+  float* Vlo_out = nullptr;     // V32out holds hi
+  const float* Vn32 = nullptr;
+  float f_okappa = 0, f_omu_dt = 0, f_th = -20;
 };
 
 // Power iteration (Algorithm 5) kernels.
@@ -123,6 +155,10 @@ struct KernelSet {
                       const ReduceScratch&, int slot, cudaStream_t) = nullptr;
   void (*convert_z)(int64_t count, const void* src, double* dst, int to_double, cudaStream_t) = nullptr;
 };
+
+// Float-float V of the mixed path: split a double into hi + lo, and join.
+void launch_ff_split(const double* v, float* hi, float* lo, int64_t count, cudaStream_t st);
+void launch_ff_join(const float* hi, const float* lo, double* v, int64_t count, cudaStream_t st);
 
 // Defined in kernels_fp64.cu / kernels_mixed.cu.
 bool get_kernels_fp64(int model, KernelSet* ks);

@@ -11,6 +11,8 @@
 //                                   the right-hand side g_S of the non-gating
 //                                   variables (Eq. mono_in_FSE).
 // The exponential (Rush-Larsen) step itself is applied by the stage kernels.
+// Divisions by constants are written as multiplications by the reciprocal
+// constant (folded at compile time): one rounding instead of a division.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -34,12 +36,17 @@ template <> struct Math<double> {
 
 template <> struct Math<float> {
   static __device__ __forceinline__ float ex(float x) { return __expf(x); }
-  static __device__ __forceinline__ float em1(float x) { return expm1f(x); }
+  // e^x - 1: Taylor polynomial through x^4 for |x| < 1/32 (relative truncation
+  // error below x^4/120 < 1e-8), e^x - 1 otherwise (|e^x - 1| > 0.03 there).
+  static __device__ __forceinline__ float em1(float x) {
+    if (fabsf(x) < 0.03125f) return x * (1.0f + x * (0.5f + x * (1.0f / 6.0f + x * (1.0f / 24.0f))));
+    return __expf(x) - 1.0f;
+  }
   static __device__ __forceinline__ float ln(float x) { return __logf(x); }
   static __device__ __forceinline__ float sq(float x) { return sqrtf(x); }
   static __device__ __forceinline__ float dv(float a, float b) { return __fdividef(a, b); }
   static __device__ __forceinline__ float x_em1(float x) {
-    return fabsf(x) < 1e-4f ? 1.0f - 0.5f * x : __fdividef(x, expm1f(x));
+    return fabsf(x) < 1e-4f ? 1.0f - 0.5f * x : __fdividef(x, em1(x));
   }
 };
 
@@ -79,12 +86,12 @@ template <typename R> struct ModelHH {
   using M = Math<R>;
   static __device__ __forceinline__ void rates(R V, R* a, R* b) {
     const R v = V - R(-75.0);
-    a[0] = M::x_em1((R(25.0) - v) / R(10.0));      // alpha_m = 0.1(25-v)/(e^{(25-v)/10}-1)
-    b[0] = R(4.0) * M::ex(-v / R(18.0));            // beta_m
-    a[1] = R(0.07) * M::ex(-v / R(20.0));           // alpha_h
-    b[1] = R(1.0) / (M::ex((R(30.0) - v) / R(10.0)) + R(1.0));  // beta_h
-    a[2] = R(0.1) * M::x_em1((R(10.0) - v) / R(10.0));  // alpha_n = 0.01(10-v)/(e^{(10-v)/10}-1)
-    b[2] = R(0.125) * M::ex(-v / R(80.0));          // beta_n
+    a[0] = M::x_em1((R(25.0) - v) * R(1.0 / 10.0));      // alpha_m = 0.1(25-v)/(e^{(25-v)/10}-1)
+    b[0] = R(4.0) * M::ex(-v * R(1.0 / 18.0));            // beta_m
+    a[1] = R(0.07) * M::ex(-v * R(1.0 / 20.0));           // alpha_h
+    b[1] = R(1.0) / (M::ex((R(30.0) - v) * R(1.0 / 10.0)) + R(1.0));  // beta_h
+    a[2] = R(0.1) * M::x_em1((R(10.0) - v) * R(1.0 / 10.0));  // alpha_n = 0.01(10-v)/(e^{(10-v)/10}-1)
+    b[2] = R(0.125) * M::ex(-v * R(1.0 / 80.0));          // beta_n
   }
   static __device__ __forceinline__ void gating(R V, const R*, const R*, R* lam, R* zinf) {
     R a[3], b[3];
@@ -122,22 +129,22 @@ template <typename R> struct ModelTTP06 {
     const R CaSS = zS[5];
     // I_Na gates
     {
-      const R s = sig((R(-56.86) - V) / R(9.03));
+      const R s = sig((R(-56.86) - V) * R(1.0 / 9.03));
       zinf[0] = s * s;
-      const R am = sig((R(-60.0) - V) / R(5.0));
-      const R bm = R(0.1) * sig((V + R(35.0)) / R(5.0)) + R(0.10) * sig((V - R(50.0)) / R(200.0));
+      const R am = sig((R(-60.0) - V) * R(1.0 / 5.0));
+      const R bm = R(0.1) * sig((V + R(35.0)) * R(1.0 / 5.0)) + R(0.10) * sig((V - R(50.0)) * R(1.0 / 200.0));
       lam[0] = -R(1) / (am * bm);
     }
-    const R hs = sig((V + R(71.55)) / R(7.43));
+    const R hs = sig((V + R(71.55)) * R(1.0 / 7.43));
     zinf[1] = hs * hs;
     zinf[2] = hs * hs;
     if (V >= R(-40.0)) {
-      const R bh = R(0.77) / (R(0.13) * (R(1) + M::ex(-(V + R(10.66)) / R(11.1))));
+      const R bh = R(0.77) / (R(0.13) * (R(1) + M::ex(-(V + R(10.66)) * R(1.0 / 11.1))));
       lam[1] = -bh;  // alpha_h = 0
       const R bj = R(0.6) * M::ex(R(0.057) * V) / (R(1) + M::ex(R(-0.1) * (V + R(32.0))));
       lam[2] = -bj;  // alpha_j = 0
     } else {
-      const R ah = R(0.057) * M::ex(-(V + R(80.0)) / R(6.8));
+      const R ah = R(0.057) * M::ex(-(V + R(80.0)) * R(1.0 / 6.8));
       const R bh = R(2.7) * M::ex(R(0.079) * V) + R(3.1e5) * M::ex(R(0.3485) * V);
       lam[1] = -(ah + bh);
       const R aj = (R(-2.5428e4) * M::ex(R(0.2444) * V) - R(6.948e-6) * M::ex(R(-0.04391) * V)) *
@@ -146,43 +153,43 @@ template <typename R> struct ModelTTP06 {
       lam[2] = -(aj + bj);
     }
     // I_Kr gates
-    zinf[3] = sig((R(-26.0) - V) / R(7.0));
-    lam[3] = -R(1) / ((R(450.0) * sig((R(-45.0) - V) / R(10.0))) * (R(6.0) * sig((V + R(30.0)) / R(11.5))));
-    zinf[4] = sig((V + R(88.0)) / R(24.0));
-    lam[4] = -R(1) / ((R(3.0) * sig((R(-60.0) - V) / R(20.0))) * (R(1.12) * sig((V - R(60.0)) / R(20.0))));
+    zinf[3] = sig((R(-26.0) - V) * R(1.0 / 7.0));
+    lam[3] = -R(1) / ((R(450.0) * sig((R(-45.0) - V) * R(1.0 / 10.0))) * (R(6.0) * sig((V + R(30.0)) * R(1.0 / 11.5))));
+    zinf[4] = sig((V + R(88.0)) * R(1.0 / 24.0));
+    lam[4] = -R(1) / ((R(3.0) * sig((R(-60.0) - V) * R(1.0 / 20.0))) * (R(1.12) * sig((V - R(60.0)) * R(1.0 / 20.0))));
     // I_Ks gate
-    zinf[5] = sig((R(-5.0) - V) / R(14.0));
-    lam[5] = -R(1) / ((R(1400.0) / M::sq(R(1) + M::ex((R(5.0) - V) / R(6.0)))) * sig((V - R(35.0)) / R(15.0)) +
+    zinf[5] = sig((R(-5.0) - V) * R(1.0 / 14.0));
+    lam[5] = -R(1) / ((R(1400.0) / M::sq(R(1) + M::ex((R(5.0) - V) * R(1.0 / 6.0)))) * sig((V - R(35.0)) * R(1.0 / 15.0)) +
                       R(80.0));
     // I_to gates (epicardial s)
-    zinf[6] = sig((R(20.0) - V) / R(6.0));
+    zinf[6] = sig((R(20.0) - V) * R(1.0 / 6.0));
     {
       const R d40 = V + R(40.0);
-      lam[6] = -R(1) / (R(9.5) * M::ex(-(d40 * d40) / R(1800.0)) + R(0.8));
+      lam[6] = -R(1) / (R(9.5) * M::ex(-(d40 * d40) * R(1.0 / 1800.0)) + R(0.8));
     }
-    zinf[7] = sig((V + R(20.0)) / R(5.0));
+    zinf[7] = sig((V + R(20.0)) * R(1.0 / 5.0));
     {
       const R d45 = V + R(45.0);
-      lam[7] = -R(1) / (R(85.0) * M::ex(-(d45 * d45) / R(320.0)) + R(5.0) * sig((V - R(20.0)) / R(5.0)) + R(3.0));
+      lam[7] = -R(1) / (R(85.0) * M::ex(-(d45 * d45) * R(1.0 / 320.0)) + R(5.0) * sig((V - R(20.0)) * R(1.0 / 5.0)) + R(3.0));
     }
     // I_CaL gates
-    zinf[8] = sig((R(-8.0) - V) / R(7.5));
-    lam[8] = -R(1) / ((R(1.4) * sig((R(-35.0) - V) / R(13.0)) + R(0.25)) * (R(1.4) * sig((V + R(5.0)) / R(5.0))) +
-                      sig((R(50.0) - V) / R(20.0)));
-    zinf[9] = sig((V + R(20.0)) / R(7.0));
+    zinf[8] = sig((R(-8.0) - V) * R(1.0 / 7.5));
+    lam[8] = -R(1) / ((R(1.4) * sig((R(-35.0) - V) * R(1.0 / 13.0)) + R(0.25)) * (R(1.4) * sig((V + R(5.0)) * R(1.0 / 5.0))) +
+                      sig((R(50.0) - V) * R(1.0 / 20.0)));
+    zinf[9] = sig((V + R(20.0)) * R(1.0 / 7.0));
     {
       const R d27 = V + R(27.0);
-      lam[9] = -R(1) / (R(1102.5) * M::ex(-(d27 * d27) / R(225.0)) + R(200.0) * sig((R(13.0) - V) / R(10.0)) +
-                        R(180.0) * sig((V + R(30.0)) / R(10.0)) + R(20.0));
+      lam[9] = -R(1) / (R(1102.5) * M::ex(-(d27 * d27) * R(1.0 / 225.0)) + R(200.0) * sig((R(13.0) - V) * R(1.0 / 10.0)) +
+                        R(180.0) * sig((V + R(30.0)) * R(1.0 / 10.0)) + R(20.0));
     }
-    zinf[10] = R(0.67) * sig((V + R(35.0)) / R(7.0)) + R(0.33);
+    zinf[10] = R(0.67) * sig((V + R(35.0)) * R(1.0 / 7.0)) + R(0.33);
     {
       const R d25 = V + R(25.0);
-      lam[10] = -R(1) / (R(600.0) * M::ex(-(d25 * d25) / R(170.0)) + R(31.0) * sig((R(25.0) - V) / R(10.0)) +
-                         R(16.0) * sig((V + R(30.0)) / R(10.0)));
+      lam[10] = -R(1) / (R(600.0) * M::ex(-(d25 * d25) * R(1.0 / 170.0)) + R(31.0) * sig((R(25.0) - V) * R(1.0 / 10.0)) +
+                         R(16.0) * sig((V + R(30.0)) * R(1.0 / 10.0)));
     }
     {
-      const R c = CaSS / R(0.05);
+      const R c = CaSS * R(1.0 / 0.05);
       const R q = R(1) + c * c;
       zinf[11] = R(0.6) / q + R(0.4);
       lam[11] = -R(1) / (R(80.0) / q + R(2.0));
@@ -199,7 +206,7 @@ template <typename R> struct ModelTTP06 {
     const R E_Na = RTF * M::ln(R(Nao) / Nai);
     const R E_Ks = RTF * M::ln((R(Ko) + R(0.03) * R(Nao)) / (Ki + R(0.03) * Nai));
     const R E_Ca = R(0.5) * RTF * M::ln(R(Cao) / Cai);
-    const R sqko = M::sq(R(Ko) / R(5.4));
+    const R sqko = M::sq(R(Ko) * R(1.0 / 5.4));
     const R VK = V - E_K;
     const R aK1 = R(0.1) / (R(1) + M::ex(R(0.06) * (VK - R(200.0))));
     const R bK1 = (R(3.0) * M::ex(R(0.0002) * (VK + R(100.0))) + M::ex(R(0.1) * (VK - R(10.0)))) /
@@ -222,7 +229,7 @@ template <typename R> struct ModelTTP06 {
     const R I_NaK = R(2.724) * R(Ko / (Ko + 1.0)) * Nai / (Nai + R(40.0)) /
                     (R(1) + R(0.1245) * M::ex(R(-0.1) * V * iRTF) + R(0.0353) * M::ex(-V * iRTF));
     const R I_pCa = R(0.1238) * Cai / (R(0.0005) + Cai);
-    const R I_pK = R(0.0146) * VK / (R(1) + M::ex((R(25.0) - V) / R(5.98)));
+    const R I_pK = R(0.0146) * VK / (R(1) + M::ex((R(25.0) - V) * R(1.0 / 5.98)));
     Iion = I_Kr + I_Ks + I_K1 + I_to + I_Na + I_bNa + I_CaL + I_bCa + I_NaK + I_NaCa + I_pCa + I_pK;
 
     // calcium dynamics

@@ -127,6 +127,11 @@ struct emrkc_solver {
   double* d_V[3] = {nullptr, nullptr, nullptr};
   void* d_Z[3] = {nullptr, nullptr, nullptr};
   double* d_U[3] = {nullptr, nullptr, nullptr};
+  float* d_V32[3] = {nullptr, nullptr, nullptr};  // mixed: hi part of V per state buffer
+  float* d_Vlo[3] = {nullptr, nullptr, nullptr};  // mixed: lo part of V (V = hi + lo)
+  float* d_Vn32 = nullptr;                         // mixed: hi of V_n when s >= 2
+  float* d_D[3] = {nullptr, nullptr, nullptr};    // mixed: inner increments delta_k
+  float* d_LV = nullptr;                          // mixed: L V_{j-1}
   void* d_F = nullptr;
   uint8_t* d_mask = nullptr;
   double* d_vF = nullptr;
@@ -151,6 +156,7 @@ struct emrkc_solver {
   double last_eta = 0, last_rhoF = 0, last_rhoS = 0;
   int itF = 0, itS = 0;
   int64_t total_it = 0, launches = 0;
+  int64_t mat_entries = 0, mat_slots = 0;
   bool act_on = false;
   double phase_ms[EMRKC_NUM_PHASES] = {0};
   int64_t phase_launches[EMRKC_NUM_PHASES] = {0};
@@ -228,7 +234,9 @@ void free_all(emrkc_solver* s) {
   void* ptrs[] = {s->d_slice_ptr, s->d_width, s->d_col, s->d_val, s->d_val32, s->d_V[0], s->d_V[1], s->d_V[2],
                   s->d_Z[0], s->d_Z[1], s->d_Z[2], s->d_U[0], s->d_U[1], s->d_U[2], s->d_F, s->d_mask, s->d_vF,
                   s->d_vF2, s->d_vS, s->d_vS2, s->d_fy, s->d_act, s->d_Vn, s->d_tmp, s->d_rest, s->d_flags,
-                  s->rs.partials, s->rs.ticket, s->rs.result};
+                  s->rs.partials, s->rs.ticket, s->rs.result, s->d_V32[0], s->d_V32[1], s->d_V32[2],
+                  s->d_D[0], s->d_D[1], s->d_D[2], s->d_LV, s->d_Vlo[0], s->d_Vlo[1], s->d_Vlo[2],
+                  s->d_Vn32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (s->h_pin) cudaFreeHost(s->h_pin);
@@ -260,12 +268,18 @@ int check_flags(emrkc_solver* s) {
   return EMRKC_OK;
 }
 
+// Mixed path: write V = hi + lo of the current state into the double buffer.
+void materialise_V(emrkc_solver* s) {
+  if (s->d_V32[s->cur]) launch_ff_join(s->d_V32[s->cur], s->d_Vlo[s->cur], s->d_V[s->cur], s->n, s->stream);
+}
+
 double stim_at(const emrkc_solver* s, double t) {
   return (s->d_mask != nullptr && s->t_on <= t && t <= s->t_off) ? s->amp : 0.0;
 }
 
 // Algorithm 5 on f_F (V block only).
 int power_F(emrkc_solver* s) {
+  materialise_V(s);
   double* V = s->d_V[s->cur];
   s->launch(EMRKC_PHASE_OTHER, [&] { launch_sumsq(s->n, V, s->rs, 0, s->stream); });
   s->launch(EMRKC_PHASE_OTHER, [&] { launch_sumsq(s->n, s->d_vF, s->rs, 1, s->stream); });
@@ -312,6 +326,7 @@ int power_F(emrkc_solver* s) {
 
 // Algorithm 5 on f_S (full state), evaluated in FP64.
 int power_S(emrkc_solver* s) {
+  materialise_V(s);
   double* V = s->d_V[s->cur];
   const int64_t rows = s->N;
   PowerSArgs a;
@@ -421,6 +436,29 @@ int do_step(emrkc_solver* s, double dt) {
     a.threshold = s->opt.act_threshold;
     a.flags = s->d_flags;
     a.Vn_copy = (j == 1 && S >= 2) ? s->d_Vn : nullptr;
+    a.inv_eta = 1.0 / eta;
+    a.mu1 = ci.mu[1];
+    a.V32m1 = s->d_V32[bm1];
+    a.V32out = s->d_V32[bo];
+    a.Vlo_m1 = s->d_Vlo[bm1];
+    a.Vhi_m2 = j >= 2 ? s->d_V32[bm2] : nullptr;
+    a.Vlo_m2 = j >= 2 ? s->d_Vlo[bm2] : nullptr;
+    a.Vlo_out = s->d_Vlo[bo];
+    a.Vn32 = (S == 1) ? s->d_V32[b0] : s->d_Vn32;
+    a.Vn32_copy = (j == 1 && S >= 2) ? s->d_Vn32 : nullptr;
+    a.f_th = (float)s->opt.act_threshold;
+    a.D1 = s->d_D[0];
+    a.LV = s->d_LV;
+    a.f_nu = (float)a.nu;
+    a.f_kappa = (float)a.kappa;
+    a.f_mudt = (float)a.mu_dt;
+    a.f_inv_eta = (float)(1.0 / eta);
+    a.f_cm = (float)a.cm_inner;
+    a.f_mu1 = (float)ci.mu[1];
+    a.f_mu1eta = (float)(ci.mu[1] * eta);
+    a.f_eta = (float)eta;
+    a.f_stim = (float)a.stim;
+    a.f_inv_Cm = (float)(1.0 / s->Cm);
     s->launch(EMRKC_PHASE_STAGE, [&] { s->ks.stage(a, s->ell, j >= 2, s->stream); });
     for (int k = 2; k <= Mi; ++k) {
       InnerArgs b;
@@ -447,6 +485,25 @@ int do_step(emrkc_solver* s, double dt) {
       b.dt = dt;
       b.threshold = s->opt.act_threshold;
       b.flags = s->d_flags;
+      b.inv_eta = 1.0 / eta;
+      b.d1 = s->d_D[(k - 2) % 3];
+      b.d2 = (k - 2 == 0) ? nullptr : s->d_D[(k - 3) % 3];
+      b.dk = s->d_D[(k - 1) % 3];
+      b.LV = s->d_LV;
+      b.V32out = s->d_V32[bo];
+      b.Vhi1 = s->d_V32[bm1];
+      b.Vlo1 = s->d_Vlo[bm1];
+      b.Vhi2 = j >= 2 ? s->d_V32[bm2] : nullptr;
+      b.Vlo2 = j >= 2 ? s->d_Vlo[bm2] : nullptr;
+      b.Vlo_out = s->d_Vlo[bo];
+      b.Vn32 = a.Vn32;
+      b.f_okappa = (float)a.kappa;
+      b.f_omu_dt = (float)a.mu_dt;
+      b.f_th = a.f_th;
+      b.f_nu = (float)ci.nu[k];
+      b.f_kappa = (float)ci.kappa[k];
+      b.f_mueta = (float)(ci.mu[k] * eta);
+      b.f_inv_eta = (float)(1.0 / eta);
       s->launch(EMRKC_PHASE_INNER, [&] { s->ks.inner(b, s->ell, s->stream); });
     }
   }
@@ -500,6 +557,9 @@ int build_matrix(emrkc_solver* s, const emrkc_matrix* m) {
     sptr[b + 1] = sptr[b] + (int64_t)w * 32;
   }
   const int64_t total = sptr[ns];
+  s->mat_slots = total;
+  s->mat_entries = 0;
+  for (int64_t i = 0; i < n; ++i) s->mat_entries += (int64_t)rows[i].size();
   std::vector<int32_t> col(std::max<int64_t>(total, 1), 0);
   std::vector<double> val(mixed ? 0 : std::max<int64_t>(total, 1), 0.0);
   std::vector<float> val32(mixed ? std::max<int64_t>(total, 1) : 0, 0.0f);
@@ -592,7 +652,8 @@ int state_copy(emrkc_solver* s, int var, double* buf, int64_t len, bool to_host,
                                       : (to_host ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice);
   const size_t row = (size_t)s->n * sizeof(double), pitch_b = (size_t)s->n * sizeof(double);
   cudaError_t e = cudaSuccess;
-  // V
+  // V (mixed path: materialise hi + lo as double first)
+  if (var <= 0 && to_host) materialise_V(s);
   if (var <= 0) {
     e = to_host ? cudaMemcpyAsync(buf, s->d_V[s->cur], row, kind, s->stream)
                 : cudaMemcpyAsync(s->d_V[s->cur], buf, row, kind, s->stream);
@@ -621,6 +682,8 @@ int state_copy(emrkc_solver* s, int var, double* buf, int64_t len, bool to_host,
     }
     if (e != cudaSuccess) return s->cuda_fail(e, "state copy");
   }
+  if (!to_host && var <= 0 && s->d_V32[s->cur])
+    launch_ff_split(s->d_V[s->cur], s->d_V32[s->cur], s->d_Vlo[s->cur], s->n, s->stream);
   e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return s->cuda_fail(e, "state copy");
   return EMRKC_OK;
@@ -754,6 +817,15 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
     fail |= dalloc(&s->d_U[b], ld) != cudaSuccess;
   }
   fail |= cudaMalloc(&s->d_F, ld * s->rsize) != cudaSuccess;
+  if (s->precision == EMRKC_PREC_MIXED) {
+    for (int b = 0; b < 3; ++b) {
+      fail |= dalloc(&s->d_V32[b], ld) != cudaSuccess;
+      fail |= dalloc(&s->d_Vlo[b], ld) != cudaSuccess;
+      fail |= dalloc(&s->d_D[b], ld) != cudaSuccess;
+    }
+    fail |= dalloc(&s->d_LV, ld) != cudaSuccess;
+    fail |= dalloc(&s->d_Vn32, ld) != cudaSuccess;
+  }
   fail |= dalloc(&s->d_vF, ld) != cudaSuccess;
   fail |= dalloc(&s->d_vF2, ld) != cudaSuccess;
   fail |= dalloc(&s->d_vS, (int64_t)s->N * ld) != cudaSuccess;
@@ -786,6 +858,7 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
   cudaMemcpy(s->d_rest, rest.data(), rest.size() * sizeof(double), cudaMemcpyHostToDevice);
   for (int b = 0; b < 3; ++b) {
     launch_fill(s->d_V[b], ld, rest[0], s->stream);
+    if (s->d_V32[b]) launch_ff_split(s->d_V[b], s->d_V32[b], s->d_Vlo[b], ld, s->stream);
     if (nz > 0) launch_fill_rows(s->d_Z[b], (int)s->zsize, s->n, ld, (int)nz, s->d_rest + 1, s->stream);
   }
   launch_fill(s->d_act, ld, std::nan(""), s->stream);
@@ -894,6 +967,8 @@ int emrkc_get_stats(emrkc_solver* s, emrkc_stats* out) {
   out->pow_iters_S = s->itS;
   out->total_pow_iters = s->total_it;
   out->launches = s->launches;
+  out->matrix_entries = s->mat_entries;
+  out->matrix_slots = s->mat_slots;
   for (int k = 0; k < EMRKC_NUM_PHASES; ++k) {
     out->phase_ms[k] = s->phase_ms[k];
     out->phase_launches[k] = s->phase_launches[k];
