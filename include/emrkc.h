@@ -202,6 +202,27 @@ int emrkc_get_activation_times(emrkc_solver* s, double* host_out, int64_t n);
  * raw estimates (without the safety factor) and iteration counts. */
 int emrkc_estimate_rho(emrkc_solver* s, double* rho_F, double* rho_S, int* it_F, int* it_S);
 
+/* Allocation-free variant of the f_F half of emrkc_estimate_rho (the paper
+ * has no counterpart: it exists for callers that must not allocate device
+ * memory while they run, e.g. a host whose allocator owns the whole GPU or a
+ * time-critical loop that cannot afford cudaMalloc's synchronisation).
+ * Runs Algorithm 5 on f_F for the solver's current V with caller-owned
+ * device vectors: d_v (n doubles; in: start or warm-start direction, out:
+ * final iterate) and d_w (n doubles of work space); rho_warm is the warm
+ * start (0 for none).  Writes the raw estimate (no safety factor) and the
+ * iteration count.  The reduction scratch (8 KiB of partial sums, 8 result
+ * slots and a ticket counter, 8.5 KiB in all) is a static device array that
+ * every GPU loading the library holds until exit; the first call on a device
+ * looks its address up (cudaGetSymbolAddress) and zeroes the ticket, so make
+ * that first call before any stream capture.  Every call shares the array:
+ * calls that overlap on the GPU (other streams, other threads) race.  The
+ * grid is capped at 1024 blocks, the capacity of the scratch; a problem that
+ * would need more is rejected.  Errors: EMRKC_ERR_ARG for a null pointer or
+ * n != number of nodes, EMRKC_ERR_CUDA if the set-up fails.  Calls no
+ * cudaMalloc / cudaFree and synchronises the solver's stream. */
+int emrkc_estimate_rho_F_noalloc(emrkc_solver* s, double* d_v, double* d_w, int64_t n, double rho_warm,
+                                 double* rho_out, int* it_out);
+
 /* Set the time and step counter (checkpoint/resume together with set_state). */
 int emrkc_set_time(emrkc_solver* s, double t, int64_t steps);
 

@@ -168,6 +168,15 @@ class Solver:
                                                  C.byref(its)))
         return rf.value, rs.value, itf.value, its.value
 
+    def estimate_rho_F_noalloc(self, d_v, d_w, n, rho_warm=0.0):
+        """Algorithm 5 on f_F with caller-owned device vectors (pointers) and the
+        library's static scratch; allocates no device memory."""
+        rho = C.c_double()
+        it = C.c_int()
+        self._check(self._lib.emrkc_estimate_rho_F_noalloc(self._h, C.c_void_p(d_v), C.c_void_p(d_w), n,
+                                                           rho_warm, C.byref(rho), C.byref(it)))
+        return rho.value, it.value
+
     def set_time(self, t, steps):
         self._check(self._lib.emrkc_set_time(self._h, t, steps))
 

@@ -75,6 +75,8 @@ SIGNATURES = {
     "emrkc_get_activation_times": (C.c_int, [_P, _PD, C.c_int64]),
     "emrkc_estimate_rho": (C.c_int, [_P, _PD, _PD, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "emrkc_set_time": (C.c_int, [_P, C.c_double, C.c_int64]),
+    "emrkc_estimate_rho_F_noalloc": (C.c_int, [_P, C.c_void_p, C.c_void_p, C.c_int64, C.c_double, _PD,
+                                               C.POINTER(C.c_int)]),
     "emrkc_get_stats": (C.c_int, [_P, C.POINTER(Stats)]),
     "emrkc_last_error": (C.c_char_p, [_P]),
     "emrkc_destroy": (None, [_P]),

@@ -171,4 +171,10 @@ void launch_fill(double* x, int64_t count, double value, cudaStream_t st);
 void launch_fill_rows(void* z, int zsize, int64_t n, int64_t ld, int rows, const double* values,
                       cudaStream_t st);
 
+// Allocation-free power iteration on f_F (noalloc.cu): static device scratch.
+int noalloc_scratch(int device, cudaStream_t st, ReduceScratch* out, const char** why);
+int noalloc_max_blocks();
+void noalloc_sumsq(int64_t count, const double* x, const ReduceScratch& rs, int slot, cudaStream_t st);
+void noalloc_power_F(const PowerFArgs& a, const Ell& A, bool mixed, const ReduceScratch& rs, cudaStream_t st);
+
 }  // namespace emrkc

@@ -981,6 +981,78 @@ const char* emrkc_last_error(const emrkc_solver* s) {
   return s->err.c_str();
 }
 
+int emrkc_estimate_rho_F_noalloc(emrkc_solver* s, double* d_v, double* d_w, int64_t n, double rho_warm,
+                                 double* rho_out, int* it_out) {
+  if (!s) return EMRKC_ERR_ARG;
+  if (!d_v || !d_w || !rho_out) return s->fail(EMRKC_ERR_ARG, "null pointer");
+  if (n != s->n) return s->fail(EMRKC_ERR_ARG, "vector length must equal the number of nodes");
+  // the reduction launches min(ceil(n/256), kReduceMaxBlocks) blocks, one partial sum each
+  const int64_t blocks = std::min<int64_t>((n + kReduceBlock - 1) / kReduceBlock, kReduceMaxBlocks);
+  if (blocks > noalloc_max_blocks())
+    return s->fail(EMRKC_ERR_ARG, "problem needs more reduction blocks than the static scratch holds");
+  if (!(rho_warm >= 0.0) || !std::isfinite(rho_warm)) return s->fail(EMRKC_ERR_ARG, "rho_warm must be >= 0");
+  cudaSetDevice(s->device);
+  ReduceScratch rs;
+  const char* why = "";
+  if (noalloc_scratch(s->device, s->stream, &rs, &why) != 0) return s->fail(EMRKC_ERR_CUDA, why);
+  materialise_V(s);
+  const double* V = s->d_V[s->cur];
+  const bool mixed = s->precision == EMRKC_PREC_MIXED;
+  double res[2] = {0.0, 0.0};
+  auto read = [&](int first, int count) -> int {
+    cudaError_t e = cudaMemcpyAsync(res, rs.result + first, count * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return s->cuda_fail(e, "allocation-free power iteration");
+    return EMRKC_OK;
+  };
+  noalloc_sumsq(n, V, rs, 0, s->stream);
+  noalloc_sumsq(n, d_v, rs, 1, s->stream);
+  int rc = read(0, 2);
+  if (rc) return rc;
+  const double ny = std::sqrt(res[0]);
+  double nv = std::sqrt(res[1]);
+  const double delta = ny > 0.0 ? ny * s->opt.pow_eps : s->opt.pow_eps;
+  double rho = rho_warm;
+  int it = 0;
+  if (nv == 0.0) {
+    *rho_out = 0.0;
+    if (it_out) *it_out = 0;
+    return EMRKC_OK;
+  }
+  double* cur = d_v;
+  double* nxt = d_w;
+  double q = delta / nv, rho_old = 0.0;
+  while (std::fabs(rho - rho_old) >= s->opt.pow_tol * rho && it < s->opt.pow_max_iter) {
+    rho_old = rho;
+    PowerFArgs a;
+    a.n = n;
+    a.V = V;
+    a.v_old = cur;
+    a.v_new = nxt;
+    a.q = q;
+    a.slot = 2;
+    noalloc_power_F(a, s->ell, mixed, rs, s->stream);
+    if ((rc = read(2, 1))) return rc;
+    std::swap(cur, nxt);
+    ++it;
+    nv = std::sqrt(res[0]);
+    if (nv == 0.0) {
+      rho = 0.0;
+      break;
+    }
+    q = delta / nv;
+    rho = nv / delta;
+  }
+  if (cur != d_v) {
+    cudaError_t e = cudaMemcpyAsync(d_v, cur, n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return s->cuda_fail(e, "allocation-free power iteration");
+  }
+  *rho_out = rho;
+  if (it_out) *it_out = it;
+  return EMRKC_OK;
+}
+
 void emrkc_destroy(emrkc_solver* s) {
   if (!s) return;
   free_all(s);
