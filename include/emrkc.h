@@ -117,6 +117,9 @@ typedef struct {
   int device;         /* CUDA device ordinal                                */
   int profile;        /* 1: time every kernel class with CUDA events        */
   int use_graphs;     /* 1: replay each fixed (s, m) step as a CUDA graph  */
+  double rho_S_min;   /* known bound on rho(f_S): the step uses
+                         max(safety * estimate, rho_S_min) (Sec. 3.1: rho is
+                         known or estimated); 0 = estimate only            */
 } emrkc_options;
 
 /* Kernel classes reported in emrkc_stats.phase_ms / phase_launches. */
@@ -233,6 +236,77 @@ int emrkc_get_stats(emrkc_solver* s, emrkc_stats* out);
 const char* emrkc_last_error(const emrkc_solver* s);
 
 void emrkc_destroy(emrkc_solver* s);
+
+/* ---- Batched persistent step --------------------------------------------
+ * Many independent monodomain problems (instances) of different sizes,
+ * ionic models and stage counts advance one emRKC step each in ONE persistent
+ * kernel launch per step (replayed as a CUDA graph).  Every instance is a
+ * mixed-precision solver (EMRKC_PREC_MIXED) whose state stays on the device.
+ * The rho policy of a batch is EMRKC_RHO_ONCE (Algorithm 5 when an instance
+ * takes its first step) or EMRKC_RHO_FIXED; s and m per instance are then
+ * fixed while dt is unchanged.  s, m <= 32 and s * m <= 64 per instance.
+ * Instances can be added and removed between steps (continuous batching).  */
+typedef struct emrkc_batch emrkc_batch;
+
+typedef struct {
+  int64_t n;          /* nodes                                   */
+  int N;              /* state variables                         */
+  int model;          /* ionic model                             */
+  int s, m;           /* stage counts (0 before the first step)  */
+  double t;           /* time of the instance (ms)               */
+  int64_t steps;      /* steps taken                             */
+  int64_t device_bytes; /* device memory held by the instance    */
+} emrkc_batch_info;
+
+typedef struct {
+  int instances;
+  int64_t total_nodes;
+  int64_t items;        /* work items per step                    */
+  int tile, block, grid;/* launch configuration in use            */
+  int64_t launches;     /* persistent launches so far             */
+  int64_t device_bytes; /* all instances plus the batch tables    */
+} emrkc_batch_stats;
+
+/* Options: device, cuda_stream, seed, act_threshold, rho_every (ONCE or
+ * FIXED with rho_F/rho_S), use_graphs are used; precision is forced to MIXED.
+ * opt may be NULL.  The batch starts with tile 1024 nodes, block 128. */
+int emrkc_batch_create(const emrkc_options* opt, emrkc_batch** out);
+/* Add an instance (copies its inputs; same arguments as emrkc_create).
+ * inst_opt (may be NULL: the batch's options) sets the instance's rho policy
+ * (ONCE or FIXED, rho_F, rho_S, rho_S_min), seed and activation threshold;
+ * precision, stream and device are the batch's.  *id_out receives a
+ * batch-unique id.  Takes effect at the next step. */
+int emrkc_batch_add(emrkc_batch* b, const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_model,
+                    const emrkc_stimulus* stim, const emrkc_options* inst_opt, int* id_out);
+/* Remove an instance and free its device memory. */
+int emrkc_batch_remove(emrkc_batch* b, int id);
+/* One emRKC step of size dt for every instance: one persistent launch. */
+int emrkc_batch_step(emrkc_batch* b, double dt);
+/* Wait for enqueued steps; EMRKC_ERR_NONFINITE if an instance produced a
+ * non-finite V, EMRKC_ERR_TIMEOUT if a dependency wait gave up. */
+int emrkc_batch_sync(emrkc_batch* b);
+int emrkc_batch_get_state(emrkc_batch* b, int id, int var, double* host_out, int64_t len);
+int emrkc_batch_set_state(emrkc_batch* b, int id, int var, const double* host_in, int64_t len);
+int emrkc_batch_get_activation_times(emrkc_batch* b, int id, double* host_out, int64_t n);
+int emrkc_batch_get_info(emrkc_batch* b, int id, emrkc_batch_info* out);
+int emrkc_batch_get_stats(emrkc_batch* b, emrkc_batch_stats* out);
+/* Launch configuration: tile in {256, 512, ..., 8192} nodes, block 128 or 256. */
+int emrkc_batch_set_config(emrkc_batch* b, int tile, int block);
+/* Time each (tile, block) candidate over `reps` steps of size dt without
+ * advancing any instance (the candidates run with bookkeeping and
+ * activation writes disabled) and keep the fastest.  Returns EMRKC_ERR_STATE
+ * (configuration unchanged) if an instance has s >= 3, whose dry steps would
+ * overwrite its current state buffer.  Outputs may be NULL. */
+int emrkc_batch_autotune(emrkc_batch* b, double dt, int reps, int* tile_out, int* block_out, double* ms_out);
+/* Diagnostics: polls of a dependency wait before the persistent kernel gives
+ * up, records EMRKC_ERR_TIMEOUT (reported by emrkc_batch_sync) and returns;
+ * default 2^24 (about 2 s with 100 ns back-off).  limit >= 0. */
+int emrkc_batch_set_spin_limit(emrkc_batch* b, int64_t limit);
+/* Device bytes an instance of n nodes with nnz_per_row stored entries per
+ * row would hold (for admission control against an HBM budget). */
+int64_t emrkc_instance_bytes(int64_t n, double nnz_per_row, int ionic_model);
+const char* emrkc_batch_last_error(const emrkc_batch* b);
+void emrkc_batch_destroy(emrkc_batch* b);
 
 #ifdef __cplusplus
 }

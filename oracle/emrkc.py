@@ -139,10 +139,13 @@ class OracleRun:
     rho_every = k >= 1 recomputes rho_F and rho_S every k-th step (warm
     started), rho_every = 0 only before the first step; fixed_rho =
     (rho_F, rho_S) bypasses the power iteration and uses the values as given.
+    rho_S_min is a known bound on the stiffness of f_S (Sec. 3.1: rho is
+    "known or estimated"); the step uses max(safety * estimate, rho_S_min).
     """
 
     def __init__(self, prob: Monodomain, Y0=None, rho_every=1, fixed_rho=None, seed=0,
-                 safety=SAFETY, act_threshold=-20.0, pow_tol=1e-2, pow_eps=1e-8, pow_max_iter=50):
+                 safety=SAFETY, act_threshold=-20.0, pow_tol=1e-2, pow_eps=1e-8, pow_max_iter=50,
+                 rho_S_min=0.0):
         self.p = prob
         self.Y = prob.initial_state() if Y0 is None else np.array(Y0, dtype=np.float64)
         self.t = 0.0
@@ -156,6 +159,7 @@ class OracleRun:
         self.rhoF_raw = 0.0
         self.rhoS_raw = 0.0
         self.act_threshold = act_threshold
+        self.rho_S_min = rho_S_min  # known lower bound on rho(f_S) (the rho of Alg. 1 may be known)
         self.act = np.full(prob.n, np.nan)
         self.log = []  # (s, m, rho_F, rho_S, itF, itS) per step
 
@@ -176,7 +180,7 @@ class OracleRun:
             if due:
                 itF, itS = self.update_rho()
             rho_F = self.safety * self.rhoF_raw
-            rho_S = self.safety * self.rhoS_raw
+            rho_S = max(self.safety * self.rhoS_raw, self.rho_S_min)
         V_old = self.Y[0].copy()
         Y, s, m, eta = self.p.emrkc_step(self.t, self.Y, dt, rho_F, rho_S)
         V_new = Y[0]

@@ -80,7 +80,8 @@ class Solver:
     def __init__(self, row_ptr, col, K, M, *, chi=1400.0, Cm=1.0, model=MODEL_HH, mask=None,
                  amplitude=50.0, t_on=0.0, t_off=1.0, precision=PREC_FP64, rho_every=1,
                  rho_F=0.0, rho_S=0.0, seed=0, act_threshold=-20.0, stream=None, device=0,
-                 profile=False, use_graphs=True, pow_tol=1e-2, pow_max_iter=50, safety=1.05):
+                 profile=False, use_graphs=True, pow_tol=1e-2, pow_max_iter=50, safety=1.05,
+                 rho_S_min=0.0):
         self._lib = lib()
         self._h = C.c_void_p()
         self.row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
@@ -114,6 +115,7 @@ class Solver:
         o.pow_tol = pow_tol
         o.pow_max_iter = pow_max_iter
         o.safety = safety
+        o.rho_S_min = rho_S_min
         rc = self._lib.emrkc_create(C.byref(mat), C.byref(tis), model, C.byref(stim), C.byref(o),
                                     C.byref(self._h))
         if rc != 0:
@@ -204,3 +206,139 @@ class Solver:
 
     def __exit__(self, *a):
         self.close()
+
+
+def instance_bytes(n, nnz_per_row, model):
+    """Device bytes one batched (mixed-precision) instance holds."""
+    return int(lib().emrkc_instance_bytes(int(n), float(nnz_per_row), int(model)))
+
+
+class Batch:
+    """Many monodomain instances advanced together by one persistent launch per step."""
+
+    def __init__(self, *, rho_every=RHO_ONCE, rho_F=0.0, rho_S=0.0, seed=0, act_threshold=-20.0,
+                 stream=None, device=0, use_graphs=True):
+        self._lib = lib()
+        self._h = C.c_void_p()
+        o = default_options()
+        o.precision = PREC_MIXED
+        o.rho_every = rho_every
+        o.rho_F = rho_F
+        o.rho_S = rho_S
+        o.seed = seed
+        o.act_threshold = act_threshold
+        o.cuda_stream = stream
+        o.device = device
+        o.use_graphs = int(use_graphs)
+        self._rho_every, self._rho_F, self._rho_S = rho_every, rho_F, rho_S
+        rc = self._lib.emrkc_batch_create(C.byref(o), C.byref(self._h))
+        if rc != 0:
+            raise EmrkcError(rc, self._lib.emrkc_batch_last_error(None).decode())
+        self._n = {}
+        self._N = {}
+
+    def _check(self, rc):
+        if rc != 0:
+            raise EmrkcError(rc, self._lib.emrkc_batch_last_error(self._h).decode())
+
+    def add(self, row_ptr, col, K, M, *, chi=1400.0, Cm=1.0, model=MODEL_TTP06, mask=None, amplitude=50.0,
+            t_on=0.0, t_off=1.0, rho_every=None, rho_F=0.0, rho_S=0.0, rho_S_min=0.0, seed=0,
+            act_threshold=-20.0):
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        K = np.ascontiguousarray(K, dtype=np.float64)
+        M = np.ascontiguousarray(M, dtype=np.float64)
+        n = M.size
+        mat = Matrix(n, K.size, row_ptr.ctypes.data_as(C.POINTER(C.c_int64)),
+                     col.ctypes.data_as(C.POINTER(C.c_int32)), _dp(K), _dp(M))
+        tis = Tissue(chi, Cm)
+        stim = Stimulus()
+        if mask is not None:
+            mk = np.ascontiguousarray(mask, dtype=np.uint8)
+            stim.node_mask = mk.ctypes.data_as(C.POINTER(C.c_uint8))
+        stim.amplitude = amplitude
+        stim.t_on = t_on
+        stim.t_off = t_off
+        o = default_options()
+        o.rho_every = self._rho_every if rho_every is None else rho_every
+        o.rho_F = rho_F if rho_every is not None else self._rho_F
+        o.rho_S = rho_S if rho_every is not None else self._rho_S
+        o.rho_S_min = rho_S_min
+        o.seed = seed
+        o.act_threshold = act_threshold
+        out = C.c_int()
+        self._check(self._lib.emrkc_batch_add(self._h, C.byref(mat), C.byref(tis), model, C.byref(stim),
+                                              C.byref(o), C.byref(out)))
+        self._n[out.value] = n
+        self._N[out.value] = num_vars(model)
+        return out.value
+
+    def add_workload(self, w, **kw):
+        rp, col, K, M = assemble_p1(w.coords, w.cells, w.D)
+        return self.add(rp, col, K, M, chi=w.chi, Cm=w.Cm, model=w.model, mask=w.stim_mask,
+                        amplitude=w.stim_amp, t_on=w.t_on, t_off=w.t_off, **kw)
+
+    def remove(self, iid):
+        self._check(self._lib.emrkc_batch_remove(self._h, iid))
+        self._n.pop(iid, None)
+        self._N.pop(iid, None)
+
+    def step(self, dt):
+        self._check(self._lib.emrkc_batch_step(self._h, dt))
+
+    def sync(self):
+        self._check(self._lib.emrkc_batch_sync(self._h))
+
+    def get_state(self, iid, var=-1, out=None):
+        n, N = self._n[iid], self._N[iid]
+        shape = (N, n) if var == -1 else (n,)
+        if out is None:
+            out = np.empty(shape)
+        self._check(self._lib.emrkc_batch_get_state(self._h, iid, var, _dp(out), out.size))
+        return out
+
+    def set_state(self, iid, values, var=-1):
+        values = np.ascontiguousarray(values, dtype=np.float64)
+        self._check(self._lib.emrkc_batch_set_state(self._h, iid, var, _dp(values), values.size))
+
+    def activation_times(self, iid):
+        out = np.empty(self._n[iid])
+        self._check(self._lib.emrkc_batch_get_activation_times(self._h, iid, _dp(out), out.size))
+        return out
+
+    def info(self, iid):
+        from ._ffi import BatchInfo
+        st = BatchInfo()
+        self._check(self._lib.emrkc_batch_get_info(self._h, iid, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in BatchInfo._fields_}
+
+    def stats(self):
+        from ._ffi import BatchStats
+        st = BatchStats()
+        self._check(self._lib.emrkc_batch_get_stats(self._h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in BatchStats._fields_}
+
+    def set_config(self, tile, block):
+        self._check(self._lib.emrkc_batch_set_config(self._h, tile, block))
+
+    def set_spin_limit(self, limit):
+        self._check(self._lib.emrkc_batch_set_spin_limit(self._h, limit))
+
+    def autotune(self, dt, reps=3):
+        t, b, ms = C.c_int(), C.c_int(), C.c_double()
+        self._check(self._lib.emrkc_batch_autotune(self._h, dt, reps, C.byref(t), C.byref(b), C.byref(ms)))
+        return t.value, b.value, ms.value
+
+    def ids(self):
+        return list(self._n)
+
+    def close(self):
+        if self._h:
+            self._lib.emrkc_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

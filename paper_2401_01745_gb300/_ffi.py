@@ -41,7 +41,8 @@ class Options(C.Structure):
                 ("rho_S", C.c_double), ("eps", C.c_double), ("safety", C.c_double),
                 ("pow_tol", C.c_double), ("pow_eps", C.c_double), ("pow_max_iter", C.c_int),
                 ("seed", C.c_uint64), ("act_threshold", C.c_double), ("cuda_stream", C.c_void_p),
-                ("device", C.c_int), ("profile", C.c_int), ("use_graphs", C.c_int)]
+                ("device", C.c_int), ("profile", C.c_int), ("use_graphs", C.c_int),
+                ("rho_S_min", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -51,6 +52,17 @@ class Stats(C.Structure):
                 ("launches", C.c_int64), ("matrix_entries", C.c_int64), ("matrix_slots", C.c_int64),
                 ("phase_ms", C.c_double * NUM_PHASES),
                 ("phase_launches", C.c_int64 * NUM_PHASES)]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("n", C.c_int64), ("N", C.c_int), ("model", C.c_int), ("s", C.c_int), ("m", C.c_int),
+                ("t", C.c_double), ("steps", C.c_int64), ("device_bytes", C.c_int64)]
+
+
+class BatchStats(C.Structure):
+    _fields_ = [("instances", C.c_int), ("total_nodes", C.c_int64), ("items", C.c_int64),
+                ("tile", C.c_int), ("block", C.c_int), ("grid", C.c_int), ("launches", C.c_int64),
+                ("device_bytes", C.c_int64)]
 
 
 _P = C.c_void_p
@@ -80,6 +92,24 @@ SIGNATURES = {
     "emrkc_get_stats": (C.c_int, [_P, C.POINTER(Stats)]),
     "emrkc_last_error": (C.c_char_p, [_P]),
     "emrkc_destroy": (None, [_P]),
+    "emrkc_batch_create": (C.c_int, [C.POINTER(Options), C.POINTER(_P)]),
+    "emrkc_batch_add": (C.c_int, [_P, C.POINTER(Matrix), C.POINTER(Tissue), C.c_int, C.POINTER(Stimulus),
+                                  C.POINTER(Options), C.POINTER(C.c_int)]),
+    "emrkc_batch_remove": (C.c_int, [_P, C.c_int]),
+    "emrkc_batch_step": (C.c_int, [_P, C.c_double]),
+    "emrkc_batch_sync": (C.c_int, [_P]),
+    "emrkc_batch_get_state": (C.c_int, [_P, C.c_int, C.c_int, _PD, C.c_int64]),
+    "emrkc_batch_set_state": (C.c_int, [_P, C.c_int, C.c_int, _PD, C.c_int64]),
+    "emrkc_batch_get_activation_times": (C.c_int, [_P, C.c_int, _PD, C.c_int64]),
+    "emrkc_batch_get_info": (C.c_int, [_P, C.c_int, C.POINTER(BatchInfo)]),
+    "emrkc_batch_get_stats": (C.c_int, [_P, C.POINTER(BatchStats)]),
+    "emrkc_batch_set_config": (C.c_int, [_P, C.c_int, C.c_int]),
+    "emrkc_batch_set_spin_limit": (C.c_int, [_P, C.c_int64]),
+    "emrkc_batch_autotune": (C.c_int, [_P, C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                       C.POINTER(C.c_double)]),
+    "emrkc_instance_bytes": (C.c_int64, [C.c_int64, C.c_double, C.c_int]),
+    "emrkc_batch_last_error": (C.c_char_p, [_P]),
+    "emrkc_batch_destroy": (None, [_P]),
 }
 
 _lib = None

@@ -1,0 +1,182 @@
+// Batched persistent emRKC step: many independent monodomain instances of
+// different sizes, ionic models and stage counts (s, m) advance one step in
+// ONE launch.
+//
+// Work is a phase-major list of items (instance, phase, tile); phase p of an
+// instance is stage j = p / m + 1 with inner stage k = p % m + 1 (k = 1: the
+// fused stage work, k >= 2: an inner SpMV stage).  Persistent CTAs take items
+// in list order from an atomic ticket.  An item of phase p > 0 waits until all
+// tiles of phase p - 1 of its instance are done (per-instance counters).
+// Because items are taken in order and an item only waits on items earlier in
+// the list, every awaited item is already held by a running CTA: the schedule
+// cannot deadlock, whatever the grid size.  Waits are still bounded: after
+// spin_limit polls the kernel records an error and every CTA returns.
+//
+// The per-node arithmetic is the mixed-precision stage / inner code of the
+// single-instance kernels (stage_node_mixed, inner_node_mixed), with loads of
+// data produced within the launch taken through L2 (ld.cg).
+#include <cuda/atomic>
+
+#include "kernels.cuh"
+
+namespace emrkc {
+
+template <class Model>
+__device__ __forceinline__ void batch_stage_rows(const StageArgs& a, const Ell& A, int64_t r0, int64_t r1, bool has_m2) {
+  if (has_m2) {
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) stage_node_mixed<Model, true, true>(a, A, i);
+  } else {
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) stage_node_mixed<Model, false, true>(a, A, i);
+  }
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) batch_step_kernel(const BatchCtl c) {
+  __shared__ unsigned int s_item;
+  __shared__ int s_abort;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_abort = 0;
+      // stop early if another CTA gave up on a wait
+      if (cuda::atomic_ref<int, cuda::thread_scope_device>(*c.err).load(cuda::memory_order_relaxed) != 0)
+        s_item = 0xffffffffu;
+      else
+        s_item = atomicAdd(c.ticket, 1u);
+    }
+    __syncthreads();
+    const unsigned int it = s_item;
+    if (it >= c.n_items) return;
+    const uint64_t d = c.items[it];
+    const int ii = (int)(d >> 40);
+    const int p = (int)((d >> 32) & 0xffu);
+    const int tile = (int)(d & 0xffffffffu);
+    BatchInst* I = c.inst + ii;
+    if (p > 0) {
+      if (threadIdx.x == 0) {
+        cuda::atomic_ref<unsigned int, cuda::thread_scope_device> cnt(c.done[ii * kBatchMaxPhases + p - 1]);
+        const unsigned int need = (unsigned int)I->ntiles;
+        long long k = 0;
+        while (cnt.load(cuda::memory_order_acquire) < need) {
+          if (++k > c.spin_limit) {
+            atomicOr(c.err, 2);
+            s_abort = 1;
+            break;
+          }
+          __nanosleep(100);
+        }
+      }
+      __syncthreads();
+      if (s_abort) return;
+    }
+    const int s = I->s, m = I->m, cur = I->cur;
+    const int j = p / m + 1, k = p % m + 1;
+    const int bm1 = (cur + j - 1) % 3, bm2 = (cur + j + 1) % 3, bo = (cur + j) % 3;
+    const int64_t r0 = (int64_t)tile * c.tile;
+    const int64_t r1 = (r0 + c.tile < I->n) ? r0 + c.tile : I->n;
+    float* const Vn32 = (s == 1) ? I->Vhi[cur] : I->Vn32;
+    double* const act = c.dry ? nullptr : I->act;
+    if (k == 1) {
+      StageArgs a;
+      a.n = I->n;
+      a.ld = I->ld;
+      a.Zm1 = I->Z[bm1];
+      a.Zm2 = j >= 2 ? I->Z[bm2] : nullptr;
+      a.Zout = I->Z[bo];
+      a.m = m;
+      a.F = I->F;
+      a.mask = I->mask;
+      const double ts = __dadd_rn(I->t, __dmul_rn(I->o_c[j - 1], I->dt));
+      a.f_stim = (I->mask != nullptr && I->t_on <= ts && ts <= I->t_off) ? (float)I->amp : 0.0f;
+      a.f_inv_Cm = I->f_inv_Cm;
+      a.final_stage = (j == s && m == 1) ? 1 : 0;
+      a.Vn32 = Vn32;
+      a.act = act;
+      a.t_n = I->t;
+      a.dt = I->dt;
+      a.f_th = I->f_th;
+      a.flags = I->flags;
+      a.Vn32_copy = (j == 1 && s >= 2) ? I->Vn32 : nullptr;
+      a.V32m1 = I->Vhi[bm1];
+      a.Vlo_m1 = I->Vlo[bm1];
+      a.Vhi_m2 = j >= 2 ? I->Vhi[bm2] : nullptr;
+      a.Vlo_m2 = j >= 2 ? I->Vlo[bm2] : nullptr;
+      a.V32out = I->Vhi[bo];
+      a.Vlo_out = I->Vlo[bo];
+      a.D1 = I->D[0];
+      a.LV = I->LV;
+      a.f_nu = I->o_nu[j];
+      a.f_kappa = I->o_kappa[j];
+      a.f_mudt = I->o_mudt[j];
+      a.f_inv_eta = I->f_inv_eta;
+      a.f_cm = I->f_cm;
+      a.f_mu1 = I->f_mu1;
+      a.f_mu1eta = I->f_mu1eta;
+      a.f_eta = I->f_eta;
+      const bool has_m2 = j >= 2;
+      switch (I->model) {
+        case 0: batch_stage_rows<ModelNone<float>>(a, I->ell, r0, r1, has_m2); break;
+        case 1: batch_stage_rows<ModelPassive<float>>(a, I->ell, r0, r1, has_m2); break;
+        case 2: batch_stage_rows<ModelHH<float>>(a, I->ell, r0, r1, has_m2); break;
+        default: batch_stage_rows<ModelTTP06<float>>(a, I->ell, r0, r1, has_m2); break;
+      }
+    } else {
+      InnerArgs b;
+      b.n = I->n;
+      b.F = I->F;
+      b.last = (k == m) ? 1 : 0;
+      b.final_stage = (j == s && k == m) ? 1 : 0;
+      b.Vn32 = Vn32;
+      b.act = act;
+      b.t_n = I->t;
+      b.dt = I->dt;
+      b.f_th = I->f_th;
+      b.flags = I->flags;
+      b.d1 = I->D[(k - 2) % 3];
+      b.d2 = (k == 2) ? nullptr : I->D[(k - 3) % 3];
+      b.dk = I->D[(k - 1) % 3];
+      b.LV = I->LV;
+      b.V32out = I->Vhi[bo];
+      b.Vhi1 = I->Vhi[bm1];
+      b.Vlo1 = I->Vlo[bm1];
+      b.Vhi2 = j >= 2 ? I->Vhi[bm2] : nullptr;
+      b.Vlo2 = j >= 2 ? I->Vlo[bm2] : nullptr;
+      b.Vlo_out = I->Vlo[bo];
+      b.f_nu = I->i_nu[k];
+      b.f_kappa = I->i_kappa[k];
+      b.f_mueta = I->i_mueta[k];
+      b.f_inv_eta = I->f_inv_eta;
+      b.f_okappa = I->o_kappa[j];
+      b.f_omu_dt = I->o_mudt[j];
+      for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) inner_node_mixed<true>(b, I->ell, i);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      cuda::atomic_ref<unsigned int, cuda::thread_scope_device> cnt(c.done[ii * kBatchMaxPhases + p]);
+      const unsigned int prev = cnt.fetch_add(1u, cuda::memory_order_acq_rel);
+      // the last tile of the last phase advances the instance: y_{n+1} = g_s
+      if (p == I->P - 1 && prev + 1 == (unsigned int)I->ntiles && !c.dry) {
+        I->cur = (cur + s) % 3;
+        I->t = I->t + I->dt;
+        I->steps = I->steps + 1;
+      }
+    }
+  }
+}
+
+void launch_batch_step(const BatchCtl& c, int grid, int block, cudaStream_t st) {
+  if (block == 256) batch_step_kernel<256><<<grid, 256, 0, st>>>(c);
+  else batch_step_kernel<128><<<grid, 128, 0, st>>>(c);
+}
+
+int batch_blocks_per_sm(int block) {
+  int nb = 0;
+  if (block == 256)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_step_kernel<256>, 256, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_step_kernel<128>, 128, 0);
+  return nb;
+}
+
+}  // namespace emrkc

@@ -1,0 +1,568 @@
+// Host runtime of the batched persistent step (emrkc_batch_* in emrkc.h).
+//
+// Each instance is an ordinary mixed-precision solver (it owns its buffers);
+// the batch keeps a device table of the instances (BatchInst), a phase-major
+// work list and per-instance phase counters, and replays
+//   memset(done) -> memset(ticket) -> persistent kernel
+// as one CUDA graph per step.  The plan (stage counts, coefficients, work
+// list) is rebuilt when instances join or leave or dt changes; instance time
+// and buffer rotation advance on the device and are mirrored on the host.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "emrkc.h"
+#include "launch.h"
+#include "solver_internal.h"
+
+using namespace emrkc;
+
+namespace {
+
+thread_local std::string g_batch_create_error;
+
+struct Member {
+  int id = 0;
+  emrkc_solver* s = nullptr;
+  bool rho_ready = false;
+  int S = 0, M = 0;
+};
+
+}  // namespace
+
+struct emrkc_batch {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  emrkc_options opt{};
+  std::vector<Member> members;
+  int next_id = 1;
+  bool dirty = true;
+  double plan_dt = -1.0;
+  std::vector<BatchInst> h_inst;
+  BatchInst* d_inst = nullptr;
+  size_t inst_cap = 0;
+  uint64_t* d_items = nullptr;
+  size_t items_cap = 0;
+  unsigned int n_items = 0;
+  unsigned int* d_ticket = nullptr;
+  unsigned int* d_done = nullptr;
+  size_t done_cap = 0;
+  int* d_err = nullptr;
+  int tile = 1024, block = 128, grid = 0;
+  long long spin_limit = 1 << 24;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches = 0;
+  std::string err;
+
+  int fail(int code, const std::string& m) {
+    err = m;
+    return code;
+  }
+  int cuda_fail(cudaError_t e, const char* what) {
+    err = std::string(what) + ": " + cudaGetErrorString(e);
+    return EMRKC_ERR_CUDA;
+  }
+  Member* find(int id) {
+    for (auto& m : members)
+      if (m.id == id) return &m;
+    return nullptr;
+  }
+  void drop_graph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+  }
+};
+
+namespace {
+
+template <class T>
+cudaError_t grow(T** p, size_t* cap, size_t need) {
+  if (need <= *cap && *p) return cudaSuccess;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  size_t c = std::max<size_t>(need, 1);
+  c = c + c / 4;
+  cudaError_t e = cudaMalloc((void**)p, c * sizeof(T));
+  *cap = (e == cudaSuccess) ? c : 0;
+  return e;
+}
+
+BatchCtl make_ctl(emrkc_batch* b, int dry) {
+  BatchCtl c;
+  c.inst = b->d_inst;
+  c.items = b->d_items;
+  c.n_items = b->n_items;
+  c.tile = b->tile;
+  c.ticket = b->d_ticket;
+  c.done = b->d_done;
+  c.err = b->d_err;
+  c.dry = dry;
+  c.spin_limit = b->spin_limit;
+  return c;
+}
+
+// Fill the device table entry of one instance for step size dt.
+int fill_inst(emrkc_batch* b, Member& mb, double dt, BatchInst* I) {
+  emrkc_solver* s = mb.s;
+  double rhoF, rhoS;
+  if (s->opt.rho_every == EMRKC_RHO_FIXED) {
+    rhoF = s->opt.rho_F;
+    rhoS = s->opt.rho_S;
+  } else {
+    if (!mb.rho_ready) {
+      int rc = solver_update_rho(s);
+      if (rc) return b->fail(rc, std::string("power iteration: ") + s->err);
+      mb.rho_ready = true;
+    }
+    rhoF = s->opt.safety * s->rhoF_raw;
+    rhoS = std::max(s->opt.safety * s->rhoS_raw, s->opt.rho_S_min);
+  }
+  double l_s = 0.0;
+  const int S = stages_for(dt, rhoS, s->opt.eps, &l_s);
+  const double eta = 2.0 * dt / l_s;
+  const int Mi = stages_for(eta, rhoF, s->opt.eps, nullptr);
+  if (S > kBatchMaxStages || Mi > kBatchMaxStages || S * Mi > kBatchMaxPhases)
+    return b->fail(EMRKC_ERR_ARG, "stage counts beyond the batch limits (s, m <= 32, s*m <= 64)");
+  const Coeffs& co = s->coeffs(S);
+  const Coeffs& ci = s->coeffs(Mi);
+  *I = BatchInst();
+  I->model = s->model;
+  I->s = S;
+  I->m = Mi;
+  I->P = S * Mi;
+  I->cur = s->cur;
+  I->n = s->n;
+  I->ld = s->ld;
+  I->ntiles = (int)((s->n + b->tile - 1) / b->tile);
+  for (int k = 0; k < 3; ++k) {
+    I->Vhi[k] = s->d_V32[k];
+    I->Vlo[k] = s->d_Vlo[k];
+    I->Z[k] = static_cast<float*>(s->d_Z[k]);
+    I->D[k] = s->d_D[k];
+  }
+  I->LV = s->d_LV;
+  I->F = static_cast<float*>(s->d_F);
+  I->Vn32 = s->d_Vn32;
+  I->mask = s->d_mask;
+  I->act = s->act_on ? s->d_act : nullptr;
+  I->flags = s->d_flags;
+  I->ell = s->ell;
+  I->t = s->t;
+  I->dt = dt;
+  I->amp = s->amp;
+  I->t_on = s->t_on;
+  I->t_off = s->t_off;
+  I->steps = s->steps;
+  I->f_th = (float)s->opt.act_threshold;
+  I->f_inv_Cm = (float)(1.0 / s->Cm);
+  I->f_eta = (float)eta;
+  I->f_inv_eta = (float)(1.0 / eta);
+  I->f_cm = (float)ci.c[Mi];
+  I->f_mu1 = (float)ci.mu[1];
+  I->f_mu1eta = (float)(ci.mu[1] * eta);
+  for (int j = 0; j <= S; ++j) {
+    I->o_c[j] = co.c[j];
+    I->o_nu[j] = j >= 2 ? (float)co.nu[j] : 1.0f;
+    I->o_kappa[j] = j >= 2 ? (float)co.kappa[j] : 0.0f;
+    I->o_mudt[j] = j >= 1 ? (float)(co.mu[j] * dt) : 0.0f;
+  }
+  for (int k = 0; k <= Mi; ++k) {
+    I->i_nu[k] = (float)ci.nu[k];
+    I->i_kappa[k] = (float)ci.kappa[k];
+    I->i_mueta[k] = (float)(ci.mu[k] * eta);
+  }
+  mb.S = S;
+  mb.M = Mi;
+  return EMRKC_OK;
+}
+
+int rebuild(emrkc_batch* b, double dt) {
+  b->drop_graph();
+  const size_t ni = b->members.size();
+  b->h_inst.assign(ni, BatchInst());
+  int maxP = 0;
+  for (size_t i = 0; i < ni; ++i) {
+    int rc = fill_inst(b, b->members[i], dt, &b->h_inst[i]);
+    if (rc) return rc;
+    maxP = std::max(maxP, b->h_inst[i].P);
+  }
+  std::vector<uint64_t> items;
+  for (int p = 0; p < maxP; ++p)
+    for (size_t i = 0; i < ni; ++i)
+      if (p < b->h_inst[i].P)
+        for (int t = 0; t < b->h_inst[i].ntiles; ++t) items.push_back(batch_item((int)i, p, t));
+  if (items.size() >= 0xffffffffull) return b->fail(EMRKC_ERR_ARG, "too many work items");
+  b->n_items = (unsigned int)items.size();
+  cudaError_t e;
+  if ((e = grow(&b->d_inst, &b->inst_cap, ni)) != cudaSuccess) return b->fail(EMRKC_ERR_OOM, "batch table");
+  if ((e = grow(&b->d_items, &b->items_cap, items.size())) != cudaSuccess) return b->fail(EMRKC_ERR_OOM, "batch items");
+  if ((e = grow(&b->d_done, &b->done_cap, std::max<size_t>(ni, 1) * kBatchMaxPhases)) != cudaSuccess)
+    return b->fail(EMRKC_ERR_OOM, "batch counters");
+  if (ni) e = cudaMemcpyAsync(b->d_inst, b->h_inst.data(), ni * sizeof(BatchInst), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess && !items.empty())
+    e = cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return b->cuda_fail(e, "batch plan upload");
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+  const int per_sm = std::max(1, batch_blocks_per_sm(b->block));
+  b->grid = std::max(1, sms * per_sm);
+  b->plan_dt = dt;
+  b->dirty = false;
+  return EMRKC_OK;
+}
+
+// Enqueue one step: counters reset + persistent launch (as a graph if enabled).
+int enqueue_step(emrkc_batch* b, int dry) {
+  const size_t ni = b->members.size();
+  if (ni == 0 || b->n_items == 0) return EMRKC_OK;
+  cudaError_t e;
+  if (!dry && b->opt.use_graphs) {
+    if (!b->exec) {
+      e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return b->cuda_fail(e, "graph capture");
+      cudaMemsetAsync(b->d_done, 0, ni * kBatchMaxPhases * sizeof(unsigned int), b->stream);
+      cudaMemsetAsync(b->d_ticket, 0, sizeof(unsigned int), b->stream);
+      launch_batch_step(make_ctl(b, 0), b->grid, b->block, b->stream);
+      e = cudaStreamEndCapture(b->stream, &b->graph);
+      if (e != cudaSuccess) return b->cuda_fail(e, "graph capture");
+      e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+      if (e != cudaSuccess) return b->cuda_fail(e, "graph instantiation");
+    }
+    e = cudaGraphLaunch(b->exec, b->stream);
+    if (e != cudaSuccess) return b->cuda_fail(e, "graph launch");
+  } else {
+    cudaMemsetAsync(b->d_done, 0, ni * kBatchMaxPhases * sizeof(unsigned int), b->stream);
+    cudaMemsetAsync(b->d_ticket, 0, sizeof(unsigned int), b->stream);
+    launch_batch_step(make_ctl(b, dry), b->grid, b->block, b->stream);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return b->cuda_fail(e, "batch launch");
+  }
+  ++b->launches;
+  return EMRKC_OK;
+}
+
+int64_t solver_bytes(const emrkc_solver* s) {
+  const int64_t ld = s->ld, N = s->N;
+  int64_t bytes = 0;
+  bytes += 3 * ld * 8 + 3 * std::max<int64_t>(N - 1, 1) * ld * (int64_t)s->zsize + 3 * ld * 8;  // V, z, U
+  bytes += ld * (int64_t)s->rsize;                                                                // F
+  bytes += 2 * ld * 8 + 3 * N * ld * 8;                                                           // power iteration
+  bytes += 2 * ld * 8 + std::max<int64_t>(N - 1, 1) * ld * 8 + 64 * 8 + 16;                       // act, Vn, tmp, rest, flags
+  if (s->precision == EMRKC_PREC_MIXED) bytes += 10 * ld * 4;                                     // V hi/lo, delta, LV, Vn32
+  bytes += s->mat_slots * (4 + (s->precision == EMRKC_PREC_MIXED ? 4 : 8)) + (s->ell.n_slices + 1) * 12;
+  if (s->d_mask) bytes += s->n;
+  return bytes;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t emrkc_instance_bytes(int64_t n, double nnz_per_row, int model) {
+  const int N = emrkc_num_vars(model);
+  if (N < 1 || n <= 0) return -1;
+  const int64_t ld = (n + 63) / 64 * 64;
+  int64_t bytes = 3 * ld * 8 + 3 * std::max(N - 1, 1) * ld * 4 + 3 * ld * 8 + ld * 4;
+  bytes += 2 * ld * 8 + 3 * (int64_t)N * ld * 8;
+  bytes += 2 * ld * 8 + std::max(N - 1, 1) * ld * 8 + 64 * 8 + 16;
+  bytes += 10 * ld * 4;
+  bytes += (int64_t)std::ceil(nnz_per_row * (double)ld) * 8 + (ld / 32 + 1) * 12 + n;
+  return bytes;
+}
+
+int emrkc_batch_create(const emrkc_options* opt, emrkc_batch** out) {
+  if (!out) {
+    g_batch_create_error = "out is NULL";
+    return EMRKC_ERR_ARG;
+  }
+  *out = nullptr;
+  emrkc_options o;
+  if (opt) o = *opt;
+  else emrkc_default_options(&o);
+  if (o.rho_every != EMRKC_RHO_ONCE && o.rho_every != EMRKC_RHO_FIXED) {
+    g_batch_create_error = "a batch supports the rho policies ONCE and FIXED";
+    return EMRKC_ERR_ARG;
+  }
+  o.precision = EMRKC_PREC_MIXED;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || o.device < 0 || o.device >= ndev) {
+    g_batch_create_error = "no usable CUDA device";
+    return EMRKC_ERR_CUDA;
+  }
+  auto* b = new emrkc_batch();
+  b->opt = o;
+  b->device = o.device;
+  cudaSetDevice(b->device);
+  if (o.cuda_stream) {
+    b->stream = (cudaStream_t)o.cuda_stream;
+  } else {
+    if ((e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+      g_batch_create_error = "stream creation failed";
+      delete b;
+      return EMRKC_ERR_CUDA;
+    }
+    b->own_stream = true;
+  }
+  b->opt.cuda_stream = b->stream;
+  if (cudaMalloc(&b->d_ticket, sizeof(unsigned int)) != cudaSuccess || cudaMalloc(&b->d_err, sizeof(int)) != cudaSuccess) {
+    g_batch_create_error = "device allocation failed";
+    emrkc_batch_destroy(b);
+    return EMRKC_ERR_OOM;
+  }
+  cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
+  cudaMemsetAsync(b->d_ticket, 0, sizeof(unsigned int), b->stream);
+  cudaStreamSynchronize(b->stream);
+  *out = b;
+  return EMRKC_OK;
+}
+
+int emrkc_batch_add(emrkc_batch* b, const emrkc_matrix* mat, const emrkc_tissue* tissue, int model,
+                    const emrkc_stimulus* stim, const emrkc_options* inst_opt, int* id_out) {
+  if (!b) return EMRKC_ERR_ARG;
+  cudaSetDevice(b->device);
+  emrkc_options o = b->opt;
+  if (inst_opt) {
+    o = *inst_opt;
+    o.precision = EMRKC_PREC_MIXED;
+    o.cuda_stream = b->stream;
+    o.device = b->device;
+    o.profile = 0;
+  }
+  if (o.rho_every != EMRKC_RHO_ONCE && o.rho_every != EMRKC_RHO_FIXED)
+    return b->fail(EMRKC_ERR_ARG, "a batched instance supports the rho policies ONCE and FIXED");
+  emrkc_solver* s = nullptr;
+  int rc = emrkc_create(mat, tissue, model, stim, &o, &s);
+  if (rc) return b->fail(rc, std::string("instance: ") + emrkc_last_error(nullptr));
+  Member mb;
+  mb.id = b->next_id++;
+  mb.s = s;
+  b->members.push_back(mb);
+  b->dirty = true;
+  if (id_out) *id_out = mb.id;
+  return EMRKC_OK;
+}
+
+int emrkc_batch_remove(emrkc_batch* b, int id) {
+  if (!b) return EMRKC_ERR_ARG;
+  cudaSetDevice(b->device);
+  for (size_t i = 0; i < b->members.size(); ++i) {
+    if (b->members[i].id == id) {
+      cudaStreamSynchronize(b->stream);
+      emrkc_destroy(b->members[i].s);
+      b->members.erase(b->members.begin() + (long)i);
+      b->dirty = true;
+      return EMRKC_OK;
+    }
+  }
+  return b->fail(EMRKC_ERR_ARG, "unknown instance id");
+}
+
+int emrkc_batch_step(emrkc_batch* b, double dt) {
+  if (!b) return EMRKC_ERR_ARG;
+  if (!(dt > 0) || !std::isfinite(dt)) return b->fail(EMRKC_ERR_ARG, "dt must be positive and finite");
+  cudaSetDevice(b->device);
+  if (b->dirty || dt != b->plan_dt) {
+    int rc = rebuild(b, dt);
+    if (rc) return rc;
+  }
+  int rc = enqueue_step(b, 0);
+  if (rc) return rc;
+  for (size_t i = 0; i < b->members.size(); ++i) {
+    Member& mb = b->members[i];
+    emrkc_solver* s = mb.s;
+    s->cur = (s->cur + mb.S) % 3;
+    s->t += dt;
+    s->steps += 1;
+    s->last_s = mb.S;
+    s->last_m = mb.M;
+    BatchInst& I = b->h_inst[i];
+    I.cur = s->cur;
+    I.t = s->t;
+    I.steps = s->steps;
+  }
+  return EMRKC_OK;
+}
+
+int emrkc_batch_sync(emrkc_batch* b) {
+  if (!b) return EMRKC_ERR_ARG;
+  cudaSetDevice(b->device);
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return b->cuda_fail(e, "stream synchronisation");
+  int err = 0;
+  e = cudaMemcpy(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return b->cuda_fail(e, "error flag");
+  if (err) return b->fail(EMRKC_ERR_TIMEOUT, "a dependency wait of the persistent kernel gave up");
+  for (auto& mb : b->members) {
+    int rc = emrkc_sync(mb.s);
+    if (rc == EMRKC_ERR_NONFINITE) return b->fail(rc, "instance " + std::to_string(mb.id) + ": non-finite V");
+    if (rc) return b->fail(rc, mb.s->err);
+  }
+  return EMRKC_OK;
+}
+
+int emrkc_batch_get_state(emrkc_batch* b, int id, int var, double* host_out, int64_t len) {
+  if (!b) return EMRKC_ERR_ARG;
+  Member* mb = b->find(id);
+  if (!mb) return b->fail(EMRKC_ERR_ARG, "unknown instance id");
+  int rc = emrkc_get_state(mb->s, var, host_out, len);
+  if (rc) return b->fail(rc, mb->s->err);
+  return EMRKC_OK;
+}
+
+int emrkc_batch_set_state(emrkc_batch* b, int id, int var, const double* host_in, int64_t len) {
+  if (!b) return EMRKC_ERR_ARG;
+  Member* mb = b->find(id);
+  if (!mb) return b->fail(EMRKC_ERR_ARG, "unknown instance id");
+  int rc = emrkc_set_state(mb->s, var, host_in, len);
+  if (rc) return b->fail(rc, mb->s->err);
+  return EMRKC_OK;
+}
+
+int emrkc_batch_get_activation_times(emrkc_batch* b, int id, double* host_out, int64_t n) {
+  if (!b) return EMRKC_ERR_ARG;
+  Member* mb = b->find(id);
+  if (!mb) return b->fail(EMRKC_ERR_ARG, "unknown instance id");
+  int rc = emrkc_get_activation_times(mb->s, host_out, n);
+  if (rc) return b->fail(rc, mb->s->err);
+  return EMRKC_OK;
+}
+
+int emrkc_batch_get_info(emrkc_batch* b, int id, emrkc_batch_info* out) {
+  if (!b || !out) return EMRKC_ERR_ARG;
+  Member* mb = b->find(id);
+  if (!mb) return b->fail(EMRKC_ERR_ARG, "unknown instance id");
+  out->n = mb->s->n;
+  out->N = mb->s->N;
+  out->model = mb->s->model;
+  out->s = mb->S;
+  out->m = mb->M;
+  out->t = mb->s->t;
+  out->steps = mb->s->steps;
+  out->device_bytes = solver_bytes(mb->s);
+  return EMRKC_OK;
+}
+
+int emrkc_batch_get_stats(emrkc_batch* b, emrkc_batch_stats* out) {
+  if (!b || !out) return EMRKC_ERR_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->instances = (int)b->members.size();
+  for (auto& mb : b->members) {
+    out->total_nodes += mb.s->n;
+    out->device_bytes += solver_bytes(mb.s);
+  }
+  out->device_bytes += (int64_t)(b->inst_cap * sizeof(BatchInst) + b->items_cap * 8 + b->done_cap * 4 + 8);
+  out->items = b->n_items;
+  out->tile = b->tile;
+  out->block = b->block;
+  out->grid = b->grid;
+  out->launches = b->launches;
+  return EMRKC_OK;
+}
+
+int emrkc_batch_set_config(emrkc_batch* b, int tile, int block) {
+  if (!b) return EMRKC_ERR_ARG;
+  if (tile < 256 || tile > 8192 || (tile & (tile - 1)) != 0 || (block != 128 && block != 256))
+    return b->fail(EMRKC_ERR_ARG, "tile must be a power of two in [256, 8192] and block 128 or 256");
+  if (tile != b->tile || block != b->block) {
+    b->tile = tile;
+    b->block = block;
+    b->dirty = true;
+  }
+  return EMRKC_OK;
+}
+
+int emrkc_batch_autotune(emrkc_batch* b, double dt, int reps, int* tile_out, int* block_out, double* ms_out) {
+  if (!b) return EMRKC_ERR_ARG;
+  if (!(dt > 0) || reps < 1) return b->fail(EMRKC_ERR_ARG, "dt > 0 and reps >= 1 required");
+  cudaSetDevice(b->device);
+  if (b->members.empty()) return b->fail(EMRKC_ERR_STATE, "empty batch");
+  int rc = rebuild(b, dt);
+  if (rc) return rc;
+  for (auto& mb : b->members)
+    if (mb.S >= 3) return b->fail(EMRKC_ERR_STATE, "an instance has s >= 3: dry steps would overwrite its state");
+  const int tiles[] = {512, 1024, 2048, 4096};
+  const int blocks[] = {128, 256};
+  const int keep_tile = b->tile, keep_block = b->block;
+  int best_tile = keep_tile, best_block = keep_block;
+  double best = 1e300;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int tl : tiles) {
+    for (int bl : blocks) {
+      b->tile = tl;
+      b->block = bl;
+      if ((rc = rebuild(b, dt))) break;
+      if ((rc = enqueue_step(b, 1))) break;
+      cudaEventRecord(e0, b->stream);
+      for (int r = 0; r < reps && !rc; ++r) rc = enqueue_step(b, 1);
+      cudaEventRecord(e1, b->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      const double per = ms / reps;
+      if (per < best) {
+        best = per;
+        best_tile = tl;
+        best_block = bl;
+      }
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->tile = best_tile;
+  b->block = best_block;
+  b->dirty = true;
+  if (rc) {
+    b->tile = keep_tile;
+    b->block = keep_block;
+    return rc;
+  }
+  int err = 0;
+  cudaMemcpy(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (err) return b->fail(EMRKC_ERR_TIMEOUT, "a dependency wait gave up during autotuning");
+  if (tile_out) *tile_out = best_tile;
+  if (block_out) *block_out = best_block;
+  if (ms_out) *ms_out = best;
+  return EMRKC_OK;
+}
+
+int emrkc_batch_set_spin_limit(emrkc_batch* b, int64_t limit) {
+  if (!b) return EMRKC_ERR_ARG;
+  if (limit < 0) return b->fail(EMRKC_ERR_ARG, "limit must be >= 0");
+  b->spin_limit = limit;
+  b->drop_graph();
+  return EMRKC_OK;
+}
+
+const char* emrkc_batch_last_error(const emrkc_batch* b) {
+  if (!b) return g_batch_create_error.c_str();
+  return b->err.c_str();
+}
+
+void emrkc_batch_destroy(emrkc_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (auto& mb : b->members) emrkc_destroy(mb.s);
+  b->members.clear();
+  b->drop_graph();
+  void* ptrs[] = {b->d_inst, b->d_items, b->d_ticket, b->d_done, b->d_err};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+}  // extern "C"

@@ -30,15 +30,25 @@ __device__ __forceinline__ double ell_dot64(const Ell& A, int64_t i, const doubl
   return acc;
 }
 
+// Loads of data that may have been written earlier in the same launch by
+// another SM (the batched persistent kernel) go through L2 only (ld.cg): L1
+// is not coherent across SMs.  Single-step kernels use read-only loads.
+template <bool CG, typename T>
+__device__ __forceinline__ T ldm(const T* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return __ldg(p);
+}
+
 // Mixed: sum_{k != i} L_ik (x_k - x_i) in FP32 (row sums of L vanish, so
 // this equals (L x)_i; differences keep the FP32 sum well conditioned).
+template <bool CG = false>
 __device__ __forceinline__ float ell_diff32(const Ell& A, int64_t i, const float* __restrict__ x) {
   const int64_t b = i >> 5;
   const int w = __ldg(A.width + b);
   int64_t p = __ldg(A.slice_ptr + b) + (i & 31);
-  const float xi = __ldg(x + i);
+  const float xi = ldm<CG>(x + i);
   float acc = 0.0f;
-  for (int k = 0; k < w; ++k, p += 32) acc += __ldg(A.val32 + p) * (__ldg(x + __ldg(A.col + p)) - xi);
+  for (int k = 0; k < w; ++k, p += 32) acc += __ldg(A.val32 + p) * (ldm<CG>(x + __ldg(A.col + p)) - xi);
   return acc;
 }
 
@@ -157,21 +167,19 @@ __global__ void __launch_bounds__(128) stage_kernel_fp64(const StageArgs a, cons
 // exponentials and L V in FP32 (on the FP32 mirror of V); V itself is only
 // updated in FP64 (m == 1).  For m >= 2 the inner stages carry the FP32
 // increments delta_k = u_k - V_{j-1}; this kernel writes delta_1, L V and F.
-template <class Model, bool HAS_M2>
-__global__ void __launch_bounds__(128) stage_kernel_mixed(const StageArgs a, const Ell A) {
+template <class Model, bool HAS_M2, bool CG = false>
+__device__ __forceinline__ void stage_node_mixed(const StageArgs& a, const Ell& A, const int64_t i) {
   constexpr int NE = Model::NE, NS = Model::NS, NZ = NE + NS;
   using M = Math<float>;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
   const int64_t ld = a.ld;
   const float* __restrict__ Zm1 = static_cast<const float*>(a.Zm1);
   const float* __restrict__ Zm2 = static_cast<const float*>(a.Zm2);
   float* __restrict__ Zout = static_cast<float*>(a.Zout);
 
-  const float V = a.V32m1[i];
+  const float V = ldm<CG>(a.V32m1 + i);
   float z[NZ > 0 ? NZ : 1];
 #pragma unroll
-  for (int k = 0; k < NZ; ++k) z[k] = Zm1[k * ld + i];
+  for (int k = 0; k < NZ; ++k) z[k] = ldm<CG>(Zm1 + k * ld + i);
 
   float zE1[NE > 0 ? NE : 1];
   if constexpr (NE > 0) {
@@ -191,29 +199,36 @@ __global__ void __launch_bounds__(128) stage_kernel_mixed(const StageArgs a, con
     for (int k = 0; k < NZ; ++k) {
       const float fbar = (k < NE) ? (zE1[k < NE ? k : 0] - z[k]) * a.f_inv_eta : a.f_cm * gS[k >= NE ? k - NE : 0];
       float out;
-      if constexpr (HAS_M2) out = a.f_nu * z[k] + a.f_kappa * Zm2[k * ld + i] + a.f_mudt * fbar;
+      if constexpr (HAS_M2) out = a.f_nu * z[k] + a.f_kappa * ldm<CG>(Zm2 + k * ld + i) + a.f_mudt * fbar;
       else out = z[k] + a.f_mudt * fbar;
       Zout[k * ld + i] = out;
     }
   }
-  const float LV = ell_diff32(A, i, a.V32m1);
+  const float LV = ell_diff32<CG>(A, i, a.V32m1);
   if (a.Vn32_copy != nullptr) a.Vn32_copy[i] = V;
   if (a.m == 1) {
     // V_j = V_{j-1} + kappa (V_{j-2} - V_{j-1}) + mu dt f_bar  (nu + kappa = 1)
     const float fbarV = a.f_mu1 * (LV + F);
-    const float lo1 = a.Vlo_m1[i];
+    const float lo1 = ldm<CG>(a.Vlo_m1 + i);
     float inc = a.f_mudt * fbarV;
-    if constexpr (HAS_M2) inc += a.f_kappa * ((a.Vhi_m2[i] - V) + (a.Vlo_m2[i] - lo1));
+    if constexpr (HAS_M2) inc += a.f_kappa * ((ldm<CG>(a.Vhi_m2 + i) - V) + (ldm<CG>(a.Vlo_m2 + i) - lo1));
     float hi, lo;
     ff_add(V, lo1, inc, hi, lo);
     a.V32out[i] = hi;
     a.Vlo_out[i] = lo;
-    if (a.final_stage) step_epilogue_ff(i, a.Vn32[i], hi, a.act, a.t_n, a.dt, a.f_th, a.flags);
+    if (a.final_stage) step_epilogue_ff(i, ldm<CG>(a.Vn32 + i), hi, a.act, a.t_n, a.dt, a.f_th, a.flags);
   } else {
     a.D1[i] = a.f_mu1eta * (LV + F);
     a.LV[i] = LV;
     static_cast<float*>(a.F)[i] = F;
   }
+}
+
+template <class Model, bool HAS_M2>
+__global__ void __launch_bounds__(128) stage_kernel_mixed(const StageArgs a, const Ell A) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  stage_node_mixed<Model, HAS_M2, false>(a, A, i);
 }
 
 // Inner RKC stage k >= 2 (FP64 path), Algorithm 1 applied to f_u = f_F + frozen f_S.
@@ -240,25 +255,30 @@ static __global__ void __launch_bounds__(256) inner_kernel_fp64(const InnerArgs 
 // delta_k = nu'_k delta_{k-1} + kappa'_k delta_{k-2} + mu'_k eta (L V + L delta_{k-1} + F)
 // (nu'_k + kappa'_k = 1 makes this the u-recurrence shifted by V); the last
 // stage forms f_bar_V = delta_m / eta and updates the float-float V.
-static __global__ void __launch_bounds__(256) inner_kernel_mixed(const InnerArgs a, const Ell A) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
-  const float Ld = ell_diff32(A, i, a.d1);
-  const float F = static_cast<const float*>(a.F)[i];
-  float dk = a.f_nu * a.d1[i] + a.f_mueta * (a.LV[i] + Ld + F);
-  if (a.d2 != nullptr) dk += a.f_kappa * a.d2[i];
+template <bool CG = false>
+__device__ __forceinline__ void inner_node_mixed(const InnerArgs& a, const Ell& A, const int64_t i) {
+  const float Ld = ell_diff32<CG>(A, i, a.d1);
+  const float F = ldm<CG>(static_cast<const float*>(a.F) + i);
+  float dk = a.f_nu * ldm<CG>(a.d1 + i) + a.f_mueta * (ldm<CG>(a.LV + i) + Ld + F);
+  if (a.d2 != nullptr) dk += a.f_kappa * ldm<CG>(a.d2 + i);
   if (!a.last) {
     a.dk[i] = dk;
     return;
   }
-  const float hi1 = a.Vhi1[i], lo1 = a.Vlo1[i];
+  const float hi1 = ldm<CG>(a.Vhi1 + i), lo1 = ldm<CG>(a.Vlo1 + i);
   float inc = a.f_omu_dt * (dk * a.f_inv_eta);
-  if (a.Vhi2 != nullptr) inc += a.f_okappa * ((a.Vhi2[i] - hi1) + (a.Vlo2[i] - lo1));
+  if (a.Vhi2 != nullptr) inc += a.f_okappa * ((ldm<CG>(a.Vhi2 + i) - hi1) + (ldm<CG>(a.Vlo2 + i) - lo1));
   float hi, lo;
   ff_add(hi1, lo1, inc, hi, lo);
   a.V32out[i] = hi;
   a.Vlo_out[i] = lo;
-  if (a.final_stage) step_epilogue_ff(i, a.Vn32[i], hi, a.act, a.t_n, a.dt, a.f_th, a.flags);
+  if (a.final_stage) step_epilogue_ff(i, ldm<CG>(a.Vn32 + i), hi, a.act, a.t_n, a.dt, a.f_th, a.flags);
+}
+
+static __global__ void __launch_bounds__(256) inner_kernel_mixed(const InnerArgs a, const Ell A) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  inner_node_mixed<false>(a, A, i);
 }
 
 // ---------------------------------------------------------------------------

@@ -171,6 +171,57 @@ void launch_fill(double* x, int64_t count, double value, cudaStream_t st);
 void launch_fill_rows(void* z, int zsize, int64_t n, int64_t ld, int rows, const double* values,
                       cudaStream_t st);
 
+// ---- Batched persistent step (batch.cu, batch_host.cpp) -------------------
+constexpr int kBatchMaxStages = 32;  // s, m <= 32 for a batched instance
+constexpr int kBatchMaxPhases = 64;  // s * m <= 64
+
+// One instance of the batch as the persistent kernel sees it (device table).
+// All buffers belong to the instance's own mixed-precision solver.
+struct BatchInst {
+  int model = 0, s = 1, m = 1, P = 1;  // P = s * m phases per step
+  int cur = 0, ntiles = 0;
+  int64_t n = 0, ld = 0;
+  float* Vhi[3] = {nullptr, nullptr, nullptr};
+  float* Vlo[3] = {nullptr, nullptr, nullptr};
+  float* Z[3] = {nullptr, nullptr, nullptr};
+  float* D[3] = {nullptr, nullptr, nullptr};
+  float* LV = nullptr;
+  float* F = nullptr;
+  float* Vn32 = nullptr;
+  const uint8_t* mask = nullptr;
+  double* act = nullptr;
+  int* flags = nullptr;
+  Ell ell{};
+  double t = 0, dt = 0, amp = 0, t_on = 0, t_off = -1;
+  int64_t steps = 0;
+  float f_th = -20, f_inv_Cm = 1, f_eta = 0, f_inv_eta = 1, f_cm = 1, f_mu1 = 1, f_mu1eta = 0;
+  double o_c[kBatchMaxStages + 1];      // outer stage times c_j
+  float o_nu[kBatchMaxStages + 1];      // outer nu_j (1 for j = 1)
+  float o_kappa[kBatchMaxStages + 1];   // outer kappa_j (0 for j = 1)
+  float o_mudt[kBatchMaxStages + 1];    // outer mu_j dt
+  float i_nu[kBatchMaxStages + 1];      // inner nu'_k
+  float i_kappa[kBatchMaxStages + 1];   // inner kappa'_k
+  float i_mueta[kBatchMaxStages + 1];   // inner mu'_k eta
+};
+
+// Work item: (instance, phase, tile), phase-major order.
+struct BatchCtl {
+  BatchInst* inst = nullptr;
+  const uint64_t* items = nullptr;
+  unsigned int n_items = 0;
+  int tile = 1024;                 // nodes per work item
+  unsigned int* ticket = nullptr;  // next item to take
+  unsigned int* done = nullptr;    // [instance * kBatchMaxPhases + phase] completed tiles
+  int* err = nullptr;              // bit 1: a dependency wait gave up
+  long long spin_limit = 1 << 24;  // iterations of a dependency wait before giving up
+  int dry = 0;                     // 1: no bookkeeping, no activation writes (autotuning)
+};
+inline uint64_t batch_item(int inst, int phase, int tile) {
+  return ((uint64_t)(uint32_t)inst << 40) | ((uint64_t)(uint32_t)phase << 32) | (uint32_t)tile;
+}
+void launch_batch_step(const BatchCtl& c, int grid, int block, cudaStream_t st);
+int batch_blocks_per_sm(int block);
+
 // Allocation-free power iteration on f_F (noalloc.cu): static device scratch.
 int noalloc_scratch(int device, cudaStream_t st, ReduceScratch* out, const char** why);
 int noalloc_max_blocks();

@@ -20,6 +20,7 @@
 
 #include "emrkc.h"
 #include "launch.h"
+#include "solver_internal.h"
 
 using namespace emrkc;
 
@@ -27,195 +28,7 @@ namespace {
 
 thread_local std::string g_create_error;
 
-// ---- Algorithm 1 on the host (FP64) -----------------------------------------
-// get_stages: smallest s >= 1 with beta s^2 >= dt rho, beta = 2 - 4 eps / 3.
-int stages_for(double dt, double rho, double eps, double* l_s) {
-  const double beta = 2.0 - 4.0 * eps / 3.0;
-  double s_real = std::ceil(std::sqrt(dt * rho / beta));
-  int s = (s_real < 1.0 || !(s_real == s_real)) ? 1 : (int)s_real;
-  if (s < 1) s = 1;
-  if (l_s) *l_s = beta * (double)s * (double)s;
-  return s;
-}
-
-// get_coeffs: Chebyshev T_j(w0) by the three-term recurrence and
-// T_s'(w0) = s U_{s-1}(w0) with U by its own recurrence.
-struct Coeffs {
-  std::vector<double> mu, nu, kappa, c;
-};
-
-Coeffs make_coeffs(int s, double eps) {
-  Coeffs co;
-  co.mu.assign(s + 1, 0.0);
-  co.nu.assign(s + 1, 0.0);
-  co.kappa.assign(s + 1, 0.0);
-  co.c.assign(s + 1, 0.0);
-  const double w0 = 1.0 + eps / ((double)s * (double)s);
-  std::vector<double> T(s + 1), U(s + 1);
-  T[0] = 1.0;
-  U[0] = 1.0;
-  if (s >= 1) {
-    T[1] = w0;
-    U[1] = 2.0 * w0;
-  }
-  for (int j = 1; j < s; ++j) {
-    T[j + 1] = 2.0 * w0 * T[j] - T[j - 1];
-    U[j + 1] = 2.0 * w0 * U[j] - U[j - 1];
-  }
-  const double dTs = (double)s * U[s - 1];
-  const double w1 = T[s] / dTs;
-  co.mu[1] = w1 / w0;
-  co.c[1] = co.mu[1];
-  for (int j = 2; j <= s; ++j) {
-    // b_j = 1 / T_j(w0)
-    co.mu[j] = 2.0 * w1 * T[j - 1] / T[j];
-    co.nu[j] = 2.0 * w0 * T[j - 1] / T[j];
-    co.kappa[j] = -T[j - 2] / T[j];
-    co.c[j] = co.nu[j] * co.c[j - 1] + co.kappa[j] * co.c[j - 2] + co.mu[j];
-  }
-  return co;
-}
-
-
-// Rest states (Sec. 5: "provided by the ionic model's definition").
-std::vector<double> rest_state(int model) {
-  switch (model) {
-    case EMRKC_MODEL_NONE:
-      return {0.0};
-    case EMRKC_MODEL_PASSIVE:
-      return {0.0, 1.0, 1.0};
-    case EMRKC_MODEL_HH: {
-      // gates at z_inf(V_rest), rates at v = 0
-      const double am = 2.5 / std::expm1(2.5), bm = 4.0;
-      const double ah = 0.07, bh = 1.0 / (std::exp(3.0) + 1.0);
-      const double an = 0.1 * 1.0 / std::expm1(1.0), bn = 0.125;
-      return {-75.0, am / (am + bm), ah / (ah + bh), an / (an + bn)};
-    }
-    case EMRKC_MODEL_TTP06_EPI:
-      // V; m h j xr1 xr2 xs r s d f f2 fCass; Rbar Ki Nai Cai CaSR CaSS
-      return {-85.23, 0.00172, 0.7444,  0.7045, 0.00621, 0.4712, 0.0095,   2.42e-8, 0.999998, 3.373e-5,
-              0.7888, 0.9755,  0.9953,  0.9073, 136.89,  8.604,  0.000126, 3.64,    0.00036};
-    default:
-      return {};
-  }
-}
-
-struct Timing {
-  int cls;
-  cudaEvent_t a, b;
-};
-
 }  // namespace
-
-struct emrkc_solver {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  emrkc_options opt{};
-  int model = 0, N = 1, nE = 0, nS = 0, precision = 0;
-  size_t zsize = 8;   // bytes per stored z value
-  size_t rsize = 8;   // bytes per forcing value (compute type)
-  int64_t n = 0, ld = 0;
-  KernelSet ks{};
-  Ell ell{};
-  // device buffers
-  int64_t* d_slice_ptr = nullptr;
-  int32_t* d_width = nullptr;
-  int32_t* d_col = nullptr;
-  double* d_val = nullptr;
-  float* d_val32 = nullptr;
-  double* d_V[3] = {nullptr, nullptr, nullptr};
-  void* d_Z[3] = {nullptr, nullptr, nullptr};
-  double* d_U[3] = {nullptr, nullptr, nullptr};
-  float* d_V32[3] = {nullptr, nullptr, nullptr};  // mixed: hi part of V per state buffer
-  float* d_Vlo[3] = {nullptr, nullptr, nullptr};  // mixed: lo part of V (V = hi + lo)
-  float* d_Vn32 = nullptr;                         // mixed: hi of V_n when s >= 2
-  float* d_D[3] = {nullptr, nullptr, nullptr};    // mixed: inner increments delta_k
-  float* d_LV = nullptr;                          // mixed: L V_{j-1}
-  void* d_F = nullptr;
-  uint8_t* d_mask = nullptr;
-  double* d_vF = nullptr;
-  double* d_vF2 = nullptr;
-  double* d_vS = nullptr;
-  double* d_vS2 = nullptr;
-  double* d_fy = nullptr;
-  double* d_act = nullptr;
-  double* d_Vn = nullptr;
-  double* d_tmp = nullptr;
-  double* d_rest = nullptr;
-  int* d_flags = nullptr;
-  ReduceScratch rs{};
-  double* h_pin = nullptr;  // pinned: [0..7] results, [8] flags
-  int cur = 0;
-  double amp = 0, t_on = 0, t_off = -1, chi = 1, Cm = 1;
-  double rhoF_raw = 0, rhoS_raw = 0;
-  bool rho_done = false;
-  double t = 0;
-  int64_t steps = 0;
-  int last_s = 0, last_m = 0;
-  double last_eta = 0, last_rhoF = 0, last_rhoS = 0;
-  int itF = 0, itS = 0;
-  int64_t total_it = 0, launches = 0;
-  int64_t mat_entries = 0, mat_slots = 0;
-  bool act_on = false;
-  double phase_ms[EMRKC_NUM_PHASES] = {0};
-  int64_t phase_launches[EMRKC_NUM_PHASES] = {0};
-  std::vector<Timing> pending;
-  std::vector<cudaEvent_t> event_pool;
-  std::map<int, Coeffs> coeff_cache;
-  std::string err;
-
-  int fail(int code, const std::string& msg) {
-    err = msg;
-    return code;
-  }
-  int cuda_fail(cudaError_t e, const char* what) {
-    err = std::string(what) + ": " + cudaGetErrorString(e);
-    return EMRKC_ERR_CUDA;
-  }
-  const Coeffs& coeffs(int s) {
-    auto it = coeff_cache.find(s);
-    if (it == coeff_cache.end()) it = coeff_cache.emplace(s, make_coeffs(s, opt.eps)).first;
-    return it->second;
-  }
-  cudaEvent_t get_event() {
-    if (!event_pool.empty()) {
-      cudaEvent_t e = event_pool.back();
-      event_pool.pop_back();
-      return e;
-    }
-    cudaEvent_t e;
-    cudaEventCreate(&e);
-    return e;
-  }
-  // Bracket one kernel launch with events when profiling.
-  template <class Fn>
-  void launch(int cls, Fn&& fn) {
-    if (opt.profile) {
-      Timing tm{cls, get_event(), get_event()};
-      cudaEventRecord(tm.a, stream);
-      fn();
-      cudaEventRecord(tm.b, stream);
-      pending.push_back(tm);
-    } else {
-      fn();
-    }
-    ++launches;
-    ++phase_launches[cls];
-  }
-  void harvest() {
-    for (auto& tm : pending) {
-      float ms = 0.f;
-      cudaEventSynchronize(tm.b);
-      cudaEventElapsedTime(&ms, tm.a, tm.b);
-      phase_ms[tm.cls] += ms;
-      event_pool.push_back(tm.a);
-      event_pool.push_back(tm.b);
-    }
-    pending.clear();
-  }
-  void* zrow(int buf, int k) const { return (char*)d_Z[buf] + (size_t)k * ld * zsize; }
-};
 
 namespace {
 
@@ -394,7 +207,7 @@ int do_step(emrkc_solver* s, double dt) {
       s->rho_done = true;
     }
     rhoF = s->opt.safety * s->rhoF_raw;
-    rhoS = s->opt.safety * s->rhoS_raw;
+    rhoS = std::max(s->opt.safety * s->rhoS_raw, s->opt.rho_S_min);
   }
   double l_s = 0.0;
   const int S = stages_for(dt, rhoS, s->opt.eps, &l_s);
@@ -691,6 +504,16 @@ int state_copy(emrkc_solver* s, int var, double* buf, int64_t len, bool to_host,
 
 }  // namespace
 
+namespace emrkc {
+int solver_update_rho(emrkc_solver* s) {
+  int rc = power_F(s);
+  if (!rc) rc = power_S(s);
+  if (!rc) s->rho_done = true;
+  return rc;
+}
+void solver_materialise_V(emrkc_solver* s) { materialise_V(s); }
+}  // namespace emrkc
+
 extern "C" {
 
 int emrkc_default_options(emrkc_options* o) {
@@ -711,6 +534,7 @@ int emrkc_default_options(emrkc_options* o) {
   o->device = 0;
   o->profile = 0;
   o->use_graphs = 1;
+  o->rho_S_min = 0.0;
   return EMRKC_OK;
 }
 
@@ -760,6 +584,10 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
   if (o.rho_every < EMRKC_RHO_FIXED || !(o.eps > 0) || !(o.safety > 0) || !(o.pow_tol > 0) || !(o.pow_eps > 0) ||
       o.pow_max_iter < 1) {
     g_create_error = "options: invalid rho policy or power-iteration parameters";
+    return EMRKC_ERR_ARG;
+  }
+  if (!(o.rho_S_min >= 0) || !std::isfinite(o.rho_S_min)) {
+    g_create_error = "options: rho_S_min must be finite and >= 0";
     return EMRKC_ERR_ARG;
   }
   if (o.rho_every == EMRKC_RHO_FIXED && (!(o.rho_F >= 0) || !(o.rho_S >= 0))) {

@@ -1,0 +1,154 @@
+"""Batched persistent step: every instance's result equals its solo run.
+
+Uneven instances (HH and TTP06, 2-D and 3-D, different sizes and stage
+counts) share one persistent launch per step; each instance's state after K
+steps is compared with the same instance run alone by the single-instance
+mixed-precision path (same per-node arithmetic, so agreement is expected to
+the last bit; the assertion allows 1e-6 of the variable's scale).
+"""
+
+import numpy as np
+import pytest
+
+import paper_2401_01745_gb300 as pkg
+from workloads import make_workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    pkg.build()
+
+
+def _solo(w, steps, dt, **kw):
+    s = pkg.Solver.from_workload(w, precision=pkg.PREC_MIXED, **kw)
+    for _ in range(steps):
+        s.step(dt)
+    s.sync()
+    Y = s.get_state()
+    act = s.activation_times()
+    st = s.stats()
+    s.close()
+    return Y, act, (st["s"], st["m"])
+
+
+def _close(Y, Yref):
+    for k in range(Y.shape[0]):
+        scale = max(np.max(np.abs(Yref[k])), 1e-12)
+        assert np.max(np.abs(Y[k] - Yref[k])) <= 1e-6 * scale, f"variable {k}"
+
+
+WORKLOADS = [("square33x29_hh", 1.0 / 64), ("slab23x9x5_ttp", 0.01), ("slab41x13x7_ttp", 0.01),
+             ("slab19x11x9_hh", 0.01), ("square61x7_ttp", 0.005)]
+
+
+def test_batch_equals_solo_rho_once():
+    dt, steps = 0.02, 60
+    ws = [make_workload(n, h=h) for n, h in WORKLOADS]
+    b = pkg.Batch(rho_every=pkg.RHO_ONCE)
+    ids = [b.add_workload(w) for w in ws]
+    for _ in range(steps):
+        b.step(dt)
+    b.sync()
+    exact = 0
+    for iid, w in zip(ids, ws):
+        Y = b.get_state(iid)
+        Yref, aref, sm = _solo(w, steps, dt, rho_every=pkg.RHO_ONCE)
+        info = b.info(iid)
+        assert (info["s"], info["m"]) == sm
+        assert info["steps"] == steps and abs(info["t"] - steps * dt) < 1e-12
+        _close(Y, Yref)
+        a = b.activation_times(iid)
+        assert np.array_equal(np.isnan(a), np.isnan(aref))
+        exact += int(np.array_equal(Y, Yref))
+    st = b.stats()
+    assert st["instances"] == len(ws) and st["launches"] == steps
+    b.close()
+    print(f"bitwise-equal instances: {exact}/{len(ws)}")
+
+
+def test_batch_equals_solo_many_stages():
+    """Fixed rho gives s = 2, m = 3 for every instance: the phase chain of the
+    persistent kernel covers outer and inner three-term recurrences."""
+    dt, steps, rF, rS = 0.05, 30, 3000.0, 60.0
+    ws = [make_workload(n, h=h) for n, h in WORKLOADS[:3]]
+    b = pkg.Batch(rho_every=pkg.RHO_FIXED, rho_F=rF, rho_S=rS)
+    ids = [b.add_workload(w) for w in ws]
+    for _ in range(steps):
+        b.step(dt)
+    b.sync()
+    for iid, w in zip(ids, ws):
+        Yref, _, sm = _solo(w, steps, dt, rho_every=pkg.RHO_FIXED, rho_F=rF, rho_S=rS)
+        assert sm[0] >= 2 and sm[1] >= 3
+        assert (b.info(iid)["s"], b.info(iid)["m"]) == sm
+        _close(b.get_state(iid), Yref)
+    b.close()
+
+
+def test_continuous_batching_join_and_leave():
+    """An instance that joins after 10 steps and one that leaves after 20 both
+    match their solo runs for the steps they took."""
+    dt = 0.02
+    wa = make_workload("slab23x9x5_ttp", h=0.01)
+    wb = make_workload("square33x29_hh", h=1.0 / 64)
+    b = pkg.Batch()
+    ia = b.add_workload(wa)
+    for _ in range(10):
+        b.step(dt)
+    ib = b.add_workload(wb)
+    for _ in range(10):
+        b.step(dt)
+    b.sync()
+    Ya = b.get_state(ia)
+    b.remove(ia)
+    for _ in range(15):
+        b.step(dt)
+    b.sync()
+    Yb = b.get_state(ib)
+    _close(Ya, _solo(wa, 20, dt, rho_every=pkg.RHO_ONCE)[0])
+    _close(Yb, _solo(wb, 25, dt, rho_every=pkg.RHO_ONCE)[0])
+    assert b.info(ib)["steps"] == 25
+    with pytest.raises(pkg.EmrkcError):
+        b.info(ia)
+    b.close()
+
+
+def test_autotune_keeps_state():
+    dt = 0.05
+    b = pkg.Batch()
+    ids = [b.add_workload(make_workload(n, h=h)) for n, h in WORKLOADS[1:3]]
+    for _ in range(3):
+        b.step(dt)
+    b.sync()
+    before = [b.get_state(i) for i in ids]
+    tile, block, ms = b.autotune(dt, reps=2)
+    assert tile in (512, 1024, 2048, 4096) and block in (128, 256) and ms > 0
+    after = [b.get_state(i) for i in ids]
+    for x, y in zip(before, after):
+        np.testing.assert_array_equal(x, y)
+    st = b.stats()
+    b.step(dt)
+    b.sync()
+    assert b.stats()["tile"] == tile
+    b.close()
+
+
+def test_dependency_wait_timeout_is_reported():
+    """With a wait limit of 0 polls, an item whose dependency is not yet done
+    gives up at once: the kernel records the failure, every CTA returns, and
+    emrkc_batch_sync reports EMRKC_ERR_TIMEOUT (no device hang, no trap)."""
+    b = pkg.Batch()
+    b.add_workload(make_workload("slab101x41x21_ttp", h=0.01))  # s = 1, m = 2: two phases
+    b.set_config(256, 128)
+    b.set_spin_limit(0)
+    code = None
+    for _ in range(5):
+        try:
+            b.step(0.05)
+            b.sync()
+        except pkg.EmrkcError as e:
+            code = e.code
+            break
+    assert code == 5
+    b.close()

@@ -203,6 +203,29 @@ def test_full_size_square65_hh_parity():
     _assert_parity(Y, act, prob, ref)
 
 
+def test_full_size_square65_hh_parity_with_rho_S_bound():
+    """The same workload with rho_S bounded below by HH's known stiffness
+    (Table 2: 40, times 1.05): s = 2 throughout, the step stays stable at
+    dt = 0.05 ms and parity holds over the whole T = 20 ms."""
+    w = make_workload("square65_hh")
+    sol = pkg.Solver.from_workload(w, rho_every=1, rho_S_min=42.0)
+    log = []
+    for _ in range(w.steps):
+        sol.step(w.dt)
+        st = sol.stats()
+        log.append((st["s"], st["m"]))
+    sol.sync()
+    Y = sol.get_state()
+    act = sol.activation_times()
+    sol.close()
+    prob = Monodomain.from_workload(w)
+    ref = OracleRun(prob, rho_every=1, rho_S_min=42.0)
+    for _ in range(w.steps):
+        ref.step(w.dt)
+    assert log == [(l[0], l[1]) for l in ref.log] and set(log) == {(2, 1)}
+    _assert_parity(Y, act, prob, ref)
+
+
 def test_full_size_slab_ttp_parity_first_steps():
     """The 201 x 71 x 31 TTP06 slab (442,401 nodes) in the launch configuration of the
     benchmark, compared with the oracle over its first steps (rho every step)."""

@@ -148,3 +148,58 @@ def make_workload(name: str, **kw) -> Workload:
 
 
 WORKLOADS = ("square65_hh", "slab_ttp", "shell_ttp")
+
+
+def batched_specs(count: int = 256, seed: int = 3, n_min: float = 8e3, n_max: float = 5e5):
+    """Specifications of the batched workload (one dict per instance).
+
+    n_i = exp(U(ln n_min, ln n_max)); geometry by coin flip: 2-D square of
+    side round(sqrt(n)) nodes (h = 1/64 cm) or 3-D slab with node counts in
+    the ratio 20:7:3 (h = 0.01 cm); sigma_l ~ U(0.8, 2.0) mS/cm, anisotropy
+    sigma_l/sigma_t ~ U(4, 10), fibres along x; a stimulus patch (radius
+    0.1 cm, 50 uA/cm^2 for 2 ms) centred at a boundary node chosen uniformly;
+    ionic model HH or TTP06 by coin flip.  All draws come from SplitMix64 on
+    (seed, instance, field).
+    """
+    import math
+
+    from .fields import splitmix64, u01
+
+    def draw(i, f):
+        return float(u01(splitmix64(np.uint64(seed), np.uint64((i << 8) | f))))
+
+    out = []
+    for i in range(count):
+        n = math.exp(math.log(n_min) + draw(i, 0) * (math.log(n_max) - math.log(n_min)))
+        is3d = draw(i, 1) < 0.5
+        sig_l = 0.8 + 1.2 * draw(i, 2)
+        ratio = 4.0 + 6.0 * draw(i, 3)
+        model = MODEL_HH if draw(i, 4) < 0.5 else MODEL_TTP06
+        if is3d:
+            k = (n / 420.0) ** (1.0 / 3.0)
+            dims = (max(2, round(20 * k)), max(2, round(7 * k)), max(2, round(3 * k)))
+            h = 0.01
+        else:
+            side = max(2, round(math.sqrt(n)))
+            dims = (side, side)
+            h = 1.0 / 64
+        out.append(dict(index=i, dims=dims, h=h, sigma_l=sig_l, sigma_t=sig_l / ratio, model=model,
+                        u_site=draw(i, 5)))
+    return out
+
+
+def batched_workload(spec) -> Workload:
+    """Build the mesh and inputs of one batched instance from its spec."""
+    dims, h = spec["dims"], spec["h"]
+    if len(dims) == 2:
+        coords, cells = square_tri_mesh(dims[0], dims[1], (dims[0] - 1) * h, (dims[1] - 1) * h)
+        D = axis_D(cells.shape[0], (spec["sigma_l"], spec["sigma_t"]))
+    else:
+        coords, cells = slab_tet_mesh(*dims, *[(d - 1) * h for d in dims])
+        D = axis_D(cells.shape[0], (spec["sigma_l"], spec["sigma_t"], spec["sigma_t"]))
+    lo, hi = coords.min(axis=0), coords.max(axis=0)
+    boundary = np.nonzero(np.any((np.abs(coords - lo) < 1e-12) | (np.abs(coords - hi) < 1e-12), axis=1))[0]
+    site = boundary[min(int(spec["u_site"] * boundary.size), boundary.size - 1)]
+    mask = radius_mask(coords, coords[site], 0.1)
+    return Workload(f"batch{spec['index']}", coords, cells, D, spec["model"], mask,
+                    t_off=2.0, dt=0.05, T=50.0, rho_every=0)
