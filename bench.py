@@ -282,6 +282,111 @@ def run_batched(args):
     return 0
 
 
+def run_served(args):
+    """Served form: Poisson request stream, HBM-budget admission, continuous batching."""
+    import torch
+
+    import paper_2401_01745_gb300 as pkg
+    from paper_2401_01745_gb300.serve import MeshCache, Server
+    from workloads.configs import request_workload, served_requests
+
+    world, rank, local = _dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pkg.build()
+    reqs = served_requests(count=args.requests, rate=20.0, seed=4)
+    cache = MeshCache(request_workload)
+    t0 = time.perf_counter()
+    cache.prepare(reqs)
+    prep_s = time.perf_counter() - t0
+    stream = torch.cuda.Stream(device=dev)
+    budget = 150e9
+    runs = {}
+    with ClockSampler(local) as clk:
+        srv = Server(cache, budget, stream=stream.cuda_stream, device=local, keep_V=False)
+        srv.run(reqs)
+        runs["offered_20_per_s"] = srv.summary()
+        srv.close()
+        cap = runs["offered_20_per_s"]["node_timesteps_per_s"]
+        work = float(np.mean([r["n_target"] * r["steps"] for r in reqs]))
+        rate = 0.7 * cap / work
+        reqs2 = served_requests(count=args.requests, rate=rate, seed=4)
+        srv = Server(cache, budget, stream=stream.cuda_stream, device=local, keep_V=False)
+        srv.run(reqs2)
+        runs["sustainable_70pct"] = dict(srv.summary(), arrival_rate_per_s=rate)
+        srv.close()
+    head = runs["offered_20_per_s"]
+    out = {"metric": METRIC + "; p50/p99 solve latency", "value": head["node_timesteps_per_s"], "unit": UNIT,
+           "n_gpus": 1, "steps": None, "warmup": 0, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "p50_latency_s": head["p50_latency_s"], "p99_latency_s": head["p99_latency_s"],
+           "config": {"workload": f"served: {args.requests} requests, Poisson arrivals 20/s, n log-U(1e4, 2e6) "
+                                  "in 8 size classes, slab or shell, HH or TTP06, horizon U(20, 400) ms, "
+                                  "dt 0.05 ms, HBM budget 150 GB, continuous batching", "mesh_prep_s": prep_s,
+                      "offered_node_timesteps_per_s": 20.0 * work},
+           "runs": runs, "clocks": clk.summary()}
+    print(json.dumps(out))
+    return 0
+
+
+def run_shell(args):
+    """Ventricle-like shell (~4.2 M nodes): mixed vs plain FP64 over T = 100 ms."""
+    import torch
+
+    import paper_2401_01745_gb300 as pkg
+    from workloads import make_workload
+
+    world, rank, local = _dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pkg.build()
+    t0 = time.perf_counter()
+    w = make_workload("shell_ttp")
+    rp, col, K, M = pkg.assemble_p1(w.coords, w.cells, w.D)
+    setup_s = time.perf_counter() - t0
+    stream = torch.cuda.Stream(device=dev)
+    H = int(round(w.T / w.dt))
+    res = {}
+    with ClockSampler(local) as clk:
+        for name, prec in (("mixed", pkg.PREC_MIXED), ("fp64", pkg.PREC_FP64)):
+            sol = pkg.Solver(rp, col, K, M, chi=w.chi, Cm=w.Cm, model=w.model, mask=w.stim_mask,
+                             amplitude=w.stim_amp, t_on=w.t_on, t_off=w.t_off, precision=prec,
+                             rho_every=0, stream=stream.cuda_stream, device=local)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                for _ in range(H):
+                    sol.step(w.dt)
+                e1.record(stream)
+            sol.sync()
+            ms = e0.elapsed_time(e1)
+            st = sol.stats()
+            res[name] = dict(V=sol.get_state(var=0), act=sol.activation_times(), ms=ms, s=st["s"], m=st["m"])
+            sol.close()
+    Va, Vb = res["fp64"]["V"], res["mixed"]["V"]
+    ta, tb = res["fp64"]["act"], res["mixed"]["act"]
+    both = np.isfinite(ta) & np.isfinite(tb)
+    err = float(np.sqrt(np.sum(M * (Va - Vb) ** 2) / np.sum(M * Va * Va)))
+    vm = w.n * H / (res["mixed"]["ms"] / 1e3)
+    v64 = w.n * H / (res["fp64"]["ms"] / 1e3)
+    out = {"metric": METRIC, "value": vm, "unit": UNIT, "n_gpus": 1, "steps": H, "warmup": 0,
+           "ms_per_step": res["mixed"]["ms"] / H, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "shell: 32x362x362 structured box mapped onto a truncated prolate-"
+                                  "ellipsoidal shell, interior jitter +-20%, fibres +60 -> -60 deg, TTP06, "
+                                  "apical stimulus, dt 0.05 ms, T 100 ms, rho once at t = 0 (timed)",
+                      "nodes": w.n, "cells": int(w.cells.shape[0]), "entries_per_row": col.size / w.n,
+                      "s": res["mixed"]["s"], "m": res["mixed"]["m"], "setup_s": setup_s},
+           "fp64": {"value": v64, "unit": UNIT, "ms_per_step": res["fp64"]["ms"] / H, "dtype": "f64"},
+           "accuracy": {"rel_l2_err_V_vs_fp64": err, "T_ms": w.T,
+                        "max_activation_diff_ms": float(np.max(np.abs(ta[both] - tb[both]))) if both.any() else None,
+                        "activated_nodes": int(both.sum()),
+                        "activation_pattern_equal": bool(np.array_equal(np.isfinite(ta), np.isfinite(tb)))},
+           "headline_speedup_vs_fp64": vm / v64, "clocks": clk.summary()}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -298,11 +403,18 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="headline only (for profiler runs)")
     ap.add_argument("--batched", action="store_true", help="batched form: many instances per launch")
     ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--shell", action="store_true", help="ventricle-like shell, mixed vs FP64 over T = 100 ms")
+    ap.add_argument("--served", action="store_true", help="served form: request stream, p50/p99 latency")
+    ap.add_argument("--requests", type=int, default=100)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.shell:
+        return run_shell(args)
+    if args.served:
+        return run_served(args)
     if args.batched:
         if args.steps == 1000:
             args.steps = 100

@@ -108,6 +108,16 @@ def test_fp64_parity_large_dt_ttp_fixed_rho():
     _assert_parity(Y, act, prob, ref)
 
 
+def test_fp64_parity_shell_unstructured():
+    """Jittered ventricle-like shell (unstructured connectivity, ~14 entries
+    per row, rotating fibres): FP64 GPU vs oracle through the apical upstroke."""
+    w = make_workload("shell_ttp", nr=6, nuv=24)
+    w.stim_amp = 100.0
+    Y, act, log, st, prob, ref, rlog = _run_pair(w, 40, rho_every=1)
+    assert log == rlog
+    _assert_parity(Y, act, prob, ref)
+
+
 def test_fp64_parity_rho_once():
     w = make_workload("slab23x9x5_ttp", h=0.01)
     Y, act, log, st, prob, ref, rlog = _run_pair(w, 50, rho_every=pkg.RHO_ONCE)

@@ -76,7 +76,7 @@ def test_assembly_matches_oracle_structured(lib, name):
 
 
 def test_assembly_matches_oracle_shell(lib):
-    coords, cells = shell_tet_mesh(4, 10, 12, seed=9)
+    coords, cells = shell_tet_mesh(4, 8, seed=9)
     rng = np.random.default_rng(2)
     D = fibre_D(rng.normal(size=(cells.shape[0], 3)), 1.33, 0.18)
     rp, col, K, M = pkg.assemble_p1(coords, cells, D)

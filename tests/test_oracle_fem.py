@@ -105,7 +105,7 @@ def test_line_mesh():
 
 @pytest.fixture(scope="module")
 def small_shell():
-    coords, cells = shell_tet_mesh(4, 12, 16, seed=5)
+    coords, cells = shell_tet_mesh(4, 9, seed=5)
     rng = np.random.default_rng(3)
     a = rng.normal(size=(cells.shape[0], 3))
     D = fibre_D(a, 1.33, 0.18)

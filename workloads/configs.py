@@ -9,9 +9,12 @@ synthetic problems stand in for them:
                D = diag(1.33, 0.18, 0.18) mS/cm (fibres along x), TTP06 epi,
                50 uA/cm^2 for t <= 2 ms on the 0.15 cm corner cube, dt 0.05,
                T 50 ms (the 3-D cuboid of Sec. 5.3 at 0.1 mm).
-  shell_ttp    32 x 256 x 512 parametric prolate-ellipsoid shell (~4.2 M
-               nodes), fibre angle +60 deg (endo) -> -60 deg (epi), TTP06,
-               apical stimulus, dt 0.05, T 100 ms.
+  shell_ttp    32 x 362 x 362 structured box mapped onto a truncated prolate-
+               ellipsoidal shell (semi-axes 5/2.5 cm outer, 4.3/1.8 cm inner,
+               cut at z = 2 cm; ~4.2 M nodes, ~24 M Kuhn tets, interior nodes
+               jittered by +-20% of the local spacing), fibre angle +60 deg
+               (endo) -> -60 deg (epi), TTP06, apical stimulus, dt 0.05,
+               T 100 ms.
 
 Tissue constants follow Table 1 in centimetres: chi = 1400 /cm, Cm = 1 uF/cm^2.
 Ionic model ids: 0 none (pure diffusion), 1 passive test model, 2 Hodgkin-
@@ -80,7 +83,7 @@ def _slab(nx, ny, nz, lx, ly, lz, model, sig=(1.33, 0.18, 0.18), corner=0.15,
 def shell_fibres(coords, cells, param):
     """Cell fibre vectors: angle +60 deg at r=0 (endo) to -60 deg at r=1 (epi)
     in the (e_phi, e_theta) tangent plane, evaluated at the cell centroid."""
-    pr, pt, pph, rs_in, rl_in, thick, z_top, nt, nphi = param
+    pr, rs_in, rl_in, thick, z_top = param
     c = coords[cells].mean(axis=1)
     rc = pr[cells].mean(axis=1)
     phi = np.arctan2(c[:, 1], c[:, 0])
@@ -108,12 +111,11 @@ def make_workload(name: str, **kw) -> Workload:
         w = _slab(201, 71, 31, 2.0, 0.7, 0.3, MODEL_HH, name=name)
     elif name == "shell_ttp":
         nr = kw.pop("nr", 32)
-        nt = kw.pop("ntheta", 256)
-        nphi = kw.pop("nphi", 512)
-        coords, cells, param = shell_tet_mesh(nr, nt, nphi, return_param=True)
+        nuv = kw.pop("nuv", 362)
+        coords, cells, param = shell_tet_mesh(nr, nuv, return_param=True)
         a_l = shell_fibres(coords, cells, param)
         D = fibre_D(a_l, 1.33, 0.18)
-        rl_out = param[4] + param[5]
+        rl_out = param[2] + param[3]
         w = Workload(name, coords, cells, D, MODEL_TTP06,
                      radius_mask(coords, (0.0, 0.0, -rl_out), 0.3),
                      t_off=2.0, dt=0.05, T=100.0, rho_every=0)
@@ -203,3 +205,58 @@ def batched_workload(spec) -> Workload:
     mask = radius_mask(coords, coords[site], 0.1)
     return Workload(f"batch{spec['index']}", coords, cells, D, spec["model"], mask,
                     t_off=2.0, dt=0.05, T=50.0, rho_every=0)
+
+
+def served_requests(count: int = 100, rate: float = 20.0, seed: int = 4, n_min: float = 1e4,
+                    n_max: float = 2e6, horizon=(20.0, 400.0), size_classes: int = 8):
+    """Seeded request stream for the served form.
+
+    Poisson arrivals (exponential inter-arrival times of mean 1/rate s); each
+    request is a monodomain solve with n ~ log-U(n_min, n_max) nodes, rounded
+    to one of ``size_classes`` log-spaced size classes so that meshes can be
+    prepared once per class; geometry slab or shell and ionic model HH or
+    TTP06 by coin flips; horizon ~ U(horizon) ms at dt = 0.05 ms.
+    """
+    import math
+
+    from .fields import splitmix64, u01
+
+    def draw(i, f):
+        return float(u01(splitmix64(np.uint64(seed), np.uint64((i << 8) | f))))
+
+    classes = np.exp(np.linspace(math.log(n_min), math.log(n_max), size_classes))
+    t = 0.0
+    out = []
+    for i in range(count):
+        t += -math.log(max(1e-300, 1.0 - draw(i, 0))) / rate
+        n = math.exp(math.log(n_min) + draw(i, 1) * (math.log(n_max) - math.log(n_min)))
+        cls = int(np.argmin(np.abs(np.log(classes) - math.log(n))))
+        geom = "slab" if draw(i, 2) < 0.5 else "shell"
+        model = MODEL_HH if draw(i, 3) < 0.5 else MODEL_TTP06
+        hz = horizon[0] + (horizon[1] - horizon[0]) * draw(i, 4)
+        steps = max(1, int(round(hz / 0.05)))
+        out.append(dict(index=i, arrival=t, n_target=float(classes[cls]), size_class=cls, geometry=geom,
+                        model=model, steps=steps))
+    return out
+
+
+def request_workload(req, model=None) -> Workload:
+    """Mesh and inputs of one served request (same for every request of its
+    geometry and size class; the ionic model is the request's)."""
+    n = req["n_target"]
+    mid = req["model"] if model is None else model
+    if req["geometry"] == "slab":
+        k = (n / 420.0) ** (1.0 / 3.0)
+        dims = (max(2, round(20 * k)), max(2, round(7 * k)), max(2, round(3 * k)))
+        h = 0.01
+        coords, cells = slab_tet_mesh(*dims, *[(d - 1) * h for d in dims])
+        D = axis_D(cells.shape[0], (1.33, 0.18, 0.18))
+        mask = corner_mask(coords, 0.15)
+    else:
+        nuv = max(4, round((11.0 * n) ** (1.0 / 3.0)))
+        nr = max(3, round(n / (nuv * nuv)))
+        coords, cells, param = shell_tet_mesh(nr, nuv, return_param=True)
+        D = fibre_D(shell_fibres(coords, cells, param), 1.33, 0.18)
+        mask = radius_mask(coords, (0.0, 0.0, -(param[2] + param[3])), 0.3)
+    return Workload(f"req{req['index']}", coords, cells, D, mid, mask, t_off=2.0, dt=0.05,
+                    T=req["steps"] * 0.05, rho_every=0)

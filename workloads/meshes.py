@@ -100,98 +100,76 @@ def _signed_vol6(coords, cells):
     return np.einsum("ij,ij->i", e1, np.cross(e2, e3))
 
 
-def shell_tet_mesh(nr: int = 32, ntheta: int = 256, nphi: int = 512, *,
-                   rs_in: float = 1.8, rl_in: float = 4.3, thick: float = 0.7,
-                   z_top: float = 2.0, jitter: float = 0.2, seed: int = 2,
+def shell_tet_mesh(nr: int = 32, nuv: int = 362, *, rs_in: float = 1.8, rl_in: float = 4.3,
+                   thick: float = 0.7, z_top: float = 2.0, jitter: float = 0.2, seed: int = 2,
                    return_param: bool = False):
     """Truncated prolate-ellipsoidal shell ("ventricle-like"), Kuhn tets.
 
-    Parametric grid (r, theta, phi) in [0,1] x [theta_top(r), pi] x [0, 2pi):
+    A structured box grid (r, u, v) in [0,1] x [-1,1]^2 is mapped onto the shell
+    without a pole: the square (u, v) goes into the unit disk by the blended
+    elliptical map x = c u sqrt(1 - v^2/4), y = c v sqrt(1 - u^2/4),
+    c = sqrt(2/3) (corners on the unit circle, edge midpoints at radius c; a
+    map that puts the whole square boundary on the circle flattens the corner
+    cells).  The radius rho and angle phi give the polar angle
+    theta = pi - rho (pi - theta_top(r)) from the apex (theta = pi), with
+    theta_top(r) = arccos(z_top/Rl(r)), so the corners reach the plane
+    z = z_top and the rim dips below it between them; then
         x = Rs(r) sin(theta) cos(phi), y = Rs(r) sin(theta) sin(phi),
-        z = Rl(r) cos(theta),  Rs = rs_in + thick*r,  Rl = rl_in + thick*r,
-    with theta_top(r) = arccos(z_top / Rl(r)) (the base plane z = z_top).
-    The theta = pi ring of every r collapses to one apex node; tetrahedra with
-    a repeated vertex are dropped.  Interior nodes (not on r=0, r=1, the base
-    or the apex) are jittered by U(-jitter, jitter) of the local parametric
-    spacing in each parametric direction (seeded counter-based generator);
-    a node's jitter is halved while any of its tetrahedra inverts.
+        z = Rl(r) cos(theta),  Rs = rs_in + thick*r,  Rl = rl_in + thick*r.
+    Interior nodes (not on r = 0, r = 1 or the truncation rim) are jittered by
+    U(-jitter, jitter) of the local parametric spacing in each parametric
+    direction (seeded counter-based generator); a node's jitter is halved
+    while any of its tetrahedra inverts or degenerates.
     """
-    nt = ntheta
     r = np.linspace(0.0, 1.0, nr)
-    # node ids: rings j < nt-1 are full, j = nt-1 is the apex (one per r)
-    n_ring = (nt - 1) * nphi
-    n_nodes = nr * (n_ring + 1)
+    uv = np.linspace(-1.0, 1.0, nuv)
+    I, J, K = np.meshgrid(np.arange(nr), np.arange(nuv), np.arange(nuv), indexing="ij")
+    n_nodes = nr * nuv * nuv
 
     def nid(i, j, k):
-        i = np.asarray(i)
-        j = np.asarray(j)
-        k = np.asarray(k)
-        base = i * (n_ring + 1)
-        return np.where(j >= nt - 1, base + n_ring, base + j * nphi + k)
+        return (np.asarray(i) * nuv + np.asarray(j)) * nuv + np.asarray(k)
 
-    # parametric coordinates of every node (apex entries set separately)
-    I, J, K = np.meshgrid(np.arange(nr), np.arange(nt - 1), np.arange(nphi), indexing="ij")
-    rr = r[I].astype(np.float64)
-    tt = J.astype(np.float64)  # theta index (fractional after jitter)
-    pp = K.astype(np.float64)
-    ids = nid(I, J, K).ravel()
-    pr = np.empty(n_nodes)
-    pt = np.empty(n_nodes)
-    pph = np.empty(n_nodes)
-    pr[ids] = rr.ravel()
-    pt[ids] = tt.ravel()
-    pph[ids] = pp.ravel()
-    apex = np.arange(nr) * (n_ring + 1) + n_ring
-    pr[apex] = r
-    pt[apex] = nt - 1
-    pph[apex] = 0.0
+    pr = r[I].ravel().astype(np.float64)
+    pu = uv[J].ravel().astype(np.float64)
+    pv = uv[K].ravel().astype(np.float64)
+    interior = ((I > 0) & (I < nr - 1) & (J > 0) & (J < nuv - 1) & (K > 0) & (K < nuv - 1)).ravel()
+    cells = _kuhn_cells(nid, nr, nuv, nuv)
 
-    interior = np.zeros(n_nodes, dtype=bool)
-    inner_mask = (I > 0) & (I < nr - 1) & (J > 0)
-    interior[ids[inner_mask.ravel()]] = True
-
-    cells = _kuhn_cells(nid, nr, nt, nphi, wrap_k=True)
-    # drop degenerate tetrahedra (repeated vertex at the apex)
-    srt = np.sort(cells, axis=1)
-    keep = np.all(srt[:, 1:] != srt[:, :-1], axis=1)
-    cells = cells[keep]
-
-    def to_xyz(pr_, pt_, pph_):
+    def to_xyz(pr_, pu_, pv_):
+        pu_ = np.clip(pu_, -1.0, 1.0)
+        pv_ = np.clip(pv_, -1.0, 1.0)
+        c = np.sqrt(2.0 / 3.0)
+        xd = c * pu_ * np.sqrt(1.0 - 0.25 * pv_ * pv_)
+        yd = c * pv_ * np.sqrt(1.0 - 0.25 * pu_ * pu_)
+        rho = np.minimum(np.hypot(xd, yd), 1.0)
+        ph = np.arctan2(yd, xd)
         rs = rs_in + thick * pr_
         rl = rl_in + thick * pr_
         th_top = np.arccos(z_top / rl)
-        th = th_top + (np.pi - th_top) * (pt_ / (nt - 1))
-        ph = 2.0 * np.pi * pph_ / nphi
-        return np.stack([rs * np.sin(th) * np.cos(ph),
-                         rs * np.sin(th) * np.sin(ph),
-                         rl * np.cos(th)], axis=1)
+        th = np.pi - rho * (np.pi - th_top)
+        return np.stack([rs * np.sin(th) * np.cos(ph), rs * np.sin(th) * np.sin(ph), rl * np.cos(th)], axis=1)
 
-    xyz0 = to_xyz(pr, pt, pph)
-    xyz0[apex, 0] = 0.0
-    xyz0[apex, 1] = 0.0
-    sign0 = np.sign(_signed_vol6(xyz0, cells))
+    xyz0 = to_xyz(pr, pu, pv)
+    vol0 = _signed_vol6(xyz0, cells)
+    sign0 = np.sign(vol0)
     if np.any(sign0 == 0):
         raise RuntimeError("degenerate tetrahedron in the unjittered shell")
-
-    # seeded jitter: three counter streams, one per parametric direction
     idx = np.arange(n_nodes, dtype=np.uint64)
     scale = np.where(interior, jitter, 0.0)
-    jr = (u01(splitmix64(np.uint64(seed) * np.uint64(3) + np.uint64(0), idx)) * 2 - 1)
-    jt = (u01(splitmix64(np.uint64(seed) * np.uint64(3) + np.uint64(1), idx)) * 2 - 1)
-    jp = (u01(splitmix64(np.uint64(seed) * np.uint64(3) + np.uint64(2), idx)) * 2 - 1)
+    jr = u01(splitmix64(np.uint64(seed) * np.uint64(3) + np.uint64(0), idx)) * 2 - 1
+    ju = u01(splitmix64(np.uint64(seed) * np.uint64(3) + np.uint64(1), idx)) * 2 - 1
+    jv = u01(splitmix64(np.uint64(seed) * np.uint64(3) + np.uint64(2), idx)) * 2 - 1
     dr = 1.0 / (nr - 1)
+    duv = 2.0 / (nuv - 1)
     for _ in range(12):
-        xyz = to_xyz(pr + scale * jr * dr, pt + scale * jt, pph + scale * jp)
-        xyz[apex, 0] = 0.0
-        xyz[apex, 1] = 0.0
+        xyz = to_xyz(pr + scale * jr * dr, pu + scale * ju * duv, pv + scale * jv * duv)
         vol = _signed_vol6(xyz, cells)
-        bad = (np.sign(vol) != sign0) | (np.abs(vol) < 1e-3 * np.abs(_signed_vol6(xyz0, cells)))
+        bad = (np.sign(vol) != sign0) | (np.abs(vol) < 1e-2 * np.abs(vol0))
         if not np.any(bad):
             break
-        bad_nodes = np.unique(cells[bad].ravel())
-        scale[bad_nodes] *= 0.5
+        scale[np.unique(cells[bad].ravel())] *= 0.5
     else:
         raise RuntimeError("shell jitter did not converge")
     if return_param:
-        return xyz, cells.astype(np.int64), (pr, pt, pph, rs_in, rl_in, thick, z_top, nt, nphi)
+        return xyz, cells.astype(np.int64), (pr, rs_in, rl_in, thick, z_top)
     return xyz, cells.astype(np.int64)
