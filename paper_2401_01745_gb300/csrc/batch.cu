@@ -21,17 +21,20 @@
 
 namespace emrkc {
 
+// Stage j = 1 reads only what earlier launches wrote (read-only cached loads
+// are safe); stage j >= 2 reads g_{j-1}, written earlier in this launch
+// (loads through L2).
 template <class Model>
 __device__ __forceinline__ void batch_stage_rows(const StageArgs& a, const Ell& A, int64_t r0, int64_t r1, bool has_m2) {
   if (has_m2) {
     for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) stage_node_mixed<Model, true, true>(a, A, i);
   } else {
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) stage_node_mixed<Model, false, true>(a, A, i);
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) stage_node_mixed<Model, false, false>(a, A, i);
   }
 }
 
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) batch_step_kernel(const BatchCtl c) {
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) batch_step_kernel(const BatchCtl c) {
   __shared__ unsigned int s_item;
   __shared__ int s_abort;
   for (;;) {

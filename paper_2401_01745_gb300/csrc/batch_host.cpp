@@ -270,7 +270,7 @@ extern "C" {
 int64_t emrkc_instance_bytes(int64_t n, double nnz_per_row, int model) {
   const int N = emrkc_num_vars(model);
   if (N < 1 || n <= 0) return -1;
-  const int64_t ld = (n + 63) / 64 * 64;
+  const int64_t ld = (n + 127) / 128 * 128;
   int64_t bytes = 3 * ld * 8 + 3 * std::max(N - 1, 1) * ld * 4 + 3 * ld * 8 + ld * 4;
   bytes += 2 * ld * 8 + 3 * (int64_t)N * ld * 8;
   bytes += 2 * ld * 8 + std::max(N - 1, 1) * ld * 8 + 64 * 8 + 16;

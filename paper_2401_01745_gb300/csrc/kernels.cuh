@@ -2,7 +2,7 @@
 // (Algorithm 5), templated on the ionic model and on the precision mode.
 //
 // Data layout in HBM (structure of arrays, leading dimension ld = n rounded
-// up to a multiple of 64):
+// up to a multiple of 128):
 //   V            double[ld]                 (every mode)
 //   z block      Z[(N-1) * ld], row k = variable k+1 (Z = double or float)
 //   L            sliced ELL, 32-row slices, slot-major inside a slice so that
@@ -49,6 +49,39 @@ __device__ __forceinline__ float ell_diff32(const Ell& A, int64_t i, const float
   const float xi = ldm<CG>(x + i);
   float acc = 0.0f;
   for (int k = 0; k < w; ++k, p += 32) acc += __ldg(A.val32 + p) * (ldm<CG>(x + __ldg(A.col + p)) - xi);
+  return acc;
+}
+
+// Split form of ell_diff32 for rows of at most W stored entries: ell_gather
+// issues every column, value and neighbour load of the row up front (into
+// registers), ell_reduce sums them later, so the loads can be in flight
+// while the caller does other work (the ionic model).  Same sum, same order.
+template <int W, bool CG = false>
+__device__ __forceinline__ int ell_gather(const Ell& A, int64_t i, const float* __restrict__ x, float (&xv)[W],
+                                          float (&lv)[W]) {
+  const int64_t b = i >> 5;
+  const int w = __ldg(A.width + b);
+  const int64_t p = __ldg(A.slice_ptr + b) + (i & 31);
+  int32_t c[W];
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    if (k < w) {
+      c[k] = __ldg(A.col + p + 32 * k);
+      lv[k] = __ldg(A.val32 + p + 32 * k);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < W; ++k)
+    if (k < w) xv[k] = ldm<CG>(x + c[k]);
+  return w;
+}
+
+template <int W>
+__device__ __forceinline__ float ell_reduce(const float (&xv)[W], const float (&lv)[W], int w, float xi) {
+  float acc = 0.0f;
+#pragma unroll
+  for (int k = 0; k < W; ++k)
+    if (k < w) acc += lv[k] * (xv[k] - xi);
   return acc;
 }
 
@@ -231,6 +264,189 @@ __global__ void __launch_bounds__(128) stage_kernel_mixed(const StageArgs a, con
   stage_node_mixed<Model, HAS_M2, false>(a, A, i);
 }
 
+// ---------------------------------------------------------------------------
+// Persistent, bulk-copy pipelined variant of the mixed stage kernel.
+//
+// A CTA of 128 threads owns tiles of 128 consecutive nodes (tile, tile + G,
+// tile + 2G, ...).  One elected thread streams the next tiles' inputs (the
+// NZ rows of z, V hi and the stimulus mask: contiguous 512-byte / 128-byte
+// segments of the SoA arrays) into a double-buffered shared-memory stage
+// with cp.async.bulk completing on an mbarrier, while all threads compute
+// the current tile from shared memory.  Memory-level parallelism then no
+// longer depends on how many warps the register budget of the ionic model
+// leaves resident.  The sparse row and the neighbour gathers use ordinary
+// read-only loads.  Waits are bounded: after kTmaSpinLimit polls a CTA
+// records bit 1 in flags, waits (bounded) for its copies in flight and
+// returns.
+constexpr int kTmaTile = 128;
+constexpr long long kTmaSpinLimit = 1ll << 26;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Shared-memory bytes of one pipeline stage for NZ z rows.
+__host__ __device__ constexpr int tma_stage_bytes(int nz) {
+  return (nz * kTmaTile + kTmaTile) * 4 + kTmaTile;  // z rows, V hi, mask
+}
+
+template <class Model, bool HAS_M2>
+__global__ void __launch_bounds__(kTmaTile) stage_kernel_mixed_tma(const StageArgs a, const Ell A) {
+  constexpr int NE = Model::NE, NS = Model::NS, NZ = NE + NS;
+  constexpr int SB = tma_stage_bytes(NZ);
+  extern __shared__ __align__(128) unsigned char tma_smem[];
+  __shared__ __align__(8) unsigned long long bars[2];
+  __shared__ int s_abort;
+  const int tid = threadIdx.x;
+  const int64_t ntiles = (a.n + kTmaTile - 1) / kTmaTile;
+  const int64_t G = gridDim.x;
+  const unsigned bar0 = smem_u32(&bars[0]), bar1 = smem_u32(&bars[1]);
+  const unsigned stage_base = smem_u32(tma_smem);
+
+  auto issue = [&](int64_t tile, int buf) {
+    const unsigned bar = buf ? bar1 : bar0;
+    const unsigned dst = stage_base + buf * SB;
+    const int64_t off = tile * kTmaTile;
+    mbar_expect_tx(bar, (unsigned)SB);
+    const float* Zm1 = static_cast<const float*>(a.Zm1);
+#pragma unroll 1
+    for (int k = 0; k < NZ; ++k) bulk_g2s(dst + k * kTmaTile * 4, Zm1 + k * a.ld + off, kTmaTile * 4, bar);
+    bulk_g2s(dst + NZ * kTmaTile * 4, a.V32m1 + off, kTmaTile * 4, bar);
+    bulk_g2s(dst + (NZ + 1) * kTmaTile * 4, a.mask + off, kTmaTile, bar);
+  };
+
+  if (tid == 0) {
+    mbar_init(bar0, 1);
+    mbar_init(bar1, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+  }
+  __syncthreads();
+  if (a.mask == nullptr) {
+    // the stage copies the mask with the rest: a solver without stimulus has no
+    // mask array, so this variant is only launched with one
+    return;
+  }
+  const int64_t first = blockIdx.x;
+  if (tid == 0) {
+    if (first < ntiles) issue(first, 0);
+    if (first + G < ntiles) issue(first + G, 1);
+  }
+  unsigned phase[2] = {0u, 0u};
+  int it = 0;
+  for (int64_t tile = first; tile < ntiles; tile += G, ++it) {
+    const int buf = it & 1;
+    const unsigned bar = buf ? bar1 : bar0;
+    long long spins = 0;
+    bool ok = true;
+    while (!mbar_try_wait(bar, phase[buf])) {
+      if (++spins > kTmaSpinLimit) {
+        atomicOr(a.flags, 2);
+        s_abort = 1;
+        ok = false;
+        break;
+      }
+    }
+    if (ok) phase[buf] ^= 1u;
+    __syncthreads();
+    if (s_abort) break;
+    const float* sz = reinterpret_cast<const float*>(tma_smem + buf * SB);
+    const int64_t i = tile * kTmaTile + tid;
+    if (i < a.n) {
+      float z[NZ > 0 ? NZ : 1];
+#pragma unroll
+      for (int k = 0; k < NZ; ++k) z[k] = sz[k * kTmaTile + tid];
+      const float V = sz[NZ * kTmaTile + tid];
+      const unsigned char mk = reinterpret_cast<const unsigned char*>(sz + (NZ + 1) * kTmaTile)[tid];
+      using M = Math<float>;
+      float zE1[NE > 0 ? NE : 1];
+      if constexpr (NE > 0) {
+        float lam[NE], zinf[NE];
+        Model::gating(V, z, z + NE, lam, zinf);
+#pragma unroll
+        for (int k = 0; k < NE; ++k) zE1[k] = z[k] + M::em1(a.f_eta * lam[k]) * (z[k] - zinf[k]);
+      }
+      float Iion;
+      float gS[NS > 0 ? NS : 1];
+      Model::currents(V, zE1, z + NE, Iion, gS);
+      const float Istim = mk ? a.f_stim : 0.0f;
+      const float F = (Istim - Iion) * a.f_inv_Cm;
+      float* __restrict__ Zout = static_cast<float*>(a.Zout);
+      const float* __restrict__ Zm2 = static_cast<const float*>(a.Zm2);
+      const int64_t ld = a.ld;
+      if constexpr (NZ > 0) {
+#pragma unroll
+        for (int k = 0; k < NZ; ++k) {
+          const float fbar = (k < NE) ? (zE1[k < NE ? k : 0] - z[k]) * a.f_inv_eta : a.f_cm * gS[k >= NE ? k - NE : 0];
+          float out;
+          if constexpr (HAS_M2) out = a.f_nu * z[k] + a.f_kappa * __ldg(Zm2 + k * ld + i) + a.f_mudt * fbar;
+          else out = z[k] + a.f_mudt * fbar;
+          Zout[k * ld + i] = out;
+        }
+      }
+      const float LV = ell_diff32<false>(A, i, a.V32m1);
+      if (a.Vn32_copy != nullptr) a.Vn32_copy[i] = V;
+      if (a.m == 1) {
+        const float fbarV = a.f_mu1 * (LV + F);
+        const float lo1 = __ldg(a.Vlo_m1 + i);
+        float inc = a.f_mudt * fbarV;
+        if constexpr (HAS_M2) inc += a.f_kappa * ((__ldg(a.Vhi_m2 + i) - V) + (__ldg(a.Vlo_m2 + i) - lo1));
+        float hi, lo;
+        ff_add(V, lo1, inc, hi, lo);
+        a.V32out[i] = hi;
+        a.Vlo_out[i] = lo;
+        if (a.final_stage) step_epilogue_ff(i, __ldg(a.Vn32 + i), hi, a.act, a.t_n, a.dt, a.f_th, a.flags);
+      } else {
+        a.D1[i] = a.f_mu1eta * (LV + F);
+        a.LV[i] = LV;
+        static_cast<float*>(a.F)[i] = F;
+      }
+    }
+    __syncthreads();  // every thread is done with this stage buffer
+    if (tid == 0 && tile + 2 * G < ntiles) {
+      fence_proxy_async();
+      issue(tile + 2 * G, buf);
+    }
+  }
+  // on abort: give copies already in flight a bounded chance to land (a
+  // buffer whose wait gave up, and the other one if its tile was issued)
+  if (s_abort && tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      long long spins = 0;
+      while (!mbar_try_wait(b ? bar1 : bar0, phase[b]) && ++spins < kTmaSpinLimit) {
+      }
+    }
+  }
+}
+
 // Inner RKC stage k >= 2 (FP64 path), Algorithm 1 applied to f_u = f_F + frozen f_S.
 static __global__ void __launch_bounds__(256) inner_kernel_fp64(const InnerArgs a, const Ell A) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -279,6 +495,42 @@ static __global__ void __launch_bounds__(256) inner_kernel_mixed(const InnerArgs
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   inner_node_mixed<false>(a, A, i);
+}
+
+// Same stage with the row's loads issued up front (rows of at most W entries).
+template <int W>
+__global__ void __launch_bounds__(256) inner_kernel_mixed_w(const InnerArgs a, const Ell A) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  float xv[W], lv[W];
+  const int w = ell_gather<W>(A, i, a.d1, xv, lv);
+  const float d1 = __ldg(a.d1 + i);
+  const float F = __ldg(static_cast<const float*>(a.F) + i);
+  const float LVi = __ldg(a.LV + i);
+  const float d2 = (a.d2 != nullptr) ? __ldg(a.d2 + i) : 0.0f;
+  float lo1 = 0.0f, hi1 = 0.0f, hi2 = 0.0f, lo2 = 0.0f;
+  if (a.last) {
+    hi1 = __ldg(a.Vhi1 + i);
+    lo1 = __ldg(a.Vlo1 + i);
+    if (a.Vhi2 != nullptr) {
+      hi2 = __ldg(a.Vhi2 + i);
+      lo2 = __ldg(a.Vlo2 + i);
+    }
+  }
+  const float Ld = ell_reduce<W>(xv, lv, w, d1);
+  float dk = a.f_nu * d1 + a.f_mueta * (LVi + Ld + F);
+  if (a.d2 != nullptr) dk += a.f_kappa * d2;
+  if (!a.last) {
+    a.dk[i] = dk;
+    return;
+  }
+  float inc = a.f_omu_dt * (dk * a.f_inv_eta);
+  if (a.Vhi2 != nullptr) inc += a.f_okappa * ((hi2 - hi1) + (lo2 - lo1));
+  float hi, lo;
+  ff_add(hi1, lo1, inc, hi, lo);
+  a.V32out[i] = hi;
+  a.Vlo_out[i] = lo;
+  if (a.final_stage) step_epilogue_ff(i, __ldg(a.Vn32 + i), hi, a.act, a.t_n, a.dt, a.f_th, a.flags);
 }
 
 // ---------------------------------------------------------------------------
@@ -452,8 +704,15 @@ struct Kernels {
     if (a.n == 0) return;
     const unsigned g = blocks_for(a.n, 128);
     if constexpr (MIXED) {
-      if (has_m2) stage_kernel_mixed<MR, true><<<g, 128, 0, st>>>(a, A);
-      else stage_kernel_mixed<MR, false><<<g, 128, 0, st>>>(a, A);
+      if (a.mask != nullptr && a.tma_grid > 0) {
+        constexpr int SB = tma_stage_bytes(MR::NE + MR::NS);
+        if (has_m2) stage_kernel_mixed_tma<MR, true><<<a.tma_grid, kTmaTile, 2 * SB, st>>>(a, A);
+        else stage_kernel_mixed_tma<MR, false><<<a.tma_grid, kTmaTile, 2 * SB, st>>>(a, A);
+      } else if (has_m2) {
+        stage_kernel_mixed<MR, true><<<g, 128, 0, st>>>(a, A);
+      } else {
+        stage_kernel_mixed<MR, false><<<g, 128, 0, st>>>(a, A);
+      }
     } else {
       if (has_m2) stage_kernel_fp64<MR, true><<<g, 128, 0, st>>>(a, A);
       else stage_kernel_fp64<MR, false><<<g, 128, 0, st>>>(a, A);
@@ -461,7 +720,10 @@ struct Kernels {
   }
   static void inner(const InnerArgs& a, const Ell& A, cudaStream_t st) {
     if (a.n == 0) return;
-    if constexpr (MIXED) inner_kernel_mixed<<<blocks_for(a.n, 256), 256, 0, st>>>(a, A);
+    if constexpr (MIXED) {
+      if (a.ell_wmax <= 8) inner_kernel_mixed_w<8><<<blocks_for(a.n, 256), 256, 0, st>>>(a, A);
+      else inner_kernel_mixed<<<blocks_for(a.n, 256), 256, 0, st>>>(a, A);
+    }
     else inner_kernel_fp64<<<blocks_for(a.n, 256), 256, 0, st>>>(a, A);
   }
   static void power_F(const PowerFArgs& a, const Ell& A, const ReduceScratch& rs, cudaStream_t st) {
@@ -485,6 +747,20 @@ struct Kernels {
     if (g > 4096) g = 4096;
     convert_kernel<Z><<<g, 256, 0, st>>>(count, src, dst, to_double);
   }
+  // CTAs of the persistent bulk-copy stage kernel: all SMs x resident CTAs
+  static int tma_grid(int device) {
+    if constexpr (!MIXED) {
+      return 0;
+    } else {
+      constexpr int SB = tma_stage_bytes(MR::NE + MR::NS);
+      int per_sm = 0, sms = 0;
+      cudaFuncSetAttribute(stage_kernel_mixed_tma<MR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * SB);
+      cudaFuncSetAttribute(stage_kernel_mixed_tma<MR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * SB);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel_mixed_tma<MR, false>, kTmaTile, 2 * SB);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+      return per_sm * sms;
+    }
+  }
   static void fill(KernelSet* ks, int model) {
     ks->model = model;
     ks->nE = MR::NE;
@@ -497,6 +773,7 @@ struct Kernels {
     ks->fS_eval = &fS_eval;
     ks->state_sumsq = &state_sumsq;
     ks->convert_z = &convert_z;
+    ks->tma_grid = &tma_grid;
   }
 };
 

@@ -78,6 +78,8 @@ struct StageArgs {
   const float* Vn32 = nullptr;  // hi of V_n (epilogue)
   float* Vn32_copy = nullptr;   // store hi of V_n (first stage when s >= 2)
   float f_th = -20;
+  int tma_grid = 0;             // > 0: persistent bulk-copy variant with this grid
+  int ell_wmax = 1 << 30;       // widest sliced-ELL slice (selects unrolled row variants)
 };
 
 // Inner RKC stage k >= 2 over f_u(u) = L u + F:
@@ -115,6 +117,7 @@ struct InnerArgs {
   float* Vlo_out = nullptr;     // V32out holds hi
   const float* Vn32 = nullptr;
   float f_okappa = 0, f_omu_dt = 0, f_th = -20;
+  int ell_wmax = 1 << 30;       // widest sliced-ELL slice (selects unrolled row variants)
 };
 
 // Power iteration (Algorithm 5) kernels.
@@ -154,6 +157,7 @@ struct KernelSet {
   void (*state_sumsq)(int64_t n, int64_t ld, int nz, const double* V, const void* Z,
                       const ReduceScratch&, int slot, cudaStream_t) = nullptr;
   void (*convert_z)(int64_t count, const void* src, double* dst, int to_double, cudaStream_t) = nullptr;
+  int (*tma_grid)(int device) = nullptr;  // grid of the persistent stage kernel (0: not used)
 };
 
 // Float-float V of the mixed path: split a double into hi + lo, and join.

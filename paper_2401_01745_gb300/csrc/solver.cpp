@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -272,6 +273,8 @@ int do_step(emrkc_solver* s, double dt) {
     a.f_eta = (float)eta;
     a.f_stim = (float)a.stim;
     a.f_inv_Cm = (float)(1.0 / s->Cm);
+    a.tma_grid = s->tma_grid;
+    a.ell_wmax = s->ell_wmax;
     s->launch(EMRKC_PHASE_STAGE, [&] { s->ks.stage(a, s->ell, j >= 2, s->stream); });
     for (int k = 2; k <= Mi; ++k) {
       InnerArgs b;
@@ -317,6 +320,7 @@ int do_step(emrkc_solver* s, double dt) {
       b.f_kappa = (float)ci.kappa[k];
       b.f_mueta = (float)(ci.mu[k] * eta);
       b.f_inv_eta = (float)(1.0 / eta);
+      b.ell_wmax = s->ell_wmax;
       s->launch(EMRKC_PHASE_INNER, [&] { s->ks.inner(b, s->ell, s->stream); });
     }
   }
@@ -371,6 +375,8 @@ int build_matrix(emrkc_solver* s, const emrkc_matrix* m) {
   }
   const int64_t total = sptr[ns];
   s->mat_slots = total;
+  s->ell_wmax = 0;
+  for (int64_t b = 0; b < ns; ++b) s->ell_wmax = std::max<int>(s->ell_wmax, width[b]);
   s->mat_entries = 0;
   for (int64_t i = 0; i < n; ++i) s->mat_entries += (int64_t)rows[i].size();
   std::vector<int32_t> col(std::max<int64_t>(total, 1), 0);
@@ -613,13 +619,19 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
     delete s;
     return EMRKC_ERR_ARG;
   }
+  if (s->precision == EMRKC_PREC_MIXED && s->ks.tma_grid) {
+    const char* no_tma = std::getenv("EMRKC_NO_TMA");
+    if (!(no_tma && no_tma[0] == '1')) s->tma_grid = s->ks.tma_grid(s->device);
+  }
   s->N = s->ks.N;
   s->nE = s->ks.nE;
   s->nS = s->ks.nS;
   s->zsize = s->precision == EMRKC_PREC_FP64 ? 8 : 4;
   s->rsize = s->zsize;
   s->n = mat->n;
-  s->ld = (mat->n + 63) / 64 * 64;
+  // ld: multiple of 128 so that every 128-node tile of every SoA row lies in
+  // the allocation and starts on a 512-byte boundary (bulk-copy alignment)
+  s->ld = (mat->n + 127) / 128 * 128;
   s->chi = tissue->chi;
   s->Cm = tissue->Cm;
   s->act_on = !std::isnan(o.act_threshold);
@@ -671,8 +683,9 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
   if ((e = cudaMallocHost(&s->h_pin, 16 * sizeof(double))) != cudaSuccess) return bail(EMRKC_ERR_OOM, "pinned allocation failed");
   std::memset(s->h_pin, 0, 16 * sizeof(double));
   if (stim && stim->node_mask) {
-    if ((e = dalloc(&s->d_mask, s->n)) != cudaSuccess) return bail(EMRKC_ERR_OOM, "device allocation failed");
-    cudaMemcpy(s->d_mask, stim->node_mask, s->n, cudaMemcpyHostToDevice);
+    if ((e = dalloc(&s->d_mask, ld)) != cudaSuccess) return bail(EMRKC_ERR_OOM, "device allocation failed");
+    cudaMemsetAsync(s->d_mask, 0, ld, s->stream);
+    cudaMemcpyAsync(s->d_mask, stim->node_mask, s->n, cudaMemcpyHostToDevice, s->stream);
     s->amp = stim->amplitude;
     s->t_on = stim->t_on;
     s->t_off = stim->t_off;

@@ -146,6 +146,8 @@ struct emrkc_solver {
   int itF = 0, itS = 0;
   int64_t total_it = 0, launches = 0;
   int64_t mat_entries = 0, mat_slots = 0;
+  int tma_grid = 0;  // persistent bulk-copy stage kernel grid (mixed path), 0 = off
+  int ell_wmax = 0;  // widest sliced-ELL slice
   bool act_on = false;
   double phase_ms[EMRKC_NUM_PHASES] = {0};
   int64_t phase_launches[EMRKC_NUM_PHASES] = {0};
