@@ -142,6 +142,7 @@ int fill_inst(emrkc_batch* b, Member& mb, double dt, BatchInst* I) {
   I->n = s->n;
   I->ld = s->ld;
   I->ntiles = (int)((s->n + b->tile - 1) / b->tile);
+  I->wmax = s->ell_wmax;
   for (int k = 0; k < 3; ++k) {
     I->Vhi[k] = s->d_V32[k];
     I->Vlo[k] = s->d_Vlo[k];
@@ -194,11 +195,38 @@ int rebuild(emrkc_batch* b, double dt) {
     if (rc) return rc;
     maxP = std::max(maxP, b->h_inst[i].P);
   }
+  // Skewed order: an instance's phase p is emitted only after `lag` tiles of
+  // other work have been emitted since its phase p - 1, so that compute-heavy
+  // stage tiles of some instances run beside memory-bound SpMV tiles of
+  // others and a dependent tile rarely waits.  Every item still follows all
+  // items it depends on (deadlock-free in-order consumption).
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+  b->grid = std::max(1, sms * std::max(1, batch_blocks_per_sm(b->block)));
   std::vector<uint64_t> items;
-  for (int p = 0; p < maxP; ++p)
-    for (size_t i = 0; i < ni; ++i)
-      if (p < b->h_inst[i].P)
-        for (int t = 0; t < b->h_inst[i].ntiles; ++t) items.push_back(batch_item((int)i, p, t));
+  {
+    const int64_t lag = 2 * (int64_t)std::max(b->grid, 1);
+    std::vector<int> next(ni, 0);
+    std::vector<int64_t> ready(ni, 0);
+    size_t left = ni;
+    int64_t now = 0;
+    while (left > 0) {
+      int best = -1;
+      for (size_t i = 0; i < ni; ++i) {
+        if (next[i] >= b->h_inst[i].P) continue;
+        if (best < 0 || ready[i] < ready[best]) best = (int)i;
+        if (ready[i] <= now) {
+          best = (int)i;
+          break;
+        }
+      }
+      const int p = next[best];
+      for (int t = 0; t < b->h_inst[best].ntiles; ++t) items.push_back(batch_item(best, p, t));
+      now = std::max(now, ready[best]) + b->h_inst[best].ntiles;
+      ready[best] = now + lag;
+      if (++next[best] >= b->h_inst[best].P) --left;
+    }
+  }
   if (items.size() >= 0xffffffffull) return b->fail(EMRKC_ERR_ARG, "too many work items");
   b->n_items = (unsigned int)items.size();
   cudaError_t e;
@@ -211,10 +239,6 @@ int rebuild(emrkc_batch* b, double dt) {
     e = cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return b->cuda_fail(e, "batch plan upload");
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-  const int per_sm = std::max(1, batch_blocks_per_sm(b->block));
-  b->grid = std::max(1, sms * per_sm);
   b->plan_dt = dt;
   b->dirty = false;
   return EMRKC_OK;

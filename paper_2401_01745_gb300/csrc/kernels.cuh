@@ -137,6 +137,21 @@ __device__ __forceinline__ void step_epilogue_ff(int64_t i, float Vn, float Vnew
   }
 }
 
+// Exponential step (Algorithm 3, Exponential_Euler) and f_S at one node,
+// mixed path (FP32).
+template <class Model>
+__device__ __forceinline__ void ionic_mixed(float eta, float V, const float* z, float* zE1, float& Iion, float* gS) {
+  constexpr int NE = Model::NE;
+  using M = Math<float>;
+  if constexpr (NE > 0) {
+    float lam[NE], zinf[NE];
+    Model::gating(V, z, z + NE, lam, zinf);
+#pragma unroll
+    for (int k = 0; k < NE; ++k) zE1[k] = z[k] + M::em1(eta * lam[k]) * (z[k] - zinf[k]);
+  }
+  Model::currents(V, zE1, z + NE, Iion, gS);
+}
+
 // ---------------------------------------------------------------------------
 // Outer stage j (FP64 path): exponential Euler of the gates (Algorithm 3,
 // Exponential_Euler), frozen forcing f_S(t_j, y_E), first inner RKC stage and
@@ -215,15 +230,9 @@ __device__ __forceinline__ void stage_node_mixed(const StageArgs& a, const Ell& 
   for (int k = 0; k < NZ; ++k) z[k] = ldm<CG>(Zm1 + k * ld + i);
 
   float zE1[NE > 0 ? NE : 1];
-  if constexpr (NE > 0) {
-    float lam[NE], zinf[NE];
-    Model::gating(V, z, z + NE, lam, zinf);
-#pragma unroll
-    for (int k = 0; k < NE; ++k) zE1[k] = z[k] + M::em1(a.f_eta * lam[k]) * (z[k] - zinf[k]);
-  }
   float Iion;
   float gS[NS > 0 ? NS : 1];
-  Model::currents(V, zE1, z + NE, Iion, gS);
+  ionic_mixed<Model>(a.f_eta, V, z, zE1, Iion, gS);
   const float Istim = (a.mask != nullptr && a.mask[i]) ? a.f_stim : 0.0f;
   const float F = (Istim - Iion) * a.f_inv_Cm;
 
@@ -279,6 +288,7 @@ __global__ void __launch_bounds__(128) stage_kernel_mixed(const StageArgs a, con
 // records bit 1 in flags, waits (bounded) for its copies in flight and
 // returns.
 constexpr int kTmaTile = 128;
+constexpr int kTmaStageEllWidth = 8;  // rows of at most this many entries are staged too
 constexpr long long kTmaSpinLimit = 1ll << 26;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -313,15 +323,23 @@ __device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Shared-memory bytes of one pipeline stage for NZ z rows.
-__host__ __device__ constexpr int tma_stage_bytes(int nz) {
-  return (nz * kTmaTile + kTmaTile) * 4 + kTmaTile;  // z rows, V hi, mask
+// Shared-memory bytes of one pipeline stage for NZ z rows and rows of at most
+// wmax stored entries: z rows, V hi, mask, then the tile's sliced-ELL column
+// indices and values (4 slices of 32 rows).
+__host__ __device__ constexpr int tma_fixed_bytes(int nz) {
+  return (nz * kTmaTile + kTmaTile) * 4 + kTmaTile;
+}
+__host__ __device__ constexpr int tma_stage_bytes(int nz, int wmax) {
+  return tma_fixed_bytes(nz) + (wmax <= kTmaStageEllWidth ? 2 * 4 * wmax * 32 * 4 : 0);
 }
 
 template <class Model, bool HAS_M2>
 __global__ void __launch_bounds__(kTmaTile) stage_kernel_mixed_tma(const StageArgs a, const Ell A) {
   constexpr int NE = Model::NE, NS = Model::NS, NZ = NE + NS;
-  constexpr int SB = tma_stage_bytes(NZ);
+  constexpr int FB = tma_fixed_bytes(NZ);
+  const int SB = tma_stage_bytes(NZ, a.ell_wmax);
+  const bool stage_ell = a.ell_wmax <= kTmaStageEllWidth;
+  const int64_t nslices = A.n_slices;
   extern __shared__ __align__(128) unsigned char tma_smem[];
   __shared__ __align__(8) unsigned long long bars[2];
   __shared__ int s_abort;
@@ -335,12 +353,21 @@ __global__ void __launch_bounds__(kTmaTile) stage_kernel_mixed_tma(const StageAr
     const unsigned bar = buf ? bar1 : bar0;
     const unsigned dst = stage_base + buf * SB;
     const int64_t off = tile * kTmaTile;
-    mbar_expect_tx(bar, (unsigned)SB);
+    const int64_t s0 = tile * (kTmaTile / 32);
+    const int64_t s1 = (s0 + kTmaTile / 32 < nslices) ? s0 + kTmaTile / 32 : nslices;
+    const int64_t e0 = __ldg(A.slice_ptr + s0), e1 = __ldg(A.slice_ptr + s1);
+    const unsigned ell_bytes = stage_ell ? (unsigned)((e1 - e0) * 4) : 0u;
+    mbar_expect_tx(bar, (unsigned)FB + 2u * ell_bytes);
     const float* Zm1 = static_cast<const float*>(a.Zm1);
 #pragma unroll 1
     for (int k = 0; k < NZ; ++k) bulk_g2s(dst + k * kTmaTile * 4, Zm1 + k * a.ld + off, kTmaTile * 4, bar);
     bulk_g2s(dst + NZ * kTmaTile * 4, a.V32m1 + off, kTmaTile * 4, bar);
     bulk_g2s(dst + (NZ + 1) * kTmaTile * 4, a.mask + off, kTmaTile, bar);
+    if (stage_ell && ell_bytes > 0) {
+      const unsigned half = (unsigned)(4 * a.ell_wmax * 32 * 4);
+      bulk_g2s(dst + FB, A.col + e0, ell_bytes, bar);
+      bulk_g2s(dst + FB + half, A.val32 + e0, ell_bytes, bar);
+    }
   };
 
   if (tid == 0) {
@@ -386,17 +413,10 @@ __global__ void __launch_bounds__(kTmaTile) stage_kernel_mixed_tma(const StageAr
       for (int k = 0; k < NZ; ++k) z[k] = sz[k * kTmaTile + tid];
       const float V = sz[NZ * kTmaTile + tid];
       const unsigned char mk = reinterpret_cast<const unsigned char*>(sz + (NZ + 1) * kTmaTile)[tid];
-      using M = Math<float>;
       float zE1[NE > 0 ? NE : 1];
-      if constexpr (NE > 0) {
-        float lam[NE], zinf[NE];
-        Model::gating(V, z, z + NE, lam, zinf);
-#pragma unroll
-        for (int k = 0; k < NE; ++k) zE1[k] = z[k] + M::em1(a.f_eta * lam[k]) * (z[k] - zinf[k]);
-      }
       float Iion;
       float gS[NS > 0 ? NS : 1];
-      Model::currents(V, zE1, z + NE, Iion, gS);
+      ionic_mixed<Model>(a.f_eta, V, z, zE1, Iion, gS);
       const float Istim = mk ? a.f_stim : 0.0f;
       const float F = (Istim - Iion) * a.f_inv_Cm;
       float* __restrict__ Zout = static_cast<float*>(a.Zout);
@@ -412,7 +432,18 @@ __global__ void __launch_bounds__(kTmaTile) stage_kernel_mixed_tma(const StageAr
           Zout[k * ld + i] = out;
         }
       }
-      const float LV = ell_diff32<false>(A, i, a.V32m1);
+      // sparse row from the staged tile: slot k of row i at (slice offset) + 32 k + lane
+      float LV = 0.0f;
+      if (!stage_ell) {
+        LV = ell_diff32<false>(A, i, a.V32m1);
+      } else {
+        const int64_t b = i >> 5;
+        const int w = __ldg(A.width + b);
+        const int base = (int)(__ldg(A.slice_ptr + b) - __ldg(A.slice_ptr + tile * (kTmaTile / 32))) + (tid & 31);
+        const int32_t* scol = reinterpret_cast<const int32_t*>(tma_smem + buf * SB + FB);
+        const float* sval = reinterpret_cast<const float*>(tma_smem + buf * SB + FB + 4 * a.ell_wmax * 32 * 4);
+        for (int k = 0; k < w; ++k) LV += sval[base + 32 * k] * (__ldg(a.V32m1 + scol[base + 32 * k]) - V);
+      }
       if (a.Vn32_copy != nullptr) a.Vn32_copy[i] = V;
       if (a.m == 1) {
         const float fbarV = a.f_mu1 * (LV + F);
@@ -498,23 +529,21 @@ static __global__ void __launch_bounds__(256) inner_kernel_mixed(const InnerArgs
 }
 
 // Same stage with the row's loads issued up front (rows of at most W entries).
-template <int W>
-__global__ void __launch_bounds__(256) inner_kernel_mixed_w(const InnerArgs a, const Ell A) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
+template <int W, bool CG = false>
+__device__ __forceinline__ void inner_node_mixed_w(const InnerArgs& a, const Ell& A, const int64_t i) {
   float xv[W], lv[W];
-  const int w = ell_gather<W>(A, i, a.d1, xv, lv);
-  const float d1 = __ldg(a.d1 + i);
-  const float F = __ldg(static_cast<const float*>(a.F) + i);
-  const float LVi = __ldg(a.LV + i);
-  const float d2 = (a.d2 != nullptr) ? __ldg(a.d2 + i) : 0.0f;
+  const int w = ell_gather<W, CG>(A, i, a.d1, xv, lv);
+  const float d1 = ldm<CG>(a.d1 + i);
+  const float F = ldm<CG>(static_cast<const float*>(a.F) + i);
+  const float LVi = ldm<CG>(a.LV + i);
+  const float d2 = (a.d2 != nullptr) ? ldm<CG>(a.d2 + i) : 0.0f;
   float lo1 = 0.0f, hi1 = 0.0f, hi2 = 0.0f, lo2 = 0.0f;
   if (a.last) {
-    hi1 = __ldg(a.Vhi1 + i);
-    lo1 = __ldg(a.Vlo1 + i);
+    hi1 = ldm<CG>(a.Vhi1 + i);
+    lo1 = ldm<CG>(a.Vlo1 + i);
     if (a.Vhi2 != nullptr) {
-      hi2 = __ldg(a.Vhi2 + i);
-      lo2 = __ldg(a.Vlo2 + i);
+      hi2 = ldm<CG>(a.Vhi2 + i);
+      lo2 = ldm<CG>(a.Vlo2 + i);
     }
   }
   const float Ld = ell_reduce<W>(xv, lv, w, d1);
@@ -530,7 +559,14 @@ __global__ void __launch_bounds__(256) inner_kernel_mixed_w(const InnerArgs a, c
   ff_add(hi1, lo1, inc, hi, lo);
   a.V32out[i] = hi;
   a.Vlo_out[i] = lo;
-  if (a.final_stage) step_epilogue_ff(i, __ldg(a.Vn32 + i), hi, a.act, a.t_n, a.dt, a.f_th, a.flags);
+  if (a.final_stage) step_epilogue_ff(i, ldm<CG>(a.Vn32 + i), hi, a.act, a.t_n, a.dt, a.f_th, a.flags);
+}
+
+template <int W>
+__global__ void __launch_bounds__(256) inner_kernel_mixed_w(const InnerArgs a, const Ell A) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  inner_node_mixed_w<W, false>(a, A, i);
 }
 
 // ---------------------------------------------------------------------------
@@ -705,7 +741,7 @@ struct Kernels {
     const unsigned g = blocks_for(a.n, 128);
     if constexpr (MIXED) {
       if (a.mask != nullptr && a.tma_grid > 0) {
-        constexpr int SB = tma_stage_bytes(MR::NE + MR::NS);
+        const int SB = tma_stage_bytes(MR::NE + MR::NS, a.ell_wmax);
         if (has_m2) stage_kernel_mixed_tma<MR, true><<<a.tma_grid, kTmaTile, 2 * SB, st>>>(a, A);
         else stage_kernel_mixed_tma<MR, false><<<a.tma_grid, kTmaTile, 2 * SB, st>>>(a, A);
       } else if (has_m2) {
@@ -748,11 +784,11 @@ struct Kernels {
     convert_kernel<Z><<<g, 256, 0, st>>>(count, src, dst, to_double);
   }
   // CTAs of the persistent bulk-copy stage kernel: all SMs x resident CTAs
-  static int tma_grid(int device) {
+  static int tma_grid(int device, int wmax) {
     if constexpr (!MIXED) {
       return 0;
     } else {
-      constexpr int SB = tma_stage_bytes(MR::NE + MR::NS);
+      const int SB = tma_stage_bytes(MR::NE + MR::NS, wmax);
       int per_sm = 0, sms = 0;
       cudaFuncSetAttribute(stage_kernel_mixed_tma<MR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * SB);
       cudaFuncSetAttribute(stage_kernel_mixed_tma<MR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * SB);

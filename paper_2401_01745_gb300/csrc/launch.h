@@ -157,7 +157,7 @@ struct KernelSet {
   void (*state_sumsq)(int64_t n, int64_t ld, int nz, const double* V, const void* Z,
                       const ReduceScratch&, int slot, cudaStream_t) = nullptr;
   void (*convert_z)(int64_t count, const void* src, double* dst, int to_double, cudaStream_t) = nullptr;
-  int (*tma_grid)(int device) = nullptr;  // grid of the persistent stage kernel (0: not used)
+  int (*tma_grid)(int device, int wmax) = nullptr;  // grid of the persistent stage kernel (0: not used)
 };
 
 // Float-float V of the mixed path: split a double into hi + lo, and join.
@@ -184,6 +184,7 @@ constexpr int kBatchMaxPhases = 64;  // s * m <= 64
 struct BatchInst {
   int model = 0, s = 1, m = 1, P = 1;  // P = s * m phases per step
   int cur = 0, ntiles = 0;
+  int wmax = 0;  // widest sliced-ELL slice
   int64_t n = 0, ld = 0;
   float* Vhi[3] = {nullptr, nullptr, nullptr};
   float* Vlo[3] = {nullptr, nullptr, nullptr};

@@ -518,6 +518,7 @@ int solver_update_rho(emrkc_solver* s) {
   return rc;
 }
 void solver_materialise_V(emrkc_solver* s) { materialise_V(s); }
+
 }  // namespace emrkc
 
 extern "C" {
@@ -619,10 +620,6 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
     delete s;
     return EMRKC_ERR_ARG;
   }
-  if (s->precision == EMRKC_PREC_MIXED && s->ks.tma_grid) {
-    const char* no_tma = std::getenv("EMRKC_NO_TMA");
-    if (!(no_tma && no_tma[0] == '1')) s->tma_grid = s->ks.tma_grid(s->device);
-  }
   s->N = s->ks.N;
   s->nE = s->ks.nE;
   s->nS = s->ks.nS;
@@ -649,6 +646,10 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
     s->own_stream = true;
   }
   if ((rc = build_matrix(s, mat))) return bail(rc, "");
+  if (s->precision == EMRKC_PREC_MIXED && s->ks.tma_grid) {
+    const char* no_tma = std::getenv("EMRKC_NO_TMA");
+    if (!(no_tma && no_tma[0] == '1')) s->tma_grid = s->ks.tma_grid(s->device, s->ell_wmax);
+  }
   const int64_t ld = s->ld, nz = s->N - 1;
   bool fail = false;
   for (int b = 0; b < 3; ++b) {

@@ -245,15 +245,20 @@ def test_full_size_slab_ttp_parity_first_steps():
     _assert_parity(Y, act, prob, ref)
 
 
-@pytest.mark.parametrize("name,dt,steps,h", [
-    ("slab41x15x7_ttp", 0.05, 300, 0.01),
-    ("square33x33_hh", 0.02, 300, 1.0 / 64),
+@pytest.mark.parametrize("name,dt,steps,h,amp_scale", [
+    ("slab41x15x7_ttp", 0.05, 300, 0.01, 1.0),
+    ("square33x33_hh", 0.02, 300, 1.0 / 64, 1.0),
+    # a stimulus eight times stronger drives V above +100 mV while it is on
+    ("slab21x9x5_ttp", 0.05, 16, 0.01, 8.0),
 ])
-def test_mixed_precision_vs_fp64(name, dt, steps, h):
+def test_mixed_precision_vs_fp64(name, dt, steps, h, amp_scale):
     w = make_workload(name, h=h)
     w.dt = dt
+    w.stim_amp = w.stim_amp * amp_scale
     Y64, a64, log64, *_ = _run_pair(w, steps, oracle=False)
     Y32, a32, log32, *_ = _run_pair(w, steps, precision=pkg.PREC_MIXED, oracle=False)
+    if amp_scale > 1.0:
+        assert np.nanmax(Y64[0]) > 100.0
     prob = Monodomain.from_workload(w)
     err = prob.l2_norm(Y32[0] - Y64[0]) / prob.l2_norm(Y64[0])
     assert err <= 1e-3, f"mixed vs FP64 rel L2 error in V {err:.3e}"
