@@ -63,6 +63,21 @@ extern "C" {
 /* rho_every >= 1: power iteration every rho_every-th step (warm started)   */
 #define EMRKC_RHO_FIXED -1 /* use options.rho_F / rho_S as given            */
 
+/* ---- time integrators (Sec. 5) ---------------------------------------- */
+#define EMRKC_METHOD_EMRKC 0   /* Algorithm 3 (default)                      */
+#define EMRKC_METHOD_EXEX_RL 1 /* Algorithm 4 with the diffusion step taken
+                                  explicitly: the paper's fine-step reference
+                                  solver (Sec. 5).  FP64 only; rho options
+                                  unused; s = m = 0 in the stats            */
+#define EMRKC_METHOD_IMEX_RL 2 /* Algorithm 4: gates by exponential Euler,
+                                  z_S by explicit Euler, then the implicit
+                                  diffusion step (Cm M + dt K / chi) V_{n+1}
+                                  = Cm M V_n + dt M (I_stim - I_ion), solved
+                                  on the device by Jacobi-preconditioned CG
+                                  in the lumped-mass inner product (stop at
+                                  ||r||_M <= lin_rtol ||rhs||_M, warm start
+                                  V_n).  FP64 only                          */
+
 typedef struct emrkc_solver emrkc_solver; /* opaque; owns device memory */
 
 /* Sparse P1 stiffness in CSR and the row-sum lumped mass (Sec. 2.1).
@@ -120,11 +135,17 @@ typedef struct {
   double rho_S_min;   /* known bound on rho(f_S): the step uses
                          max(safety * estimate, rho_S_min) (Sec. 3.1: rho is
                          known or estimated); 0 = estimate only            */
+  int method;         /* EMRKC_METHOD_* (default EMRKC_METHOD_EMRKC)        */
+  double lin_rtol;    /* IMEX-RL: relative residual of the CG solve, 1e-10  */
+  int lin_max_iter;   /* IMEX-RL: CG iteration cap, 1000 (a solve that hits
+                         it is not an error; see emrkc_stats.lin_iters)     */
 } emrkc_options;
 
 /* Kernel classes reported in emrkc_stats.phase_ms / phase_launches. */
-#define EMRKC_PHASE_STAGE 0   /* fused RL + ionic + first SpMV + outer update */
-#define EMRKC_PHASE_INNER 1   /* inner RKC SpMV stage                         */
+#define EMRKC_PHASE_STAGE 0   /* fused RL + ionic + first SpMV + outer update
+                                 (EXEX-RL: the whole step; IMEX-RL: the ionic
+                                 half and the CG set-up)                      */
+#define EMRKC_PHASE_INNER 1   /* inner RKC SpMV stage (IMEX-RL: the CG solve) */
 #define EMRKC_PHASE_POWER_F 2 /* power iteration on f_F                       */
 #define EMRKC_PHASE_POWER_S 3 /* power iteration on f_S                       */
 #define EMRKC_PHASE_OTHER 4   /* norms, start vectors, f_S(y)                 */
@@ -143,6 +164,10 @@ typedef struct {
   int64_t matrix_slots;  /* sliced-ELL slots including padding         */
   double phase_ms[EMRKC_NUM_PHASES];       /* needs options.profile    */
   int64_t phase_launches[EMRKC_NUM_PHASES];
+  int lin_iters;         /* IMEX-RL: CG iterations of the last step    */
+  int64_t total_lin_iters; /* IMEX-RL: CG iterations since create      */
+  double lin_residual;   /* IMEX-RL: ||r||_M / ||rhs||_M after the last
+                            solve                                      */
 } emrkc_stats;
 
 /* Fill *opt with the defaults listed above (FP64, rho every step, seed 0,

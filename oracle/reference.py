@@ -74,3 +74,37 @@ class ImexRL:
         rhs = p.Cm * p.M * V + dt * p.M * (p.I_stim(t) - I_ion)
         out[0] = self.lu.solve(rhs)
         return out
+
+
+class RLRun:
+    """Time-stepping driver for EXEX-RL / IMEX-RL (Sec. 5, Algorithm 4) with
+    activation times: first upward crossing of the threshold, linearly
+    interpolated within the step (the same definition as OracleRun)."""
+
+    def __init__(self, prob, method, dt, act_threshold=-20.0):
+        if method not in ("exex", "imex"):
+            raise ValueError("method must be 'exex' or 'imex'")
+        self.p = prob
+        self.method = method
+        self.dt = dt
+        self.imex = ImexRL(prob, dt) if method == "imex" else None
+        self.Y = prob.initial_state()
+        self.t = 0.0
+        self.steps = 0
+        self.th = act_threshold
+        self.act = np.full(prob.n, np.nan)
+
+    def step(self):
+        V_old = self.Y[0].copy()
+        if self.method == "imex":
+            Y = self.imex.step(self.t, self.Y)
+        else:
+            Y = exex_rl_step(self.p, self.t, self.Y, self.dt)
+        V_new = Y[0]
+        cross = np.isnan(self.act) & (V_old < self.th) & (V_new >= self.th)
+        if np.any(cross):
+            self.act[cross] = self.t + self.dt * (self.th - V_old[cross]) / (V_new[cross] - V_old[cross])
+        self.Y = Y
+        self.t += self.dt
+        self.steps += 1
+        return Y

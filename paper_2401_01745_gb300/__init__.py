@@ -18,6 +18,7 @@ from ._ffi import Matrix, Options, OwnedMatrix, Stats, Stimulus, Tissue
 MODEL_NONE, MODEL_PASSIVE, MODEL_HH, MODEL_TTP06 = 0, 1, 2, 3
 PREC_FP64, PREC_MIXED = 0, 1
 RHO_ONCE, RHO_FIXED = 0, -1
+METHOD_EMRKC, METHOD_EXEX_RL, METHOD_IMEX_RL = 0, 1, 2
 
 
 class EmrkcError(RuntimeError):
@@ -81,7 +82,7 @@ class Solver:
                  amplitude=50.0, t_on=0.0, t_off=1.0, precision=PREC_FP64, rho_every=1,
                  rho_F=0.0, rho_S=0.0, seed=0, act_threshold=-20.0, stream=None, device=0,
                  profile=False, use_graphs=True, pow_tol=1e-2, pow_max_iter=50, safety=1.05,
-                 rho_S_min=0.0):
+                 rho_S_min=0.0, method=0, lin_rtol=1e-10, lin_max_iter=1000):
         self._lib = lib()
         self._h = C.c_void_p()
         self.row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
@@ -116,6 +117,9 @@ class Solver:
         o.pow_max_iter = pow_max_iter
         o.safety = safety
         o.rho_S_min = rho_S_min
+        o.method = method
+        o.lin_rtol = lin_rtol
+        o.lin_max_iter = lin_max_iter
         rc = self._lib.emrkc_create(C.byref(mat), C.byref(tis), model, C.byref(stim), C.byref(o),
                                     C.byref(self._h))
         if rc != 0:

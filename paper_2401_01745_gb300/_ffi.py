@@ -42,7 +42,8 @@ class Options(C.Structure):
                 ("pow_tol", C.c_double), ("pow_eps", C.c_double), ("pow_max_iter", C.c_int),
                 ("seed", C.c_uint64), ("act_threshold", C.c_double), ("cuda_stream", C.c_void_p),
                 ("device", C.c_int), ("profile", C.c_int), ("use_graphs", C.c_int),
-                ("rho_S_min", C.c_double)]
+                ("rho_S_min", C.c_double), ("method", C.c_int), ("lin_rtol", C.c_double),
+                ("lin_max_iter", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -51,7 +52,8 @@ class Stats(C.Structure):
                 ("pow_iters_F", C.c_int), ("pow_iters_S", C.c_int), ("total_pow_iters", C.c_int64),
                 ("launches", C.c_int64), ("matrix_entries", C.c_int64), ("matrix_slots", C.c_int64),
                 ("phase_ms", C.c_double * NUM_PHASES),
-                ("phase_launches", C.c_int64 * NUM_PHASES)]
+                ("phase_launches", C.c_int64 * NUM_PHASES), ("lin_iters", C.c_int),
+                ("total_lin_iters", C.c_int64), ("lin_residual", C.c_double)]
 
 
 class BatchInfo(C.Structure):

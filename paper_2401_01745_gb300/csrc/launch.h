@@ -160,6 +160,60 @@ struct KernelSet {
   int (*tma_grid)(int device, int wmax) = nullptr;  // grid of the persistent stage kernel (0: not used)
 };
 
+// EXEX-RL / IMEX-RL steps (rl_methods.cu, FP64).  One step reads the state
+// buffer (V, Z) and writes (Vout, Zout).
+struct RlArgs {
+  int64_t n = 0, ld = 0;
+  const double* V = nullptr;
+  const double* Z = nullptr;     // NZ rows of ld
+  double* Vout = nullptr;        // EXEX: V_{n+1}; IMEX: x_0 = V_n
+  double* Zout = nullptr;
+  const uint8_t* mask = nullptr;
+  double stim = 0, inv_Cm = 1, dt = 0;
+  double* act = nullptr;
+  double t_n = 0, threshold = 0;
+  int* flags = nullptr;
+  // IMEX set-up
+  const double* mass = nullptr;  // lumped mass M_i
+  double* r = nullptr;
+  double* zr = nullptr;
+  double* pinv = nullptr;        // 1 / (1 - dt L_ii)
+  double* part0 = nullptr;       // 4 per set-up CTA
+};
+
+constexpr int kPcgBlock = 256;
+
+struct PcgArgs {
+  int64_t n = 0;
+  double dt = 0, rtol = 0;
+  int max_iter = 0;
+  long long spin_limit = 0;
+  const double* mass = nullptr;
+  const double* pinv = nullptr;
+  const double* Vn = nullptr;
+  double* x = nullptr;
+  double* r = nullptr;
+  double* zr = nullptr;
+  double* q = nullptr;
+  double* p0 = nullptr;
+  double* p1 = nullptr;
+  double* part = nullptr;         // 4 per CTA of the PCG launch
+  const double* part0 = nullptr;  // set-up partials
+  int n_part0 = 0;
+  double* res = nullptr;          // out: [0] final <r, r>_M, [1] <c, c>_M
+  unsigned int* bar = nullptr;    // grid barrier: [0] arrivals, [1] generation
+  unsigned long long* iters = nullptr;  // [0] last solve, [1] running total
+  int* flags = nullptr;
+  double* act = nullptr;
+  double t_n = 0, threshold = 0;
+};
+
+int rl_exex_step(int model, const RlArgs& a, const Ell& A, cudaStream_t st);
+int rl_imex_setup(int model, const RlArgs& a, const Ell& A, cudaStream_t st);
+int rl_imex_setup_grid(int64_t n);
+int pcg_grid(int device);
+cudaError_t rl_imex_pcg(const PcgArgs& a, const Ell& A, int grid, cudaStream_t st);
+
 // Float-float V of the mixed path: split a double into hi + lo, and join.
 void launch_ff_split(const double* v, float* hi, float* lo, int64_t count, cudaStream_t st);
 void launch_ff_join(const float* hi, const float* lo, double* v, int64_t count, cudaStream_t st);

@@ -50,7 +50,8 @@ void free_all(emrkc_solver* s) {
                   s->d_vF2, s->d_vS, s->d_vS2, s->d_fy, s->d_act, s->d_Vn, s->d_tmp, s->d_rest, s->d_flags,
                   s->rs.partials, s->rs.ticket, s->rs.result, s->d_V32[0], s->d_V32[1], s->d_V32[2],
                   s->d_D[0], s->d_D[1], s->d_D[2], s->d_LV, s->d_Vlo[0], s->d_Vlo[1], s->d_Vlo[2],
-                  s->d_Vn32};
+                  s->d_Vn32, s->d_mass, s->d_cg[0], s->d_cg[1], s->d_cg[2], s->d_cg[3], s->d_cg[4],
+                  s->d_cg[5], s->d_part, s->d_bar, s->d_iters, s->d_res};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (s->h_pin) cudaFreeHost(s->h_pin);
@@ -78,6 +79,12 @@ int check_flags(emrkc_solver* s) {
     cudaMemcpyAsync(s->d_flags, &zero, sizeof(int), cudaMemcpyHostToDevice, s->stream);
     cudaStreamSynchronize(s->stream);
     return s->fail(EMRKC_ERR_NONFINITE, "non-finite transmembrane potential produced by a step");
+  }
+  if (flags & 4) {
+    int zero = 0;
+    cudaMemcpyAsync(s->d_flags, &zero, sizeof(int), cudaMemcpyHostToDevice, s->stream);
+    cudaStreamSynchronize(s->stream);
+    return s->fail(EMRKC_ERR_TIMEOUT, "a grid barrier of the CG solve gave up");
   }
   return EMRKC_OK;
 }
@@ -193,7 +200,75 @@ int power_S(emrkc_solver* s) {
   return EMRKC_OK;
 }
 
+// EXEX-RL and IMEX-RL (Algorithm 4), FP64; state buffers cur -> cur + 1.
+int do_step_rl(emrkc_solver* s, double dt) {
+  const int b0 = s->cur, b1 = (s->cur + 1) % 3;
+  RlArgs a;
+  a.n = s->n;
+  a.ld = s->ld;
+  a.V = s->d_V[b0];
+  a.Z = static_cast<const double*>(s->d_Z[b0]);
+  a.Vout = s->d_V[b1];
+  a.Zout = static_cast<double*>(s->d_Z[b1]);
+  a.mask = s->d_mask;
+  a.stim = stim_at(s, s->t);
+  a.inv_Cm = 1.0 / s->Cm;
+  a.dt = dt;
+  a.act = s->act_on ? s->d_act : nullptr;
+  a.t_n = s->t;
+  a.threshold = s->opt.act_threshold;
+  a.flags = s->d_flags;
+  if (s->method == EMRKC_METHOD_EXEX_RL) {
+    s->launch(EMRKC_PHASE_STAGE, [&] { rl_exex_step(s->model, a, s->ell, s->stream); });
+  } else {
+    a.mass = s->d_mass;
+    a.r = s->d_cg[0];
+    a.zr = s->d_cg[1];
+    a.pinv = s->d_cg[5];
+    a.part0 = s->d_part;
+    s->launch(EMRKC_PHASE_STAGE, [&] { rl_imex_setup(s->model, a, s->ell, s->stream); });
+    PcgArgs c;
+    c.n = s->n;
+    c.dt = dt;
+    c.rtol = s->opt.lin_rtol;
+    c.max_iter = s->opt.lin_max_iter;
+    c.spin_limit = 1ll << 26;
+    c.mass = s->d_mass;
+    c.pinv = s->d_cg[5];
+    c.Vn = s->d_V[b0];
+    c.x = s->d_V[b1];
+    c.r = s->d_cg[0];
+    c.zr = s->d_cg[1];
+    c.q = s->d_cg[2];
+    c.p0 = s->d_cg[3];
+    c.p1 = s->d_cg[4];
+    c.part0 = s->d_part;
+    c.n_part0 = rl_imex_setup_grid(s->n);
+    c.part = s->d_part + 4 * kReduceMaxBlocks;
+    c.res = s->d_res;
+    c.bar = s->d_bar;
+    c.iters = s->d_iters;
+    c.flags = s->d_flags;
+    c.act = a.act;
+    c.t_n = s->t;
+    c.threshold = s->opt.act_threshold;
+    cudaError_t e = cudaMemsetAsync(s->d_bar, 0, 2 * sizeof(unsigned int), s->stream);
+    if (e != cudaSuccess) return s->cuda_fail(e, "barrier reset");
+    s->launch(EMRKC_PHASE_INNER, [&] { e = rl_imex_pcg(c, s->ell, s->pcg_grid, s->stream); });
+    if (e != cudaSuccess) return s->cuda_fail(e, "cooperative CG launch");
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return s->cuda_fail(e, "kernel launch");
+  s->cur = b1;
+  s->t += dt;
+  s->steps += 1;
+  s->last_s = s->last_m = 0;
+  s->last_eta = 0.0;
+  return EMRKC_OK;
+}
+
 int do_step(emrkc_solver* s, double dt) {
+  if (s->method != EMRKC_METHOD_EMRKC) return do_step_rl(s, dt);
   int rc;
   double rhoF, rhoS;
   s->itF = s->itS = 0;
@@ -542,6 +617,9 @@ int emrkc_default_options(emrkc_options* o) {
   o->profile = 0;
   o->use_graphs = 1;
   o->rho_S_min = 0.0;
+  o->method = EMRKC_METHOD_EMRKC;
+  o->lin_rtol = 1e-10;
+  o->lin_max_iter = 1000;
   return EMRKC_OK;
 }
 
@@ -597,6 +675,18 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
     g_create_error = "options: rho_S_min must be finite and >= 0";
     return EMRKC_ERR_ARG;
   }
+  if (o.method < EMRKC_METHOD_EMRKC || o.method > EMRKC_METHOD_IMEX_RL) {
+    g_create_error = "options: unknown method";
+    return EMRKC_ERR_ARG;
+  }
+  if (o.method != EMRKC_METHOD_EMRKC && o.precision != EMRKC_PREC_FP64) {
+    g_create_error = "options: EXEX-RL and IMEX-RL run in FP64 only";
+    return EMRKC_ERR_ARG;
+  }
+  if (o.method == EMRKC_METHOD_IMEX_RL && (!(o.lin_rtol >= 0) || o.lin_max_iter < 0)) {
+    g_create_error = "options: lin_rtol must be >= 0 and lin_max_iter >= 0";
+    return EMRKC_ERR_ARG;
+  }
   if (o.rho_every == EMRKC_RHO_FIXED && (!(o.rho_F >= 0) || !(o.rho_S >= 0))) {
     g_create_error = "options: fixed rho values must be >= 0";
     return EMRKC_ERR_ARG;
@@ -613,6 +703,7 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
   cudaSetDevice(s->device);
   s->model = ionic_model;
   s->precision = o.precision;
+  s->method = o.method;
   const bool ok = (s->precision == EMRKC_PREC_FP64) ? get_kernels_fp64(ionic_model, &s->ks)
                                                     : get_kernels_mixed(ionic_model, &s->ks);
   if (!ok) {
@@ -680,7 +771,25 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
   fail |= dalloc(&s->rs.partials, kReduceMaxBlocks) != cudaSuccess;
   fail |= dalloc(&s->rs.ticket, 4) != cudaSuccess;
   fail |= dalloc(&s->rs.result, 16) != cudaSuccess;
+  if (s->method == EMRKC_METHOD_IMEX_RL) {
+    s->pcg_grid = pcg_grid(s->device);
+    fail |= s->pcg_grid <= 0;
+    fail |= dalloc(&s->d_mass, ld) != cudaSuccess;
+    for (int k = 0; k < 6; ++k) fail |= dalloc(&s->d_cg[k], ld) != cudaSuccess;
+    fail |= dalloc(&s->d_part, 4 * (int64_t)(kReduceMaxBlocks + std::max(s->pcg_grid, 1))) != cudaSuccess;
+    fail |= dalloc(&s->d_bar, 2) != cudaSuccess;
+    fail |= dalloc(&s->d_iters, 2) != cudaSuccess;
+    fail |= dalloc(&s->d_res, 2) != cudaSuccess;
+  }
   if (fail) return bail(EMRKC_ERR_OOM, "device allocation failed");
+  if (s->d_mass) {
+    cudaMemsetAsync(s->d_mass, 0, ld * sizeof(double), s->stream);
+    cudaMemcpyAsync(s->d_mass, mat->lumped_mass, s->n * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+    for (int k = 0; k < 6; ++k) cudaMemsetAsync(s->d_cg[k], 0, ld * sizeof(double), s->stream);
+    cudaMemsetAsync(s->d_bar, 0, 2 * sizeof(unsigned int), s->stream);
+    cudaMemsetAsync(s->d_iters, 0, 2 * sizeof(unsigned long long), s->stream);
+    cudaMemsetAsync(s->d_res, 0, 2 * sizeof(double), s->stream);
+  }
   if ((e = cudaMallocHost(&s->h_pin, 16 * sizeof(double))) != cudaSuccess) return bail(EMRKC_ERR_OOM, "pinned allocation failed");
   std::memset(s->h_pin, 0, 16 * sizeof(double));
   if (stim && stim->node_mask) {
@@ -814,6 +923,16 @@ int emrkc_get_stats(emrkc_solver* s, emrkc_stats* out) {
   for (int k = 0; k < EMRKC_NUM_PHASES; ++k) {
     out->phase_ms[k] = s->phase_ms[k];
     out->phase_launches[k] = s->phase_launches[k];
+  }
+  if (s->d_iters) {
+    unsigned long long it[2] = {0, 0};
+    double res[2] = {0, 0};
+    cudaStreamSynchronize(s->stream);
+    cudaMemcpy(it, s->d_iters, sizeof(it), cudaMemcpyDeviceToHost);
+    cudaMemcpy(res, s->d_res, sizeof(res), cudaMemcpyDeviceToHost);
+    out->lin_iters = (int)it[0];
+    out->total_lin_iters = (int64_t)it[1];
+    out->lin_residual = res[1] > 0 ? std::sqrt(res[0] / res[1]) : 0.0;
   }
   return EMRKC_OK;
 }

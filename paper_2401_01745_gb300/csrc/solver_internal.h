@@ -147,6 +147,15 @@ struct emrkc_solver {
   int64_t total_it = 0, launches = 0;
   int64_t mat_entries = 0, mat_slots = 0;
   int tma_grid = 0;  // persistent bulk-copy stage kernel grid (mixed path), 0 = off
+  // EXEX-RL / IMEX-RL (rl_methods.cu)
+  int method = 0;
+  double* d_mass = nullptr;     // lumped mass (IMEX-RL)
+  double* d_cg[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // r, z, q, p0, p1, P^-1
+  double* d_part = nullptr;     // CG partial sums: 4 per CTA, set-up then solve
+  unsigned int* d_bar = nullptr;        // grid barrier of the CG launch
+  unsigned long long* d_iters = nullptr;  // CG iterations: last, total
+  double* d_res = nullptr;      // final <r, r>_M, <c, c>_M
+  int pcg_grid = 0;
   int ell_wmax = 0;  // widest sliced-ELL slice
   bool act_on = false;
   double phase_ms[EMRKC_NUM_PHASES] = {0};

@@ -53,6 +53,7 @@ def test_default_options(lib):
     o = pkg.default_options()
     assert o.eps == 0.05 and o.safety == 1.05 and o.pow_tol == 1e-2 and o.pow_eps == 1e-8
     assert o.rho_every == 1 and o.precision == 0 and o.act_threshold == -20.0
+    assert o.method == 0 and o.lin_rtol == 1e-10 and o.lin_max_iter == 1000
 
 
 def _csr_dense(rp, col, K, n):
@@ -118,4 +119,14 @@ def test_create_validates_arguments(lib):
     assert ei.value.code == 1
     with pytest.raises(pkg.EmrkcError) as ei:
         pkg.Solver(rp, col, K, M, model=9)
+    assert ei.value.code == 1
+    with pytest.raises(pkg.EmrkcError) as ei:  # unknown time integrator
+        pkg.Solver(rp, col, K, M, method=7)
+    assert ei.value.code == 1
+    for method in (pkg.METHOD_EXEX_RL, pkg.METHOD_IMEX_RL):  # Algorithm 4 runs in FP64 only
+        with pytest.raises(pkg.EmrkcError) as ei:
+            pkg.Solver(rp, col, K, M, method=method, precision=pkg.PREC_MIXED)
+        assert ei.value.code == 1
+    with pytest.raises(pkg.EmrkcError) as ei:
+        pkg.Solver(rp, col, K, M, method=pkg.METHOD_IMEX_RL, lin_max_iter=-1)
     assert ei.value.code == 1

@@ -8,7 +8,10 @@ Independent facts used:
   * conservation of sum_i M_ii V_i under pure diffusion with Neumann BC;
   * x <-> y mirror symmetry of the right-diagonal mesh with a corner stimulus;
   * first-order convergence against fine-step RK4 (Thm. 4.5, Sec. 5.2);
-  * closed-form largest eigenvalue for the power iteration (Algorithm 5).
+  * closed-form largest eigenvalue for the power iteration (Algorithm 5);
+  * Algorithm 4 on the same eigenvector: explicit Euler multiplies V by
+    1 + dt (lF + lS), the implicit diffusion step by (1 + dt lS) / (1 - dt lF),
+    the gate relaxes exactly and z_S takes one explicit Euler step.
 """
 
 import math
@@ -22,7 +25,7 @@ from oracle.emrkc import Monodomain, OracleRun
 from oracle.fem import assemble_p1
 from oracle.ionic import NoModel, PassiveModel, make_model
 from oracle.power import compute_rho, start_vector
-from oracle.reference import ImexRL, exex_rl_step, rk4_run
+from oracle.reference import ImexRL, RLRun, exex_rl_step, rk4_run
 from oracle.rkc import EPS_DAMP, get_stages
 from workloads import isotropic_D, line_mesh, make_workload, square_tri_mesh
 
@@ -224,3 +227,45 @@ def test_imex_rl_first_order_and_exex_agreement():
         Y = exex_rl_step(prob, t, Y, dt)
         t += dt
     assert _rel_l2(prob, Y[0], Yref[0]) < 5e-3
+
+
+@pytest.mark.parametrize("dt", [0.01, 0.2])
+@pytest.mark.parametrize("k", [2, 9])
+def test_rl_methods_closed_form_eigenvector(dt, k):
+    n, L = 20, 0.19
+    h = L / (n - 1)
+    chi, Cm, sigma = 1400.0, 1.0, 1.1
+    coords, prob = _line_problem(n, L, PassiveModel(), chi, Cm, sigma)
+    x = coords[:, 0]
+    Y = prob.initial_state()
+    Y[0] = np.cos(k * np.pi * x / L)
+    Y[1] = 0.8
+    Y[2] = -0.6
+    pm = PassiveModel()
+    lamF = -(4 * sigma / (h * h * chi * Cm)) * np.sin(k * np.pi / (2 * (n - 1))) ** 2
+    lamS = -pm.g_p / Cm
+    lamE = -(pm.a_w + pm.b_w)
+    winf = pm.a_w / (pm.a_w + pm.b_w)
+    Ye = exex_rl_step(prob, 0.0, Y, dt)
+    Yi = ImexRL(prob, dt).step(0.0, Y)
+    np.testing.assert_allclose(Ye[0], (1 + dt * (lamF + lamS)) * Y[0], rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(Yi[0], (1 + dt * lamS) / (1 - dt * lamF) * Y[0], rtol=1e-12, atol=1e-13)
+    for Y1 in (Ye, Yi):
+        np.testing.assert_allclose(Y1[1] - winf, math.exp(dt * lamE) * (Y[1] - winf), rtol=1e-13, atol=1e-15)
+        np.testing.assert_allclose(Y1[2], (1 - dt * pm.k_c) * Y[2], rtol=1e-13, atol=1e-15)
+
+
+def test_rl_driver_activation_times():
+    w = make_workload("square9x9_hh", h=0.5 / 8)
+    prob = Monodomain.from_workload(w)
+    r = RLRun(prob, "imex", 0.05)
+    for _ in range(400):
+        r.step()
+    a = r.act
+    assert np.isfinite(a).all()
+    # the stimulated corner activates first, the far corner last, and the
+    # activation time grows along the first row and along the diagonal
+    d = np.hypot(w.coords[:, 0], w.coords[:, 1])
+    assert a[np.argmin(d)] == a.min() and a[np.argmax(d)] == a.max()
+    A = a.reshape(9, 9)
+    assert np.all(np.diff(A[0, 1:]) > 0) and np.all(np.diff(np.diag(A)) > 0)
