@@ -56,7 +56,10 @@ def _sources_sha256(paths):
     return h.hexdigest()
 
 
-HH_RHO_S_MAX = 42.0  # Table 2 rho_max of HH (40) times the safety factor 1.05
+HH_RHO_S_MAX = 42.0
+# largest rho(f_S) of TTP06 over an action potential (the upstroke value of
+# the power iteration, 6.5 1/ms) times the safety factor 1.05, rounded up
+TTP_RHO_S_MAX = 7.0  # Table 2 rho_max of HH (40) times the safety factor 1.05
 METRIC = "node-timesteps/s (emRKC step, <=1e-3 rel. L2 error in V vs plain FP64)"
 UNIT = "node-timesteps/s"
 
@@ -409,6 +412,167 @@ def run_shell(args):
     return 0
 
 
+def run_compare(args):
+    """Work-precision comparison on the 3-D cuboid (Sec. 5.3 shape): emRKC
+    (FP64 and mixed) against IMEX-RL (Algorithm 4, FP64, CG to lin_rtol) at
+    several dt, errors in V at T against a fine-step EXEX-RL reference (Sec. 5
+    uses EXEX-RL at dt = 1e-4 ms; here dt_ref, stated in the output).  Each
+    run is timed with CUDA events around all its steps (state resident, no L2
+    flush: the 58k-node state fits in L2)."""
+    import torch
+
+    import paper_2401_01745_gb300 as pkg
+    from workloads import make_workload
+
+    world, rank, local = _dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pkg.build()
+    w = make_workload("slab101x36x16_ttp", h=0.02, t_off=2.0)
+    T, dt_ref = args.compare_T, args.compare_dt_ref
+    rp, col, K, M = pkg.assemble_p1(w.coords, w.cells, w.D)
+    stream = torch.cuda.Stream(device=dev)
+
+    def solve(method, prec, dt, profile=False, **kw):
+        sol = pkg.Solver(rp, col, K, M, chi=w.chi, Cm=w.Cm, model=w.model, mask=w.stim_mask,
+                         amplitude=w.stim_amp, t_on=w.t_on, t_off=w.t_off, precision=prec, rho_every=0,
+                         stream=stream.cuda_stream, device=local, method=method, profile=profile, **kw)
+        H = int(round(T / dt))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(H):
+                sol.step(dt)
+            e1.record(stream)
+        sol.sync()
+        ms = e0.elapsed_time(e1)
+        st = sol.stats()
+        V = sol.get_state(var=0)
+        sol.close()
+        return V, ms, H, st
+
+    def rel(V, Vr):
+        return float(np.sqrt(np.sum(M * (V - Vr) ** 2) / np.sum(M * Vr * Vr)))
+
+    # warm-up (module load, clocks)
+    solve(pkg.METHOD_EMRKC, pkg.PREC_MIXED, 0.1)
+    with ClockSampler(local) as clk:
+        Vref, ms_ref, H_ref, _ = solve(pkg.METHOD_EXEX_RL, pkg.PREC_FP64, dt_ref)
+        rows = []
+        for dt in args.compare_dts:
+            for name, method, prec in (("emRKC-fp64", pkg.METHOD_EMRKC, pkg.PREC_FP64),
+                                       ("emRKC-mixed", pkg.METHOD_EMRKC, pkg.PREC_MIXED),
+                                       ("IMEX-RL-fp64", pkg.METHOD_IMEX_RL, pkg.PREC_FP64)):
+                kw = {"lin_rtol": args.lin_rtol} if method == pkg.METHOD_IMEX_RL else {}
+                V, ms, H, st = solve(method, prec, dt, **kw)
+                r = {"method": name, "dt": dt, "steps": H, "ms": ms, "ms_per_step": ms / H, "rel_err_V": rel(V, Vref)}
+                if method == pkg.METHOD_IMEX_RL:
+                    r["cg_iters_per_step"] = st["total_lin_iters"] / H
+                else:
+                    r["s"], r["m"] = st["s"], st["m"]
+                rows.append(r)
+        # F wedge (Sec. 5.5): time in f_F work per step, dt = 0.05 ms, FP64 on both sides
+        _, _, He, se = solve(pkg.METHOD_EMRKC, pkg.PREC_FP64, 0.05, profile=True)
+        _, _, Hi, si = solve(pkg.METHOD_IMEX_RL, pkg.PREC_FP64, 0.05, profile=True, lin_rtol=args.lin_rtol)
+    wedge = {"dt": 0.05,
+             "emrkc_inner_spmv_ms_per_step": se["phase_ms"]["inner"] / He,
+             "emrkc_stage_ms_per_step": se["phase_ms"]["stage"] / He,
+             "emrkc_s_m": [se["s"], se["m"]],
+             "imex_cg_solve_ms_per_step": si["phase_ms"]["inner"] / Hi,
+             "imex_ionic_setup_ms_per_step": si["phase_ms"]["stage"] / Hi,
+             "imex_cg_iters_per_step": si["total_lin_iters"] / Hi,
+             "note": ("emRKC fuses its first f_F evaluation into the stage kernel (with the ionic model); its "
+                      "separate f_F work is the inner-stage SpMV kernel")}
+    best = {}
+    for r in rows:
+        if r["rel_err_V"] <= args.compare_target:
+            b = best.get(r["method"])
+            if b is None or r["ms"] < b["ms"]:
+                best[r["method"]] = r
+    out = {"metric": "work-precision: wall ms to T vs rel. L2 error in V", "unit": "ms", "n_gpus": 1,
+           "higher_is_better": False, "dtype": "mixed", "data": "synthetic",
+           "config": {"workload": "slab 101x36x16 nodes (h = 0.02 cm, 2.0x0.7x0.3 cm, 58,176 nodes), D = "
+                                  "diag(1.33, 0.18, 0.18), TTP06 epi, corner stimulus 2 ms", "T_ms": T,
+                      "reference": f"EXEX-RL FP64 at dt = {dt_ref} ms ({H_ref} steps, {ms_ref:.0f} ms)",
+                      "imex_lin_rtol": args.lin_rtol, "rho_policy": "once at t = 0"},
+           "runs": rows, "fastest_within_target": {"target_rel_err": args.compare_target, **best},
+           "f_wedge": wedge, "clocks": clk.summary()}
+    print(json.dumps(out))
+    return 0
+
+
+def run_stability(args):
+    """Practical stability (Sec. 5.1): the 1-D TTP06 cable at dx = 0.025 mm up
+    to T = 100 ms with increasing dt; the relative norm ||V_N|| / ||V*|| (V*:
+    emRKC FP64 at dt = 0.01 ms) and the stage counts, for emRKC (FP64 and
+    mixed, rho once at t = 0); and the largest stable dt of EXEX-RL."""
+    import torch
+
+    import paper_2401_01745_gb300 as pkg
+    from workloads import make_workload
+
+    world, rank, local = _dist_init()
+    torch.cuda.set_device(local)
+    pkg.build()
+    w = make_workload("cable_ttp")
+    rp, col, K, M = pkg.assemble_p1(w.coords, w.cells, w.D)
+
+    def solve(dt, T, prec, method=0, rho_every=0, rho_S_min=0.0):
+        sol = pkg.Solver(rp, col, K, M, chi=w.chi, Cm=w.Cm, model=w.model, mask=w.stim_mask,
+                         amplitude=w.stim_amp, t_on=w.t_on, t_off=w.t_off, precision=prec, rho_every=rho_every,
+                         device=local, method=method, rho_S_min=rho_S_min)
+        ok = True
+        try:
+            for _ in range(int(round(T / dt))):
+                sol.step(dt)
+            sol.sync()
+        except pkg.EmrkcError:
+            ok = False
+        st = sol.stats()
+        V = sol.get_state(var=0) if ok else None
+        sol.close()
+        return V, st, ok
+
+    Vref, _, _ = solve(0.01, 100.0, pkg.PREC_FP64)
+    nref = float(np.sqrt(M @ (Vref * Vref)))
+    rows = []
+    policies = ((pkg.PREC_FP64, "fp64", 0, 0.0, "once"), (pkg.PREC_MIXED, "mixed", 0, 0.0, "once"),
+                (pkg.PREC_FP64, "fp64", 1, 0.0, "every step"),
+                (pkg.PREC_FP64, "fp64", 0, TTP_RHO_S_MAX, f"once, rho_S >= {TTP_RHO_S_MAX}"),
+                (pkg.PREC_MIXED, "mixed", 0, TTP_RHO_S_MAX, f"once, rho_S >= {TTP_RHO_S_MAX}"))
+    for prec, pname, rho_every, rho_min, label in policies:
+        for dt in args.stability_dts:
+            V, st, ok = solve(dt, 100.0, prec, rho_every=rho_every, rho_S_min=rho_min)
+            fin = ok and bool(np.all(np.isfinite(V)))
+            rows.append({"precision": pname, "rho": label, "dt": dt,
+                         "s": st["s"], "m": st["m"],
+                         "rel_norm": float(np.sqrt(M @ (V * V)) / nref) if fin else None,
+                         "rel_err": float(np.sqrt(M @ ((V - Vref) ** 2)) / nref) if fin else None,
+                         "finite": fin})
+    exex = []
+    for dt in (0.001, 0.002, 0.003, 0.0035, 0.004, 0.005):
+        V, _, ok = solve(dt, 20.0, pkg.PREC_FP64, pkg.METHOD_EXEX_RL)
+        exex.append({"dt": dt, "bounded": bool(ok and np.all(np.abs(V) < 200))})
+    stable = [r["dt"] for r in rows if r["precision"] == "fp64" and r["rho"] == "once" and r["finite"]
+              and 0.5 < r["rel_norm"] < 1.5]
+    stable_every = [r["dt"] for r in rows if r["rho"] == "every step" and r["finite"] and 0.5 < r["rel_norm"] < 1.5]
+    stable_bound = [r["dt"] for r in rows if r["rho"].startswith("once, rho_S") and r["precision"] == "fp64"
+                    and r["finite"] and 0.5 < r["rel_norm"] < 1.5]
+    out = {"metric": "practical stability: largest dt with a bounded solution", "unit": "ms",
+           "value": max(stable) if stable else None, "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
+           "config": {"workload": "cable: [0, 2] cm, dx = 0.0025 cm (801 nodes), sigma 1.33 mS/cm, TTP06 epi, "
+                                  "stimulus x <= 0.15 cm for t <= 2 ms, T = 100 ms",
+                      "reference": "emRKC FP64 at dt = 0.01 ms",
+                      "rho_policy": "value: once at t = 0 (FP64); rows also for every step"},
+           "largest_bounded_dt_rho_every_step": max(stable_every) if stable_every else None,
+           "largest_bounded_dt_rho_S_bound": max(stable_bound) if stable_bound else None,
+           "emrkc": rows,
+           "exex_rl": {"T_ms": 20.0, "runs": exex,
+                       "largest_bounded_dt": max([e["dt"] for e in exex if e["bounded"]], default=None)}}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -428,6 +592,15 @@ def main():
     ap.add_argument("--shell", action="store_true", help="ventricle-like shell, mixed vs FP64 over T = 100 ms")
     ap.add_argument("--served", action="store_true", help="served form: request stream, p50/p99 latency")
     ap.add_argument("--requests", type=int, default=100)
+    ap.add_argument("--compare", action="store_true", help="work-precision: emRKC vs IMEX-RL vs EXEX-RL reference")
+    ap.add_argument("--compare-T", type=float, default=10.0)
+    ap.add_argument("--compare-dt-ref", type=float, default=2.5e-4)
+    ap.add_argument("--compare-dts", type=float, nargs="+", default=[0.4, 0.2, 0.1, 0.05, 0.025])
+    ap.add_argument("--compare-target", type=float, default=1e-2)
+    ap.add_argument("--lin-rtol", type=float, default=1e-8)
+    ap.add_argument("--stability", action="store_true", help="Sec. 5.1 practical-stability sweep on the 1-D cable")
+    ap.add_argument("--stability-dts", type=float, nargs="+",
+                    default=[0.05, 0.1, 0.25, 0.5, 1.0, 2.0, 3.0, 4.0, 4.5, 5.0, 6.0, 8.0])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -435,6 +608,10 @@ def main():
         return run_reference(args)
     if args.shell:
         return run_shell(args)
+    if args.compare:
+        return run_compare(args)
+    if args.stability:
+        return run_stability(args)
     if args.served:
         return run_served(args)
     if args.batched:

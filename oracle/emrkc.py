@@ -106,18 +106,34 @@ class Monodomain:
         u_eta = rkc_iteration(t, yE, eta, f_u, m, EPS_DAMP)
         return (u_eta - Y) / eta
 
+    def averaged_force_progressive(self, t, Y, eta, m):
+        """The alternative split of the auxiliary problem (Sec. 4.2, remark on
+        adding the exponential part progressively): u(0) = y and
+        u' = f_F(u) + f_S(y_E) + phi(eta Lambda(y)) f_E(y), where
+        phi(eta Lambda) f_E(y) = (y_E - y) / eta by the definition of y_E."""
+        yE = self.exponential_euler(Y, eta)
+        g = self.f_S(t, yE) + (yE - Y) / eta  # frozen during the inner iteration
+
+        def f_u(r, u):
+            return self.f_F(r, u) + g
+
+        u_eta = rkc_iteration(t, Y, eta, f_u, m, EPS_DAMP)
+        return (u_eta - Y) / eta
+
     def stage_counts(self, dt, rho_F, rho_S):
         s, l_s = get_stages(dt, rho_S, EPS_DAMP)
         eta = 2.0 * dt / l_s
         m, _ = get_stages(eta, rho_F, EPS_DAMP)
         return s, m, eta
 
-    def emrkc_step(self, t, Y, dt, rho_F, rho_S):
-        """One emRKC step; returns (y_{n+1}, s, m, eta)."""
+    def emrkc_step(self, t, Y, dt, rho_F, rho_S, progressive=False):
+        """One emRKC step; returns (y_{n+1}, s, m, eta).  progressive=True
+        uses the alternative split of the auxiliary problem."""
         s, m, eta = self.stage_counts(dt, rho_F, rho_S)
+        af = self.averaged_force_progressive if progressive else self.averaged_force
 
         def fbar(tt, yy):
-            return self.averaged_force(tt, yy, eta, m)
+            return af(tt, yy, eta, m)
 
         return rkc_iteration(t, Y, dt, fbar, s, EPS_DAMP), s, m, eta
 
@@ -145,8 +161,9 @@ class OracleRun:
 
     def __init__(self, prob: Monodomain, Y0=None, rho_every=1, fixed_rho=None, seed=0,
                  safety=SAFETY, act_threshold=-20.0, pow_tol=1e-2, pow_eps=1e-8, pow_max_iter=50,
-                 rho_S_min=0.0):
+                 rho_S_min=0.0, progressive=False):
         self.p = prob
+        self.progressive = progressive
         self.Y = prob.initial_state() if Y0 is None else np.array(Y0, dtype=np.float64)
         self.t = 0.0
         self.steps = 0
@@ -182,7 +199,7 @@ class OracleRun:
             rho_F = self.safety * self.rhoF_raw
             rho_S = max(self.safety * self.rhoS_raw, self.rho_S_min)
         V_old = self.Y[0].copy()
-        Y, s, m, eta = self.p.emrkc_step(self.t, self.Y, dt, rho_F, rho_S)
+        Y, s, m, eta = self.p.emrkc_step(self.t, self.Y, dt, rho_F, rho_S, self.progressive)
         V_new = Y[0]
         th = self.act_threshold
         cross = np.isnan(self.act) & (V_old < th) & (V_new >= th)

@@ -804,6 +804,11 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
   cudaMemsetAsync(s->rs.ticket, 0, 4 * sizeof(unsigned int), s->stream);
   cudaMemsetAsync(s->rs.result, 0, 16 * sizeof(double), s->stream);
   for (int b = 0; b < 3; ++b) cudaMemsetAsync(s->d_U[b], 0, ld * sizeof(double), s->stream);
+  // power-iteration iterates: the kernels write rows [0, n) only and the norms
+  // run over whole rows, so the padding must hold zeros in both buffers
+  cudaMemsetAsync(s->d_vF2, 0, ld * sizeof(double), s->stream);
+  cudaMemsetAsync(s->d_vS2, 0, (size_t)s->N * ld * sizeof(double), s->stream);
+  cudaMemsetAsync(s->d_fy, 0, (size_t)s->N * ld * sizeof(double), s->stream);
   // rest state in every buffer
   const auto rest = rest_state(ionic_model);
   cudaMemcpy(s->d_rest, rest.data(), rest.size() * sizeof(double), cudaMemcpyHostToDevice);

@@ -96,6 +96,21 @@ def test_fp64_parity_fixed_rho_many_stages(fixed):
     _assert_parity(Y, act, prob, ref)
 
 
+def test_fp64_parity_against_progressive_split():
+    """The GPU step also matches the oracle's progressive split of the
+    auxiliary problem (Sec. 4.2 remark), which coincides with Algorithm 3 for
+    this splitting of the monodomain system."""
+    w = make_workload("slab13x7x5_ttp", h=0.01)
+    w.dt = 0.1
+    fixed = (5000.0, 300.0)
+    Y, act, log, st, prob, ref, rlog = _run_pair(w, 25, fixed=fixed)
+    prog = OracleRun(prob, fixed_rho=fixed, progressive=True)
+    for _ in range(25):
+        prog.step(w.dt)
+    assert log == [(l[0], l[1]) for l in prog.log]
+    _assert_parity(Y, act, prob, prog)
+
+
 def test_fp64_parity_large_dt_ttp_fixed_rho():
     """dt = 0.25 ms through the TTP06 upstroke with s = 2, m = 2.  The rho
     policy is fixed here: during the upstroke the power iteration on f_S is
@@ -298,5 +313,5 @@ def test_tiny_meshes():
     for name in ["line2_hh", "line3_ttp", "square2x2_hh"]:
         w = make_workload(name)
         Y, act, log, st, prob, ref, rlog = _run_pair(w, 30)
-        assert log == rlog
+        assert log == rlog, (name, log, [(l[0], l[1], l[3]) for l in ref.log])
         _assert_parity(Y, act, prob, ref)

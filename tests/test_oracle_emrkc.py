@@ -9,6 +9,10 @@ Independent facts used:
   * x <-> y mirror symmetry of the right-diagonal mesh with a corner stimulus;
   * first-order convergence against fine-step RK4 (Thm. 4.5, Sec. 5.2);
   * closed-form largest eigenvalue for the power iteration (Algorithm 5);
+  * the progressive split of the auxiliary problem (Sec. 4.2 remark) equals
+    the split of Algorithm 3 up to rounding when f_F acts on V alone and f_E
+    on z_E alone: the inner RKC integrates the constant gate forcing exactly
+    (c_m = 1), so u_z(eta) = y_E;
   * Algorithm 4 on the same eigenvector: explicit Euler multiplies V by
     1 + dt (lF + lS), the implicit diffusion step by (1 + dt lS) / (1 - dt lF),
     the gate relaxes exactly and z_S takes one explicit Euler step.
@@ -269,3 +273,24 @@ def test_rl_driver_activation_times():
     assert a[np.argmin(d)] == a.min() and a[np.argmax(d)] == a.max()
     A = a.reshape(9, 9)
     assert np.all(np.diff(A[0, 1:]) > 0) and np.all(np.diff(np.diag(A)) > 0)
+
+
+@pytest.mark.parametrize("name,h,dt,fixed", [
+    ("square9x9_hh", 1.0 / 16, 0.05, (400.0, 60.0)),
+    ("slab7x5x4_ttp", 0.01, 0.1, (900.0, 30.0)),
+])
+def test_progressive_split_equals_algorithm3(name, h, dt, fixed):
+    w = make_workload(name, h=h)
+    prob = Monodomain.from_workload(w)
+    a = OracleRun(prob, fixed_rho=fixed)
+    b = OracleRun(prob, fixed_rho=fixed, progressive=True)
+    for _ in range(30):
+        sa, ma = a.step(dt)
+        sb, mb = b.step(dt)
+        assert (sa, ma) == (sb, mb)
+    assert sa >= 2 and ma >= 2
+    scale = np.max(np.abs(a.Y), axis=1, keepdims=True) + 1e-300
+    assert np.max(np.abs(a.Y - b.Y) / scale) <= 1e-11
+    # not vacuous: the exponential step moves the gates of the current state
+    yE = prob.exponential_euler(a.Y, 0.01)
+    assert np.max(np.abs(yE[1:1 + prob.nE] - a.Y[1:1 + prob.nE])) > 1e-4

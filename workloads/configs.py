@@ -27,7 +27,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .fields import axis_D, corner_mask, fibre_D, isotropic_D, radius_mask
+from .fields import axis_D, corner_mask, fibre_D, fibrosis_D, isotropic_D, radius_mask
 from .meshes import line_mesh, shell_tet_mesh, slab_tet_mesh, square_tri_mesh
 
 MODEL_NONE, MODEL_PASSIVE, MODEL_HH, MODEL_TTP06 = 0, 1, 2, 3
@@ -119,6 +119,27 @@ def make_workload(name: str, **kw) -> Workload:
         w = Workload(name, coords, cells, D, MODEL_TTP06,
                      radius_mask(coords, (0.0, 0.0, -rl_out), 0.3),
                      t_off=2.0, dt=0.05, T=100.0, rho_every=0)
+    elif name == "cable_ttp":
+        # Sec. 5.1 practical-stability set-up: [0, 2] cm at dx = 0.0025 cm (801
+        # nodes), sigma = 1.33 mS/cm, TTP06, stimulus on x <= 0.15 cm for
+        # t <= 2 ms, T = 100 ms
+        coords, cells = line_mesh(801, 2.0)
+        w = Workload(name, coords, cells, isotropic_D(cells.shape[0], 1, 1.33), MODEL_TTP06,
+                     (coords[:, 0] <= 0.15 + 1e-12).astype(np.uint8), t_off=2.0, dt=0.05, T=100.0,
+                     rho_every=0)
+    elif name.startswith("fibslab"):
+        # slab with fibrosis: fibres along x (sigma_l 1.33, sigma_t 0.18) and
+        # sigma_t = 0 where a seeded smooth random field (correlation length
+        # 0.05 cm) exceeds its median
+        dims, model = name[len("fibslab"):].split("_")
+        nx, ny, nz = (int(v) for v in dims.split("x"))
+        h = kw.pop("h", 0.01)
+        seed = kw.pop("seed", 11)
+        mid = {"hh": MODEL_HH, "ttp": MODEL_TTP06, "none": MODEL_NONE, "passive": MODEL_PASSIVE}[model]
+        w = _slab(nx, ny, nz, (nx - 1) * h, (ny - 1) * h, (nz - 1) * h, mid, name=name)
+        a_l = np.tile(np.array([1.0, 0.0, 0.0]), (w.cells.shape[0], 1))
+        w.D, fib = fibrosis_D(w.coords, w.cells, a_l, 1.33, 0.18, seed, 0.05)
+        w.extra["fibrotic_cells"] = fib
     elif name.startswith("square"):
         # squareNxM_model, e.g. square17x17_hh on [0, (N-1)h] with h from kw
         dims, model = name[len("square"):].split("_")
