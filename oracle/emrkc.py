@@ -8,7 +8,8 @@ z_E, the remaining rows z_S.  The split follows Eq. (mono_in_FSE):
   f_S(t, y) = (Cm^-1 (I_stim(t) - I_ion(y)), 0, g_S(y))
   f_E(y) = (0, Lambda_E (z_E - z_inf), 0)
 Algorithm 3 is followed literally, including the inner RKC iteration over
-the full state (no closed form for the constant z-components).
+the full state (no closed form for the constant z-components).  mRKC
+(Algorithm 2) with the stiffest-gate split of Sec. 3.3 is here too.
 """
 
 from __future__ import annotations
@@ -137,6 +138,70 @@ class Monodomain:
 
         return rkc_iteration(t, Y, dt, fbar, s, EPS_DAMP), s, m, eta
 
+    # -- mRKC (Algorithm 2) with the stiffest-gate split (Sec. 3.3) ----------
+    # f~_F = f_F + f_E^1 and f~_S = f_S + f_E^2 (Eq. mRCK_fFfS_monodomain),
+    # where f_E^1 holds the exponential-type term of the single stiffest gating
+    # variable (index k of z_E) and f_E^2 those of all other gates.
+    def f_E1(self, t, Y, k):
+        out = np.zeros_like(Y)
+        if self.nE:
+            V, zE, zS = self.parts(Y)
+            lam, zinf = self.model.gating(V, zE, zS)
+            out[1 + k] = lam[k] * (zE[k] - zinf[k])
+        return out
+
+    def f_E2(self, t, Y, k):
+        out = self.f_E(t, Y)
+        if self.nE:
+            out[1 + k] = 0.0
+        return out
+
+    def fF_tilde(self, t, Y, k):
+        return self.f_F(t, Y) + self.f_E1(t, Y, k)
+
+    def fS_tilde(self, t, Y, k):
+        return self.f_S(t, Y) + self.f_E2(t, Y, k)
+
+    def mrkc_averaged_force(self, t, Y, eta, m, k):
+        """Averaged_Force of Algorithm 2: m RKC stages over
+        u' = f~_F(u) + f~_S(t, y) (f~_S frozen) on [0, eta], u(0) = y."""
+        fS = self.fS_tilde(t, Y, k)
+
+        def f_u(r, u):
+            return self.fF_tilde(r, u, k) + fS
+
+        u_eta = rkc_iteration(t, Y, eta, f_u, m, EPS_DAMP)
+        return (u_eta - Y) / eta
+
+    def mrkc_step(self, t, Y, dt, rho_F, rho_S, k):
+        """One mRKC step (Algorithm 2); returns (y_{n+1}, s, m, eta)."""
+        s, m, eta = self.stage_counts(dt, rho_F, rho_S)
+
+        def fbar(tt, yy):
+            return self.mrkc_averaged_force(tt, yy, eta, m, k)
+
+        return rkc_iteration(t, Y, dt, fbar, s, EPS_DAMP), s, m, eta
+
+    def rho_Ft_fn(self, Y, k):
+        """f~_F restricted to its nonzero block (V, z_E[k]), as a function of
+        that block (the other components are held at Y)."""
+        n = self.n
+
+        def f(t, x):
+            Z = Y.copy()
+            Z[0] = x[:n]
+            Z[1 + k] = x[n:]
+            out = self.fF_tilde(t, Z, k)
+            return np.concatenate([out[0], out[1 + k]])
+
+        return f
+
+    def rho_St_fn(self, k):
+        def f(t, y):
+            return self.fS_tilde(t, y.reshape(self.N, self.n), k).ravel()
+
+        return f
+
     # -- spectral radii (Algorithm 5) ----------------------------------------
     def rho_F_fn(self, t, V):
         return self.diffusion(V)
@@ -161,9 +226,13 @@ class OracleRun:
 
     def __init__(self, prob: Monodomain, Y0=None, rho_every=1, fixed_rho=None, seed=0,
                  safety=SAFETY, act_threshold=-20.0, pow_tol=1e-2, pow_eps=1e-8, pow_max_iter=50,
-                 rho_S_min=0.0, progressive=False):
+                 rho_S_min=0.0, progressive=False, method="emrkc", stiff_gate=0):
         self.p = prob
         self.progressive = progressive
+        if method not in ("emrkc", "mrkc"):
+            raise ValueError("method must be 'emrkc' or 'mrkc'")
+        self.method = method
+        self.stiff_gate = stiff_gate
         self.Y = prob.initial_state() if Y0 is None else np.array(Y0, dtype=np.float64)
         self.t = 0.0
         self.steps = 0
@@ -171,7 +240,8 @@ class OracleRun:
         self.fixed_rho = fixed_rho
         self.safety = safety
         self.pow = dict(eps=pow_eps, tol=pow_tol, max_iter=pow_max_iter)
-        self.vF = start_vector(seed & 0xFFFFFFFFFFFFFFFF, prob.n)
+        # mRKC: f~_F acts on (V, z_E[k]), so its iterate has 2n entries
+        self.vF = start_vector(seed & 0xFFFFFFFFFFFFFFFF, prob.n * (2 if method == "mrkc" else 1))
         self.vS = start_vector(~seed & 0xFFFFFFFFFFFFFFFF, prob.N * prob.n)
         self.rhoF_raw = 0.0
         self.rhoS_raw = 0.0
@@ -182,6 +252,14 @@ class OracleRun:
 
     def update_rho(self):
         itF = itS = 0
+        if self.method == "mrkc":
+            k = self.stiff_gate
+            x = np.concatenate([self.Y[0], self.Y[1 + k]])
+            self.vF, self.rhoF_raw, itF = compute_rho(self.t, x, self.p.rho_Ft_fn(self.Y, k), self.vF,
+                                                      self.rhoF_raw, **self.pow)
+            self.vS, self.rhoS_raw, itS = compute_rho(self.t, self.Y.ravel(), self.p.rho_St_fn(k), self.vS,
+                                                      self.rhoS_raw, **self.pow)
+            return itF, itS
         self.vF, self.rhoF_raw, itF = compute_rho(self.t, self.Y[0], self.p.rho_F_fn, self.vF,
                                                   self.rhoF_raw, **self.pow)
         self.vS, self.rhoS_raw, itS = compute_rho(self.t, self.Y.ravel(), self.p.rho_S_fn, self.vS,
@@ -199,7 +277,10 @@ class OracleRun:
             rho_F = self.safety * self.rhoF_raw
             rho_S = max(self.safety * self.rhoS_raw, self.rho_S_min)
         V_old = self.Y[0].copy()
-        Y, s, m, eta = self.p.emrkc_step(self.t, self.Y, dt, rho_F, rho_S, self.progressive)
+        if self.method == "mrkc":
+            Y, s, m, eta = self.p.mrkc_step(self.t, self.Y, dt, rho_F, rho_S, self.stiff_gate)
+        else:
+            Y, s, m, eta = self.p.emrkc_step(self.t, self.Y, dt, rho_F, rho_S, self.progressive)
         V_new = Y[0]
         th = self.act_threshold
         cross = np.isnan(self.act) & (V_old < th) & (V_new >= th)
