@@ -77,6 +77,14 @@ extern "C" {
                                   in the lumped-mass inner product (stop at
                                   ||r||_M <= lin_rtol ||rhs||_M, warm start
                                   V_n).  FP64 only                          */
+#define EMRKC_METHOD_MRKC 3    /* Algorithm 2 with the split of Sec. 3.3:
+                                  f~_F = f_F + f_E^1 (the stiffest gate, the
+                                  sodium activation m = z_E[0] of HH and
+                                  TTP06, the gate of the passive model) and
+                                  f~_S = f_S + f_E^2 (all other gates); no
+                                  exponential step.  rho_F, rho_S are those
+                                  of f~_F over (V, m) and of f~_S (Algorithm
+                                  5); the rho options apply.  FP64 only     */
 
 typedef struct emrkc_solver emrkc_solver; /* opaque; owns device memory */
 

@@ -18,7 +18,7 @@ from ._ffi import Matrix, Options, OwnedMatrix, Stats, Stimulus, Tissue
 MODEL_NONE, MODEL_PASSIVE, MODEL_HH, MODEL_TTP06 = 0, 1, 2, 3
 PREC_FP64, PREC_MIXED = 0, 1
 RHO_ONCE, RHO_FIXED = 0, -1
-METHOD_EMRKC, METHOD_EXEX_RL, METHOD_IMEX_RL = 0, 1, 2
+METHOD_EMRKC, METHOD_EXEX_RL, METHOD_IMEX_RL, METHOD_MRKC = 0, 1, 2, 3
 
 
 class EmrkcError(RuntimeError):

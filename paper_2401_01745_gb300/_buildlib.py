@@ -22,7 +22,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libemrkc.so")
 
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_UNITS = ["kernels_fp64.cu", "kernels_mixed.cu", "batch.cu", "noalloc.cu", "rl_methods.cu"]
+CUDA_UNITS = ["kernels_fp64.cu", "kernels_mixed.cu", "batch.cu", "noalloc.cu", "rl_methods.cu", "mrkc.cu"]
 HOST_UNITS = ["solver.cpp", "assemble.cpp", "batch_host.cpp"]
 FAST_MATH_UNITS = {"kernels_mixed.cu", "batch.cu"}
 

@@ -160,6 +160,58 @@ struct KernelSet {
   int (*tma_grid)(int device, int wmax) = nullptr;  // grid of the persistent stage kernel (0: not used)
 };
 
+// mRKC (mrkc.cu, FP64): one outer stage (stage kernel, inner stage 1) or
+// one inner stage k >= 2 on the block (V, z_k) of the stiffest gate k.
+struct MrkcArgs {
+  int64_t n = 0, ld = 0;
+  const double* Vm1 = nullptr;   // g_{j-1}
+  const double* Zm1 = nullptr;
+  const double* Vm2 = nullptr;   // g_{j-2} (nullptr for j = 1)
+  const double* Zm2 = nullptr;
+  double* Vout = nullptr;        // g_j
+  double* Zout = nullptr;
+  double nu = 1, kappa = 0, mu_dt = 0;   // outer coefficients of stage j
+  double eta = 0, inv_eta = 0;
+  int m = 1;                     // inner stages
+  double mu1 = 0, mu1_eta = 0;   // inner stage 1
+  double inu = 0, ikappa = 0, imu_eta = 0;  // inner stage k >= 2
+  const double* uV1 = nullptr;   // u_{k-1}, u_{k-2} (V and z_k parts)
+  const double* uV2 = nullptr;
+  const double* um1 = nullptr;
+  const double* um2 = nullptr;
+  double* uVk = nullptr;         // u_k
+  double* umk = nullptr;
+  int last = 0;
+  double* F = nullptr;           // frozen V forcing of f~_S
+  const uint8_t* mask = nullptr;
+  double stim = 0, inv_Cm = 1;
+  int final_stage = 0;
+  const double* Vn = nullptr;
+  double* act = nullptr;
+  double t_n = 0, dt = 0, threshold = 0;
+  int* flags = nullptr;
+};
+
+struct MrkcPowerArgs {
+  int64_t n = 0, ld = 0;
+  const double* V = nullptr;
+  const double* Z = nullptr;     // z block of the state (FP64)
+  const double* v_old = nullptr; // 2 x ld: (v_V, v_k)
+  double* v_new = nullptr;
+  double q = 0;
+  int slot = 0;
+};
+
+struct MrkcKernels {
+  void (*stage)(const MrkcArgs&, const Ell&, bool has_m2, cudaStream_t) = nullptr;
+  void (*inner)(const MrkcArgs&, const Ell&, cudaStream_t) = nullptr;
+  void (*power_F)(const MrkcPowerArgs&, const Ell&, const ReduceScratch&, cudaStream_t) = nullptr;
+  void (*power_S)(const PowerSArgs&, const ReduceScratch&, cudaStream_t) = nullptr;
+  void (*fS)(const PowerSArgs&, double*, cudaStream_t) = nullptr;
+  int stiff_gate = -1;           // index into z_E of the gate in f~_F, -1: none
+};
+bool get_kernels_mrkc(int model, MrkcKernels* k);
+
 // EXEX-RL / IMEX-RL steps (rl_methods.cu, FP64).  One step reads the state
 // buffer (V, Z) and writes (Vout, Zout).
 struct RlArgs {

@@ -51,7 +51,7 @@ void free_all(emrkc_solver* s) {
                   s->rs.partials, s->rs.ticket, s->rs.result, s->d_V32[0], s->d_V32[1], s->d_V32[2],
                   s->d_D[0], s->d_D[1], s->d_D[2], s->d_LV, s->d_Vlo[0], s->d_Vlo[1], s->d_Vlo[2],
                   s->d_Vn32, s->d_mass, s->d_cg[0], s->d_cg[1], s->d_cg[2], s->d_cg[3], s->d_cg[4],
-                  s->d_cg[5], s->d_part, s->d_bar, s->d_iters, s->d_res};
+                  s->d_cg[5], s->d_part, s->d_bar, s->d_iters, s->d_res, s->d_Um[0], s->d_Um[1], s->d_Um[2]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (s->h_pin) cudaFreeHost(s->h_pin);
@@ -98,16 +98,22 @@ double stim_at(const emrkc_solver* s, double t) {
   return (s->d_mask != nullptr && s->t_on <= t && t <= s->t_off) ? s->amp : 0.0;
 }
 
-// Algorithm 5 on f_F (V block only).
+// Algorithm 5 on f_F (V block only); for mRKC on f~_F over (V, z_k).
 int power_F(emrkc_solver* s) {
   materialise_V(s);
   double* V = s->d_V[s->cur];
+  const bool mrkc = s->method == EMRKC_METHOD_MRKC;
+  const int ks = s->mk.stiff_gate;
+  const double* zk = (mrkc && ks >= 0) ? static_cast<const double*>(s->d_Z[s->cur]) + (size_t)ks * s->ld : nullptr;
   s->launch(EMRKC_PHASE_OTHER, [&] { launch_sumsq(s->n, V, s->rs, 0, s->stream); });
-  s->launch(EMRKC_PHASE_OTHER, [&] { launch_sumsq(s->n, s->d_vF, s->rs, 1, s->stream); });
-  int rc = read_results(s, 0, 2);
+  s->launch(EMRKC_PHASE_OTHER, [&] {
+    launch_sumsq(mrkc ? 2 * s->ld : s->n, s->d_vF, s->rs, 1, s->stream);
+  });
+  if (zk) s->launch(EMRKC_PHASE_OTHER, [&] { launch_sumsq(s->n, zk, s->rs, 4, s->stream); });
+  int rc = read_results(s, 0, zk ? 5 : 2);
   if (rc) return rc;
   if ((rc = check_flags(s))) return rc;
-  const double ny = std::sqrt(s->h_pin[0]);
+  const double ny = std::sqrt(s->h_pin[0] + (zk ? s->h_pin[4] : 0.0));
   double nv = std::sqrt(s->h_pin[1]);
   const double delta = ny > 0.0 ? ny * s->opt.pow_eps : s->opt.pow_eps;
   int it = 0;
@@ -120,14 +126,27 @@ int power_F(emrkc_solver* s) {
   double q = delta / nv, rho_old = 0.0;
   while (std::fabs(rho - rho_old) >= s->opt.pow_tol * rho && it < s->opt.pow_max_iter) {
     rho_old = rho;
-    PowerFArgs a;
-    a.n = s->n;
-    a.V = V;
-    a.v_old = s->d_vF;
-    a.v_new = s->d_vF2;
-    a.q = q;
-    a.slot = 2;
-    s->launch(EMRKC_PHASE_POWER_F, [&] { s->ks.power_F(a, s->ell, s->rs, s->stream); });
+    if (mrkc) {
+      MrkcPowerArgs a;
+      a.n = s->n;
+      a.ld = s->ld;
+      a.V = V;
+      a.Z = static_cast<const double*>(s->d_Z[s->cur]);
+      a.v_old = s->d_vF;
+      a.v_new = s->d_vF2;
+      a.q = q;
+      a.slot = 2;
+      s->launch(EMRKC_PHASE_POWER_F, [&] { s->mk.power_F(a, s->ell, s->rs, s->stream); });
+    } else {
+      PowerFArgs a;
+      a.n = s->n;
+      a.V = V;
+      a.v_old = s->d_vF;
+      a.v_new = s->d_vF2;
+      a.q = q;
+      a.slot = 2;
+      s->launch(EMRKC_PHASE_POWER_F, [&] { s->ks.power_F(a, s->ell, s->rs, s->stream); });
+    }
     if ((rc = read_results(s, 2, 1))) return rc;
     std::swap(s->d_vF, s->d_vF2);
     ++it;
@@ -160,7 +179,11 @@ int power_S(emrkc_solver* s) {
   a.Cm = s->Cm;
   s->launch(EMRKC_PHASE_OTHER, [&] { s->ks.state_sumsq(s->n, s->ld, s->N - 1, V, s->d_Z[s->cur], s->rs, 0, s->stream); });
   s->launch(EMRKC_PHASE_OTHER, [&] { launch_sumsq(rows * s->ld, s->d_vS, s->rs, 1, s->stream); });
-  s->launch(EMRKC_PHASE_OTHER, [&] { s->ks.fS_eval(a, s->d_fy, s->stream); });
+  const bool mrkc = s->method == EMRKC_METHOD_MRKC;  // f~_S = f_S + f_E^2
+  s->launch(EMRKC_PHASE_OTHER, [&] {
+    if (mrkc) s->mk.fS(a, s->d_fy, s->stream);
+    else s->ks.fS_eval(a, s->d_fy, s->stream);
+  });
   int rc = read_results(s, 0, 2);
   if (rc) return rc;
   if ((rc = check_flags(s))) return rc;
@@ -182,7 +205,10 @@ int power_S(emrkc_solver* s) {
     a.fy = s->d_fy;
     a.q = q;
     a.slot = 3;
-    s->launch(EMRKC_PHASE_POWER_S, [&] { s->ks.power_S(a, s->rs, s->stream); });
+    s->launch(EMRKC_PHASE_POWER_S, [&] {
+      if (mrkc) s->mk.power_S(a, s->rs, s->stream);
+      else s->ks.power_S(a, s->rs, s->stream);
+    });
     if ((rc = read_results(s, 3, 1))) return rc;
     std::swap(s->d_vS, s->d_vS2);
     ++it;
@@ -267,24 +293,110 @@ int do_step_rl(emrkc_solver* s, double dt) {
   return EMRKC_OK;
 }
 
-int do_step(emrkc_solver* s, double dt) {
-  if (s->method != EMRKC_METHOD_EMRKC) return do_step_rl(s, dt);
+// rho policy shared by emRKC and mRKC: (rho_F, rho_S) with the safety factor
+int step_rho(emrkc_solver* s, double* rhoF, double* rhoS) {
   int rc;
-  double rhoF, rhoS;
   s->itF = s->itS = 0;
   if (s->opt.rho_every == EMRKC_RHO_FIXED) {
-    rhoF = s->opt.rho_F;
-    rhoS = s->opt.rho_S;
-  } else {
-    const bool due = (s->opt.rho_every == EMRKC_RHO_ONCE) ? !s->rho_done : (s->steps % s->opt.rho_every == 0);
-    if (due) {
-      if ((rc = power_F(s))) return rc;
-      if ((rc = power_S(s))) return rc;
-      s->rho_done = true;
-    }
-    rhoF = s->opt.safety * s->rhoF_raw;
-    rhoS = std::max(s->opt.safety * s->rhoS_raw, s->opt.rho_S_min);
+    *rhoF = s->opt.rho_F;
+    *rhoS = s->opt.rho_S;
+    return EMRKC_OK;
   }
+  const bool due = (s->opt.rho_every == EMRKC_RHO_ONCE) ? !s->rho_done : (s->steps % s->opt.rho_every == 0);
+  if (due) {
+    if ((rc = power_F(s))) return rc;
+    if ((rc = power_S(s))) return rc;
+    s->rho_done = true;
+  }
+  *rhoF = s->opt.safety * s->rhoF_raw;
+  *rhoS = std::max(s->opt.safety * s->rhoS_raw, s->opt.rho_S_min);
+  return EMRKC_OK;
+}
+
+// mRKC (Algorithm 2), FP64.
+int do_step_mrkc(emrkc_solver* s, double dt) {
+  double rhoF, rhoS;
+  int rc = step_rho(s, &rhoF, &rhoS);
+  if (rc) return rc;
+  double l_s = 0.0;
+  const int S = stages_for(dt, rhoS, s->opt.eps, &l_s);
+  const double eta = 2.0 * dt / l_s;
+  const int Mi = stages_for(eta, rhoF, s->opt.eps, nullptr);
+  const Coeffs co = s->coeffs(S);
+  const Coeffs ci = s->coeffs(Mi);
+  const int b0 = s->cur;
+  const int ks = s->mk.stiff_gate;
+  const double* Vn = (S == 1) ? s->d_V[b0] : s->d_Vn;
+  if (S >= 2) cudaMemcpyAsync(s->d_Vn, s->d_V[b0], s->n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
+  for (int j = 1; j <= S; ++j) {
+    const int bm1 = (b0 + j - 1) % 3, bm2 = (b0 + j - 2 + 3) % 3, bo = (b0 + j) % 3;
+    MrkcArgs a;
+    a.n = s->n;
+    a.ld = s->ld;
+    a.Vm1 = s->d_V[bm1];
+    a.Zm1 = static_cast<const double*>(s->d_Z[bm1]);
+    a.Vm2 = j >= 2 ? s->d_V[bm2] : nullptr;
+    a.Zm2 = j >= 2 ? static_cast<const double*>(s->d_Z[bm2]) : nullptr;
+    a.Vout = s->d_V[bo];
+    a.Zout = static_cast<double*>(s->d_Z[bo]);
+    a.nu = j >= 2 ? co.nu[j] : 1.0;
+    a.kappa = j >= 2 ? co.kappa[j] : 0.0;
+    a.mu_dt = co.mu[j] * dt;
+    a.eta = eta;
+    a.inv_eta = 1.0 / eta;
+    a.m = Mi;
+    a.mu1 = ci.mu[1];
+    a.mu1_eta = ci.mu[1] * eta;
+    a.uVk = s->d_U[0];
+    a.umk = s->d_Um[0];
+    a.F = static_cast<double*>(s->d_F);
+    a.mask = s->d_mask;
+    a.stim = stim_at(s, s->t + co.c[j - 1] * dt);
+    a.inv_Cm = 1.0 / s->Cm;
+    a.final_stage = (j == S && Mi == 1) ? 1 : 0;
+    a.Vn = Vn;
+    a.act = s->act_on ? s->d_act : nullptr;
+    a.t_n = s->t;
+    a.dt = dt;
+    a.threshold = s->opt.act_threshold;
+    a.flags = s->d_flags;
+    s->launch(EMRKC_PHASE_STAGE, [&] { s->mk.stage(a, s->ell, j >= 2, s->stream); });
+    const double* zk0 = ks >= 0 ? a.Zm1 + (size_t)ks * s->ld : nullptr;
+    for (int k = 2; k <= Mi; ++k) {
+      MrkcArgs b = a;
+      b.uV1 = s->d_U[(k - 2) % 3];
+      b.um1 = s->d_Um[(k - 2) % 3];
+      b.uV2 = (k == 2) ? s->d_V[bm1] : s->d_U[(k - 3) % 3];
+      b.um2 = (k == 2) ? zk0 : s->d_Um[(k - 3) % 3];
+      b.uVk = s->d_U[(k - 1) % 3];
+      b.umk = s->d_Um[(k - 1) % 3];
+      b.inu = ci.nu[k];
+      b.ikappa = ci.kappa[k];
+      b.imu_eta = ci.mu[k] * eta;
+      b.last = (k == Mi) ? 1 : 0;
+      b.final_stage = (j == S && k == Mi) ? 1 : 0;
+      s->launch(EMRKC_PHASE_INNER, [&] { s->mk.inner(b, s->ell, s->stream); });
+    }
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return s->cuda_fail(e, "kernel launch");
+  s->cur = (b0 + S) % 3;
+  s->t += dt;
+  s->steps += 1;
+  s->last_s = S;
+  s->last_m = Mi;
+  s->last_eta = eta;
+  s->last_rhoF = rhoF;
+  s->last_rhoS = rhoS;
+  return EMRKC_OK;
+}
+
+int do_step(emrkc_solver* s, double dt) {
+  if (s->method == EMRKC_METHOD_EXEX_RL || s->method == EMRKC_METHOD_IMEX_RL) return do_step_rl(s, dt);
+  if (s->method == EMRKC_METHOD_MRKC) return do_step_mrkc(s, dt);
+  double rhoF, rhoS;
+  int rc = step_rho(s, &rhoF, &rhoS);
+  if (rc) return rc;
   double l_s = 0.0;
   const int S = stages_for(dt, rhoS, s->opt.eps, &l_s);
   const double eta = 2.0 * dt / l_s;
@@ -675,12 +787,12 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
     g_create_error = "options: rho_S_min must be finite and >= 0";
     return EMRKC_ERR_ARG;
   }
-  if (o.method < EMRKC_METHOD_EMRKC || o.method > EMRKC_METHOD_IMEX_RL) {
+  if (o.method < EMRKC_METHOD_EMRKC || o.method > EMRKC_METHOD_MRKC) {
     g_create_error = "options: unknown method";
     return EMRKC_ERR_ARG;
   }
   if (o.method != EMRKC_METHOD_EMRKC && o.precision != EMRKC_PREC_FP64) {
-    g_create_error = "options: EXEX-RL and IMEX-RL run in FP64 only";
+    g_create_error = "options: mRKC, EXEX-RL and IMEX-RL run in FP64 only";
     return EMRKC_ERR_ARG;
   }
   if (o.method == EMRKC_METHOD_IMEX_RL && (!(o.lin_rtol >= 0) || o.lin_max_iter < 0)) {
@@ -706,6 +818,11 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
   s->method = o.method;
   const bool ok = (s->precision == EMRKC_PREC_FP64) ? get_kernels_fp64(ionic_model, &s->ks)
                                                     : get_kernels_mixed(ionic_model, &s->ks);
+  if (ok && o.method == EMRKC_METHOD_MRKC && !get_kernels_mrkc(ionic_model, &s->mk)) {
+    g_create_error = "no mRKC kernels for this model";
+    delete s;
+    return EMRKC_ERR_ARG;
+  }
   if (!ok) {
     g_create_error = "no kernels for this model";
     delete s;
@@ -758,8 +875,12 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
     fail |= dalloc(&s->d_LV, ld) != cudaSuccess;
     fail |= dalloc(&s->d_Vn32, ld) != cudaSuccess;
   }
-  fail |= dalloc(&s->d_vF, ld) != cudaSuccess;
-  fail |= dalloc(&s->d_vF2, ld) != cudaSuccess;
+  // the f_F iterate: V only, or (V, z_k) for mRKC
+  const int64_t rowsF = (s->method == EMRKC_METHOD_MRKC) ? 2 : 1;
+  fail |= dalloc(&s->d_vF, rowsF * ld) != cudaSuccess;
+  fail |= dalloc(&s->d_vF2, rowsF * ld) != cudaSuccess;
+  if (s->method == EMRKC_METHOD_MRKC)
+    for (int b = 0; b < 3; ++b) fail |= dalloc(&s->d_Um[b], ld) != cudaSuccess;
   fail |= dalloc(&s->d_vS, (int64_t)s->N * ld) != cudaSuccess;
   fail |= dalloc(&s->d_vS2, (int64_t)s->N * ld) != cudaSuccess;
   fail |= dalloc(&s->d_fy, (int64_t)s->N * ld) != cudaSuccess;
@@ -806,7 +927,7 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
   for (int b = 0; b < 3; ++b) cudaMemsetAsync(s->d_U[b], 0, ld * sizeof(double), s->stream);
   // power-iteration iterates: the kernels write rows [0, n) only and the norms
   // run over whole rows, so the padding must hold zeros in both buffers
-  cudaMemsetAsync(s->d_vF2, 0, ld * sizeof(double), s->stream);
+  cudaMemsetAsync(s->d_vF2, 0, rowsF * ld * sizeof(double), s->stream);
   cudaMemsetAsync(s->d_vS2, 0, (size_t)s->N * ld * sizeof(double), s->stream);
   cudaMemsetAsync(s->d_fy, 0, (size_t)s->N * ld * sizeof(double), s->stream);
   // rest state in every buffer
@@ -818,7 +939,7 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
     if (nz > 0) launch_fill_rows(s->d_Z[b], (int)s->zsize, s->n, ld, (int)nz, s->d_rest + 1, s->stream);
   }
   launch_fill(s->d_act, ld, std::nan(""), s->stream);
-  launch_start_vector(o.seed, s->n, ld, 1, s->d_vF, s->stream);
+  launch_start_vector(o.seed, s->n, ld, (int)rowsF, s->d_vF, s->stream);
   launch_start_vector(~o.seed, s->n, ld, s->N, s->d_vS, s->stream);
   if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess)
     return bail(EMRKC_ERR_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));

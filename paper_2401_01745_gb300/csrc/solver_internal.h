@@ -156,6 +156,9 @@ struct emrkc_solver {
   unsigned long long* d_iters = nullptr;  // CG iterations: last, total
   double* d_res = nullptr;      // final <r, r>_M, <c, c>_M
   int pcg_grid = 0;
+  // mRKC (mrkc.cu)
+  emrkc::MrkcKernels mk{};
+  double* d_Um[3] = {nullptr, nullptr, nullptr};  // inner stages, stiff-gate part
   int ell_wmax = 0;  // widest sliced-ELL slice
   bool act_on = false;
   double phase_ms[EMRKC_NUM_PHASES] = {0};

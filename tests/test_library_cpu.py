@@ -123,7 +123,7 @@ def test_create_validates_arguments(lib):
     with pytest.raises(pkg.EmrkcError) as ei:  # unknown time integrator
         pkg.Solver(rp, col, K, M, method=7)
     assert ei.value.code == 1
-    for method in (pkg.METHOD_EXEX_RL, pkg.METHOD_IMEX_RL):  # Algorithm 4 runs in FP64 only
+    for method in (pkg.METHOD_EXEX_RL, pkg.METHOD_IMEX_RL, pkg.METHOD_MRKC):  # FP64 only
         with pytest.raises(pkg.EmrkcError) as ei:
             pkg.Solver(rp, col, K, M, method=method, precision=pkg.PREC_MIXED)
         assert ei.value.code == 1
