@@ -414,7 +414,8 @@ def run_shell(args):
 
 def run_compare(args):
     """Work-precision comparison on the 3-D cuboid (Sec. 5.3 shape): emRKC
-    (FP64 and mixed) against IMEX-RL (Algorithm 4, FP64, CG to lin_rtol) at
+    (FP64 and mixed) and mRKC (Algorithm 2, FP64) against IMEX-RL (Algorithm
+    4, FP64, CG to lin_rtol) at
     several dt, errors in V at T against a fine-step EXEX-RL reference (Sec. 5
     uses EXEX-RL at dt = 1e-4 ms; here dt_ref, stated in the output).  Each
     run is timed with CUDA events around all its steps (state resident, no L2
@@ -462,6 +463,7 @@ def run_compare(args):
         for dt in args.compare_dts:
             for name, method, prec in (("emRKC-fp64", pkg.METHOD_EMRKC, pkg.PREC_FP64),
                                        ("emRKC-mixed", pkg.METHOD_EMRKC, pkg.PREC_MIXED),
+                                       ("mRKC-fp64", pkg.METHOD_MRKC, pkg.PREC_FP64),
                                        ("IMEX-RL-fp64", pkg.METHOD_IMEX_RL, pkg.PREC_FP64)):
                 kw = {"lin_rtol": args.lin_rtol} if method == pkg.METHOD_IMEX_RL else {}
                 V, ms, H, st = solve(method, prec, dt, **kw)

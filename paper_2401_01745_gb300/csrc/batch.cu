@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) batch_step_kernel(const B
       a.V32out = I->Vhi[bo];
       a.Vlo_out = I->Vlo[bo];
       a.D1 = I->D[0];
-      a.LV = I->LV;
+      a.LV = (m >= 4) ? I->LV : nullptr;
       a.f_nu = I->o_nu[j];
       a.f_kappa = I->o_kappa[j];
       a.f_mudt = I->o_mudt[j];
@@ -139,6 +139,8 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) batch_step_kernel(const B
       b.d2 = (k == 2) ? nullptr : I->D[(k - 3) % 3];
       b.dk = I->D[(k - 1) % 3];
       b.LV = I->LV;
+      b.lf_src = (m >= 4) ? 0 : (k == 2 ? 1 : 2);
+      b.f_inv_mu1eta = I->f_inv_mu1eta;
       b.V32out = I->Vhi[bo];
       b.Vhi1 = I->Vhi[bm1];
       b.Vlo1 = I->Vlo[bm1];

@@ -169,6 +169,7 @@ int fill_inst(emrkc_batch* b, Member& mb, double dt, BatchInst* I) {
   I->f_cm = (float)ci.c[Mi];
   I->f_mu1 = (float)ci.mu[1];
   I->f_mu1eta = (float)(ci.mu[1] * eta);
+  I->f_inv_mu1eta = (float)(1.0 / (ci.mu[1] * eta));
   for (int j = 0; j <= S; ++j) {
     I->o_c[j] = co.c[j];
     I->o_nu[j] = j >= 2 ? (float)co.nu[j] : 1.0f;

@@ -11,6 +11,7 @@
 #pragma once
 
 #include <cstdint>
+#include <utility>
 
 #include "launch.h"
 #include "models.cuh"
@@ -100,6 +101,14 @@ __device__ __forceinline__ double ell_diff64(const Ell& A, int64_t i, const doub
   }
   return acc;
 }
+
+// Programmatic dependent launch (sm_90+): a kernel launched with the
+// programmatic-serialisation attribute may start while its predecessor in the
+// stream drains; it must wait (griddepcontrol.wait) before touching memory the
+// predecessor writes.  Each step kernel lets its own dependent start early.
+// Both instructions are no-ops for kernels launched without the attribute.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
 // Step epilogue: non-finite flag and activation time (first upward crossing
@@ -261,13 +270,14 @@ __device__ __forceinline__ void stage_node_mixed(const StageArgs& a, const Ell& 
     if (a.final_stage) step_epilogue_ff(i, ldm<CG>(a.Vn32 + i), hi, a.act, a.t_n, a.dt, a.f_th, a.flags);
   } else {
     a.D1[i] = a.f_mu1eta * (LV + F);
-    a.LV[i] = LV;
-    static_cast<float*>(a.F)[i] = F;
+    if (a.LV != nullptr) a.LV[i] = LV + F;  // kept for inner stages k >= 4 only
   }
 }
 
 template <class Model, bool HAS_M2>
 __global__ void __launch_bounds__(128) stage_kernel_mixed(const StageArgs a, const Ell A) {
+  pdl_trigger();
+  pdl_wait();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   stage_node_mixed<Model, HAS_M2, false>(a, A, i);
@@ -377,6 +387,8 @@ __global__ void __launch_bounds__(kTmaTile) stage_kernel_mixed_tma(const StageAr
     s_abort = 0;
   }
   __syncthreads();
+  pdl_trigger();
+  pdl_wait();
   if (a.mask == nullptr) {
     // the stage copies the mask with the rest: a solver without stimulus has no
     // mask array, so this variant is only launched with one
@@ -457,8 +469,7 @@ __global__ void __launch_bounds__(kTmaTile) stage_kernel_mixed_tma(const StageAr
         if (a.final_stage) step_epilogue_ff(i, __ldg(a.Vn32 + i), hi, a.act, a.t_n, a.dt, a.f_th, a.flags);
       } else {
         a.D1[i] = a.f_mu1eta * (LV + F);
-        a.LV[i] = LV;
-        static_cast<float*>(a.F)[i] = F;
+        if (a.LV != nullptr) a.LV[i] = LV + F;  // kept for inner stages k >= 4 only
       }
     }
     __syncthreads();  // every thread is done with this stage buffer
@@ -502,12 +513,23 @@ static __global__ void __launch_bounds__(256) inner_kernel_fp64(const InnerArgs 
 // delta_k = nu'_k delta_{k-1} + kappa'_k delta_{k-2} + mu'_k eta (L V + L delta_{k-1} + F)
 // (nu'_k + kappa'_k = 1 makes this the u-recurrence shifted by V); the last
 // stage forms f_bar_V = delta_m / eta and updates the float-float V.
+// L V_{j-1} + F of the node: delta_1 / (mu'_1 eta) while delta_1 is still one
+// of the two increments at hand (k = 2: delta_{k-1}, k = 3: delta_{k-2}), else
+// the value the stage kernel stored.
+template <bool CG>
+__device__ __forceinline__ float inner_lf(const InnerArgs& a, int64_t i, float d1, float d2) {
+  if (a.lf_src == 1) return d1 * a.f_inv_mu1eta;
+  if (a.lf_src == 2) return d2 * a.f_inv_mu1eta;
+  return ldm<CG>(a.LV + i);
+}
+
 template <bool CG = false>
 __device__ __forceinline__ void inner_node_mixed(const InnerArgs& a, const Ell& A, const int64_t i) {
   const float Ld = ell_diff32<CG>(A, i, a.d1);
-  const float F = ldm<CG>(static_cast<const float*>(a.F) + i);
-  float dk = a.f_nu * ldm<CG>(a.d1 + i) + a.f_mueta * (ldm<CG>(a.LV + i) + Ld + F);
-  if (a.d2 != nullptr) dk += a.f_kappa * ldm<CG>(a.d2 + i);
+  const float d1 = ldm<CG>(a.d1 + i);
+  const float d2 = (a.d2 != nullptr) ? ldm<CG>(a.d2 + i) : 0.0f;
+  float dk = a.f_nu * d1 + a.f_mueta * (inner_lf<CG>(a, i, d1, d2) + Ld);
+  if (a.d2 != nullptr) dk += a.f_kappa * d2;
   if (!a.last) {
     a.dk[i] = dk;
     return;
@@ -523,6 +545,8 @@ __device__ __forceinline__ void inner_node_mixed(const InnerArgs& a, const Ell& 
 }
 
 static __global__ void __launch_bounds__(256) inner_kernel_mixed(const InnerArgs a, const Ell A) {
+  pdl_trigger();
+  pdl_wait();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   inner_node_mixed<false>(a, A, i);
@@ -534,9 +558,8 @@ __device__ __forceinline__ void inner_node_mixed_w(const InnerArgs& a, const Ell
   float xv[W], lv[W];
   const int w = ell_gather<W, CG>(A, i, a.d1, xv, lv);
   const float d1 = ldm<CG>(a.d1 + i);
-  const float F = ldm<CG>(static_cast<const float*>(a.F) + i);
-  const float LVi = ldm<CG>(a.LV + i);
   const float d2 = (a.d2 != nullptr) ? ldm<CG>(a.d2 + i) : 0.0f;
+  const float LF = inner_lf<CG>(a, i, d1, d2);
   float lo1 = 0.0f, hi1 = 0.0f, hi2 = 0.0f, lo2 = 0.0f;
   if (a.last) {
     hi1 = ldm<CG>(a.Vhi1 + i);
@@ -547,7 +570,7 @@ __device__ __forceinline__ void inner_node_mixed_w(const InnerArgs& a, const Ell
     }
   }
   const float Ld = ell_reduce<W>(xv, lv, w, d1);
-  float dk = a.f_nu * d1 + a.f_mueta * (LVi + Ld + F);
+  float dk = a.f_nu * d1 + a.f_mueta * (LF + Ld);
   if (a.d2 != nullptr) dk += a.f_kappa * d2;
   if (!a.last) {
     a.dk[i] = dk;
@@ -564,6 +587,8 @@ __device__ __forceinline__ void inner_node_mixed_w(const InnerArgs& a, const Ell
 
 template <int W>
 __global__ void __launch_bounds__(256) inner_kernel_mixed_w(const InnerArgs a, const Ell A) {
+  pdl_trigger();
+  pdl_wait();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   inner_node_mixed_w<W, false>(a, A, i);
@@ -734,20 +759,42 @@ __global__ void convert_kernel(int64_t count, const void* src, double* dst, int 
 // Host-side launch helpers shared by the per-precision translation units.
 inline unsigned blocks_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
 
+// Launch with the programmatic-serialisation attribute when pdl is set.
+template <typename... KArgs, typename... Args>
+inline void launch_k(bool pdl, void (*k)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                     Args&&... args) {
+  if (!pdl) {
+    k<<<grid, block, smem, st>>>(std::forward<Args>(args)...);
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
+
 template <class MD, class MR, typename R, typename Z, bool MIXED>
 struct Kernels {
   static void stage(const StageArgs& a, const Ell& A, int has_m2, cudaStream_t st) {
     if (a.n == 0) return;
     const unsigned g = blocks_for(a.n, 128);
     if constexpr (MIXED) {
+      const bool pdl = a.pdl != 0;
       if (a.mask != nullptr && a.tma_grid > 0) {
         const int SB = tma_stage_bytes(MR::NE + MR::NS, a.ell_wmax);
-        if (has_m2) stage_kernel_mixed_tma<MR, true><<<a.tma_grid, kTmaTile, 2 * SB, st>>>(a, A);
-        else stage_kernel_mixed_tma<MR, false><<<a.tma_grid, kTmaTile, 2 * SB, st>>>(a, A);
+        if (has_m2) launch_k(pdl, stage_kernel_mixed_tma<MR, true>, a.tma_grid, kTmaTile, 2 * SB, st, a, A);
+        else launch_k(pdl, stage_kernel_mixed_tma<MR, false>, a.tma_grid, kTmaTile, 2 * SB, st, a, A);
       } else if (has_m2) {
-        stage_kernel_mixed<MR, true><<<g, 128, 0, st>>>(a, A);
+        launch_k(pdl, stage_kernel_mixed<MR, true>, g, 128, 0, st, a, A);
       } else {
-        stage_kernel_mixed<MR, false><<<g, 128, 0, st>>>(a, A);
+        launch_k(pdl, stage_kernel_mixed<MR, false>, g, 128, 0, st, a, A);
       }
     } else {
       if (has_m2) stage_kernel_fp64<MR, true><<<g, 128, 0, st>>>(a, A);
@@ -757,8 +804,9 @@ struct Kernels {
   static void inner(const InnerArgs& a, const Ell& A, cudaStream_t st) {
     if (a.n == 0) return;
     if constexpr (MIXED) {
-      if (a.ell_wmax <= 8) inner_kernel_mixed_w<8><<<blocks_for(a.n, 256), 256, 0, st>>>(a, A);
-      else inner_kernel_mixed<<<blocks_for(a.n, 256), 256, 0, st>>>(a, A);
+      const bool pdl = a.pdl != 0;
+      if (a.ell_wmax <= 8) launch_k(pdl, inner_kernel_mixed_w<8>, blocks_for(a.n, 256), 256, 0, st, a, A);
+      else launch_k(pdl, inner_kernel_mixed, blocks_for(a.n, 256), 256, 0, st, a, A);
     }
     else inner_kernel_fp64<<<blocks_for(a.n, 256), 256, 0, st>>>(a, A);
   }

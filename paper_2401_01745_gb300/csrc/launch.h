@@ -79,6 +79,7 @@ struct StageArgs {
   float* Vn32_copy = nullptr;   // store hi of V_n (first stage when s >= 2)
   float f_th = -20;
   int tma_grid = 0;             // > 0: persistent bulk-copy variant with this grid
+  int pdl = 0;                  // 1: programmatic dependent launch
   int ell_wmax = 1 << 30;       // widest sliced-ELL slice (selects unrolled row variants)
 };
 
@@ -118,6 +119,11 @@ struct InnerArgs {
   const float* Vn32 = nullptr;
   float f_okappa = 0, f_omu_dt = 0, f_th = -20;
   int ell_wmax = 1 << 30;       // widest sliced-ELL slice (selects unrolled row variants)
+  int pdl = 0;                  // 1: programmatic dependent launch
+  // mixed path: L V_{j-1} + F as delta_1 / (mu'_1 eta) from d1 (1) or d2 (2),
+  // or from the array LV (0, inner stages k >= 4)
+  int lf_src = 0;
+  float f_inv_mu1eta = 0.0f;
 };
 
 // Power iteration (Algorithm 5) kernels.
@@ -305,7 +311,7 @@ struct BatchInst {
   Ell ell{};
   double t = 0, dt = 0, amp = 0, t_on = 0, t_off = -1;
   int64_t steps = 0;
-  float f_th = -20, f_inv_Cm = 1, f_eta = 0, f_inv_eta = 1, f_cm = 1, f_mu1 = 1, f_mu1eta = 0;
+  float f_th = -20, f_inv_Cm = 1, f_eta = 0, f_inv_eta = 1, f_cm = 1, f_mu1 = 1, f_mu1eta = 0, f_inv_mu1eta = 0;
   double o_c[kBatchMaxStages + 1];      // outer stage times c_j
   float o_nu[kBatchMaxStages + 1];      // outer nu_j (1 for j = 1)
   float o_kappa[kBatchMaxStages + 1];   // outer kappa_j (0 for j = 1)

@@ -449,7 +449,7 @@ int do_step(emrkc_solver* s, double dt) {
     a.Vn32_copy = (j == 1 && S >= 2) ? s->d_Vn32 : nullptr;
     a.f_th = (float)s->opt.act_threshold;
     a.D1 = s->d_D[0];
-    a.LV = s->d_LV;
+    a.LV = (Mi >= 4) ? s->d_LV : nullptr;  // L V + F, kept for inner stages k >= 4
     a.f_nu = (float)a.nu;
     a.f_kappa = (float)a.kappa;
     a.f_mudt = (float)a.mu_dt;
@@ -461,6 +461,7 @@ int do_step(emrkc_solver* s, double dt) {
     a.f_stim = (float)a.stim;
     a.f_inv_Cm = (float)(1.0 / s->Cm);
     a.tma_grid = s->tma_grid;
+    a.pdl = s->pdl;
     a.ell_wmax = s->ell_wmax;
     s->launch(EMRKC_PHASE_STAGE, [&] { s->ks.stage(a, s->ell, j >= 2, s->stream); });
     for (int k = 2; k <= Mi; ++k) {
@@ -493,6 +494,8 @@ int do_step(emrkc_solver* s, double dt) {
       b.d2 = (k - 2 == 0) ? nullptr : s->d_D[(k - 3) % 3];
       b.dk = s->d_D[(k - 1) % 3];
       b.LV = s->d_LV;
+      b.lf_src = (Mi >= 4) ? 0 : (k == 2 ? 1 : 2);
+      b.f_inv_mu1eta = (float)(1.0 / (ci.mu[1] * eta));
       b.V32out = s->d_V32[bo];
       b.Vhi1 = s->d_V32[bm1];
       b.Vlo1 = s->d_Vlo[bm1];
@@ -508,6 +511,7 @@ int do_step(emrkc_solver* s, double dt) {
       b.f_mueta = (float)(ci.mu[k] * eta);
       b.f_inv_eta = (float)(1.0 / eta);
       b.ell_wmax = s->ell_wmax;
+      b.pdl = s->pdl;
       s->launch(EMRKC_PHASE_INNER, [&] { s->ks.inner(b, s->ell, s->stream); });
     }
   }
@@ -856,7 +860,11 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
   if ((rc = build_matrix(s, mat))) return bail(rc, "");
   if (s->precision == EMRKC_PREC_MIXED && s->ks.tma_grid) {
     const char* no_tma = std::getenv("EMRKC_NO_TMA");
-    if (!(no_tma && no_tma[0] == '1')) s->tma_grid = s->ks.tma_grid(s->device, s->ell_wmax);
+    if (!(no_tma && no_tma[0] == '1')) {
+      s->tma_grid = s->ks.tma_grid(s->device, s->ell_wmax);
+    }
+    const char* no_pdl = std::getenv("EMRKC_NO_PDL");
+    s->pdl = (no_pdl && no_pdl[0] == '1') ? 0 : 1;
   }
   const int64_t ld = s->ld, nz = s->N - 1;
   bool fail = false;

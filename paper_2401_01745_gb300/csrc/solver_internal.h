@@ -147,6 +147,7 @@ struct emrkc_solver {
   int64_t total_it = 0, launches = 0;
   int64_t mat_entries = 0, mat_slots = 0;
   int tma_grid = 0;  // persistent bulk-copy stage kernel grid (mixed path), 0 = off
+  int pdl = 0;             // mixed path: programmatic dependent launch of the step kernels
   // EXEX-RL / IMEX-RL (rl_methods.cu)
   int method = 0;
   double* d_mass = nullptr;     // lumped mass (IMEX-RL)

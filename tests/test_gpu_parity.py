@@ -283,6 +283,25 @@ def test_mixed_precision_vs_fp64(name, dt, steps, h, amp_scale):
     assert np.max(np.abs(a64[fin] - a32[fin])) <= 0.05
 
 
+@pytest.mark.parametrize("fixed,m", [((500.0, 60.0), 3), ((5000.0, 300.0), 5)])
+def test_mixed_vs_fp64_many_stages(fixed, m):
+    """Fixed rho forces m = 3 and m >= 4 in the mixed path (the inner stages
+    then take L V + F from delta_1 or from the stored array)."""
+    w = make_workload("slab21x9x5_ttp", h=0.01)
+    w.dt = 0.1
+    Y64, a64, log64, *_ = _run_pair(w, 40, fixed=fixed, oracle=False)
+    Y32, a32, log32, *_ = _run_pair(w, 40, fixed=fixed, precision=pkg.PREC_MIXED, oracle=False)
+    assert log64 == log32
+    assert log32[-1][1] == m
+    prob = Monodomain.from_workload(w)
+    err = prob.l2_norm(Y32[0] - Y64[0]) / prob.l2_norm(Y64[0])
+    assert err <= 1e-3, f"mixed vs FP64 rel L2 error in V {err:.3e}"
+    fin = np.isfinite(a64)
+    assert np.array_equal(fin, np.isfinite(a32))
+    if fin.any():
+        assert np.max(np.abs(a64[fin] - a32[fin])) <= 0.05
+
+
 def test_state_roundtrip_and_errors():
     w = make_workload("square9x7_ttp", h=0.01)
     sol = pkg.Solver.from_workload(w)
