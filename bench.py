@@ -589,6 +589,53 @@ def run_stability(args):
     return 0
 
 
+def run_latency(args):
+    """The 65 x 65 HH square (4,225 nodes) with the power iteration before
+    every step (Sec. 5.2 shape): too small to fill a GPU, so it is reported as
+    microseconds per step, FP64 and mixed, timed from rest over 400 steps."""
+    import torch
+
+    import paper_2401_01745_gb300 as pkg
+    from workloads import make_workload
+
+    world, rank, local = _dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pkg.build()
+    w = make_workload("square65_hh")
+    rp, col, K, M = pkg.assemble_p1(w.coords, w.cells, w.D)
+    stream = torch.cuda.Stream(device=dev)
+    H = int(round(w.T / w.dt))
+    out = {"metric": "latency: microseconds per emRKC step (rho every step)", "unit": "us/step",
+           "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "steps": H,
+           "config": {"workload": "square65_hh: 65x65 nodes on [0,1]^2 cm (h = 1/64), sigma 1 mS/cm, HH, corner "
+                                  "stimulus 1 ms, dt 0.05 ms, T 20 ms, rho every step (timed)", "nodes": w.n}}
+    with ClockSampler(local) as clk:
+        for name, prec in (("fp64", pkg.PREC_FP64), ("mixed", pkg.PREC_MIXED)):
+            res = []
+            for rep in range(args.warmup // 3 + 2):
+                sol = pkg.Solver(rp, col, K, M, chi=w.chi, Cm=w.Cm, model=w.model, mask=w.stim_mask,
+                                 amplitude=w.stim_amp, t_on=w.t_on, t_off=w.t_off, precision=prec, rho_every=1,
+                                 stream=stream.cuda_stream, device=local)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                with torch.cuda.stream(stream):
+                    e0.record(stream)
+                    for _ in range(H):
+                        sol.step(w.dt)
+                    e1.record(stream)
+                sol.sync()
+                st = sol.stats()
+                res.append((e0.elapsed_time(e1) * 1e3 / H, st["total_pow_iters"] / H))
+                sol.close()
+            us, its = res[-1]  # the first runs are warm-up
+            out[name] = {"us_per_step": us, "power_iterations_per_step": its,
+                         "node_timesteps_per_s": w.n / (us * 1e-6)}
+    out["value"] = out["mixed"]["us_per_step"]
+    out["clocks"] = clk.summary()
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -616,6 +663,7 @@ def main():
     ap.add_argument("--compare-wedge-dt", type=float, default=0.2)
     ap.add_argument("--lin-rtol", type=float, default=1e-8)
     ap.add_argument("--stability", action="store_true", help="Sec. 5.1 practical-stability sweep on the 1-D cable")
+    ap.add_argument("--latency", action="store_true", help="65x65 HH square, rho every step, us/step")
     ap.add_argument("--stability-dts", type=float, nargs="+",
                     default=[0.05, 0.1, 0.25, 0.5, 1.0, 2.0, 3.0, 4.0, 4.5, 5.0, 6.0, 8.0])
     args = ap.parse_args()
@@ -629,6 +677,8 @@ def main():
         return run_compare(args)
     if args.stability:
         return run_stability(args)
+    if args.latency:
+        return run_latency(args)
     if args.served:
         return run_served(args)
     if args.batched:

@@ -15,6 +15,7 @@
 
 #include "launch.h"
 #include "models.cuh"
+#include "dual.cuh"
 
 namespace emrkc {
 
@@ -653,8 +654,16 @@ __global__ void __launch_bounds__(kReduceBlock) powerF_kernel(const PowerFArgs a
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
     double fz, fy;
     if constexpr (MIXED) {
-      fz = ell_diff64(A, i, a.V, a.v_old, a.q);
-      fy = ell_diff64(A, i, a.V, nullptr, 0.0);
+      // f_F is linear: f_F(V + q v) - f_F(V) = q L v, formed in FP32 on the
+      // off-diagonal matrix (no cancellation)
+      const int64_t b = i >> 5;
+      const int w = __ldg(A.width + b);
+      int64_t p = __ldg(A.slice_ptr + b) + (i & 31);
+      const float vi = (float)a.v_old[i];
+      float acc32 = 0.0f;
+      for (int k = 0; k < w; ++k, p += 32) acc32 += __ldg(A.val32 + p) * ((float)a.v_old[__ldg(A.col + p)] - vi);
+      fz = a.q * (double)acc32;
+      fy = 0.0;
     } else {
       const int64_t b = i >> 5;
       const int w = A.width[b];
@@ -713,6 +722,36 @@ __global__ void __launch_bounds__(kReduceBlock) powerS_kernel(const PowerSArgs a
     for (int k = 0; k < N; ++k) {
       const double w = f[k] - a.fy[k * a.ld + i];
       a.v_new[k * a.ld + i] = w;
+      acc += w * w;
+    }
+  }
+  reduce_finish(acc, rs, a.slot);
+}
+
+// Mixed path: v_new = q J(y) v with J v from dual numbers (see dual.cuh); f_S
+// has no gate rows (they belong to f_E), so only V and z_S rows are nonzero.
+template <class ModelDu, typename Z>
+__global__ void __launch_bounds__(kReduceBlock) powerS_dual_kernel(const PowerSArgs a, const ReduceScratch rs) {
+  constexpr int NE = ModelDu::NE, NS = ModelDu::NS, N = 1 + NE + NS;
+  double acc = 0.0;
+  const Z* Zs = static_cast<const Z*>(a.Z);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    Dual y[N];
+    y[0] = Dual((float)a.V[i], (float)a.v_old[i]);
+#pragma unroll
+    for (int k = 1; k < N; ++k) y[k] = Dual((float)Zs[(k - 1) * a.ld + i], (float)a.v_old[k * a.ld + i]);
+    Dual I;
+    Dual gS[NS > 0 ? NS : 1];
+    ModelDu::currents(y[0], y + 1, y + 1 + NE, I, gS);
+    const double w0 = a.q * (double)(-I.d * (float)(1.0 / a.Cm));
+    a.v_new[i] = w0;
+    acc += w0 * w0;
+#pragma unroll
+    for (int k = 0; k < NE; ++k) a.v_new[(1 + k) * a.ld + i] = 0.0;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      const double w = a.q * (double)gS[k].d;
+      a.v_new[(1 + NE + k) * a.ld + i] = w;
       acc += w * w;
     }
   }
@@ -780,7 +819,7 @@ inline void launch_k(bool pdl, void (*k)(KArgs...), unsigned grid, unsigned bloc
   cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
 }
 
-template <class MD, class MR, typename R, typename Z, bool MIXED>
+template <class MD, class MR, typename R, typename Z, bool MIXED, class MDu = MD>
 struct Kernels {
   static void stage(const StageArgs& a, const Ell& A, int has_m2, cudaStream_t st) {
     if (a.n == 0) return;
@@ -814,7 +853,8 @@ struct Kernels {
     powerF_kernel<MIXED><<<reduce_grid(a.n), kReduceBlock, 0, st>>>(a, A, rs);
   }
   static void power_S(const PowerSArgs& a, const ReduceScratch& rs, cudaStream_t st) {
-    powerS_kernel<MD, Z><<<reduce_grid(a.n), kReduceBlock, 0, st>>>(a, rs);
+    if constexpr (MIXED) powerS_dual_kernel<MDu, Z><<<reduce_grid(a.n), kReduceBlock, 0, st>>>(a, rs);
+    else powerS_kernel<MD, Z><<<reduce_grid(a.n), kReduceBlock, 0, st>>>(a, rs);
   }
   static void fS_eval(const PowerSArgs& a, double* out, cudaStream_t st) {
     if (a.n == 0) return;

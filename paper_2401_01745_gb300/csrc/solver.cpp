@@ -180,10 +180,13 @@ int power_S(emrkc_solver* s) {
   s->launch(EMRKC_PHASE_OTHER, [&] { s->ks.state_sumsq(s->n, s->ld, s->N - 1, V, s->d_Z[s->cur], s->rs, 0, s->stream); });
   s->launch(EMRKC_PHASE_OTHER, [&] { launch_sumsq(rows * s->ld, s->d_vS, s->rs, 1, s->stream); });
   const bool mrkc = s->method == EMRKC_METHOD_MRKC;  // f~_S = f_S + f_E^2
-  s->launch(EMRKC_PHASE_OTHER, [&] {
-    if (mrkc) s->mk.fS(a, s->d_fy, s->stream);
-    else s->ks.fS_eval(a, s->d_fy, s->stream);
-  });
+  // f_S(y) for the differences of Algorithm 5 (the mixed path forms J v directly)
+  if (mrkc || s->precision != EMRKC_PREC_MIXED) {
+    s->launch(EMRKC_PHASE_OTHER, [&] {
+      if (mrkc) s->mk.fS(a, s->d_fy, s->stream);
+      else s->ks.fS_eval(a, s->d_fy, s->stream);
+    });
+  }
   int rc = read_results(s, 0, 2);
   if (rc) return rc;
   if ((rc = check_flags(s))) return rc;

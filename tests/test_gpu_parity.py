@@ -159,6 +159,31 @@ def test_power_iteration_matches_oracle():
     sol.close()
 
 
+@pytest.mark.parametrize("name,h", [("slab23x9x5_ttp", 0.01), ("square33x33_hh", 1.0 / 64)])
+def test_power_iteration_mixed_matches_oracle(name, h):
+    """The mixed path forms q J v (dual numbers for f_S, q L v for f_F) instead
+    of the FP64 differences of Algorithm 5; the estimates agree with the
+    oracle's finite differences far inside the iteration's 1e-2 tolerance."""
+    from oracle.power import compute_rho, start_vector
+    w = make_workload(name, h=h)
+    prob = Monodomain.from_workload(w)
+    Y = prob.initial_state()
+    # a state away from rest: 30 oracle steps through the stimulus
+    ref = OracleRun(prob, rho_every=0)
+    for _ in range(30):
+        ref.step(w.dt)
+    Y = ref.Y
+    sol = pkg.Solver.from_workload(w, seed=77, precision=pkg.PREC_MIXED)
+    sol.set_state(Y)
+    rF, rS, itF, itS = sol.estimate_rho()
+    sol.close()
+    _, rFo, itFo = compute_rho(0.0, Y[0], prob.rho_F_fn, start_vector(77, prob.n), 0.0)
+    _, rSo, itSo = compute_rho(ref.t, Y.ravel(), prob.rho_S_fn, start_vector(~77 & 0xFFFFFFFFFFFFFFFF, prob.N * prob.n), 0.0)
+    assert rF == pytest.approx(rFo, rel=1e-4)
+    assert rS == pytest.approx(rSo, rel=1e-3)
+    assert abs(itF - itFo) <= 1 and abs(itS - itSo) <= 1
+
+
 def test_passive_model_closed_form_on_gpu():
     """Sec. 4.4 amplification on a 1-D cosine eigenvector, evaluated on the GPU."""
     from numpy.polynomial import chebyshev as C
