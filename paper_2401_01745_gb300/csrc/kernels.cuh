@@ -13,6 +13,8 @@
 #include <cstdint>
 #include <utility>
 
+#include <cuda/atomic>
+
 #include "launch.h"
 #include "models.cuh"
 #include "dual.cuh"
@@ -639,6 +641,52 @@ __device__ __forceinline__ void reduce_finish(double v, const ReduceScratch& rs,
   }
 }
 
+// Grid-wide barrier of a cooperative launch (all CTAs co-resident).  Bounded:
+// after spin_limit polls it records bit 4 in flags and returns false; a CTA
+// also returns false once another one has given up.
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* flags, long long spin_limit) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> gen(bar[1]);
+    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> cnt(bar[0]);
+    const unsigned int my = gen.load(cuda::memory_order_acquire);
+    s_ok = 1;
+    __threadfence();  // the CTA's writes (ordered by the bar.sync above) before the arrival
+    if (cnt.fetch_add(1u, cuda::memory_order_acq_rel) == gridDim.x - 1) {
+      cnt.store(0u, cuda::memory_order_relaxed);
+      gen.store(my + 1u, cuda::memory_order_release);
+    } else {
+      long long k = 0;
+      while (gen.load(cuda::memory_order_acquire) == my) {
+        if (++k > spin_limit) {
+          atomicOr(flags, 4);
+          s_ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    if (s_ok && (cuda::atomic_ref<int, cuda::thread_scope_device>(*flags).load(cuda::memory_order_relaxed) & 4))
+      s_ok = 0;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Sum of column c (stride 4) of nb per-CTA partials, in the same fixed order
+// in every CTA, so that every CTA takes the same scalar.
+__device__ __forceinline__ double sum_partials(const double* part, int nb, int c, double* sh) {
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) acc += __ldcg(part + 4 * k + c);
+  const double t = block_sum(acc, sh);
+  __shared__ double s_t;
+  if (threadIdx.x == 0) s_t = t;
+  __syncthreads();
+  return s_t;
+}
+
 inline int reduce_grid(int64_t count) {
   int64_t g = (count + kReduceBlock - 1) / kReduceBlock;
   if (g < 1) g = 1;
@@ -798,6 +846,194 @@ __global__ void convert_kernel(int64_t count, const void* src, double* dst, int 
 // Host-side launch helpers shared by the per-precision translation units.
 inline unsigned blocks_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
 
+// Algorithm 5 for rho_F and rho_S in one cooperative launch: the iteration
+// loops run on the device (every CTA takes the same scalars from the same
+// partial sums, so all take the same branches) and the host reads the two
+// estimates once.  FP64 path: the differences f(y + q v) - f(y) of Algorithm
+// 5; mixed path: q J v (q L v for f_F, dual numbers for f_S).  Iterates
+// ping-pong between two buffers per estimate; out[4], out[5] say which holds
+// the last one.
+template <class MD, class MDu, typename Z, bool MIXED>
+__global__ void __launch_bounds__(kReduceBlock) power_fused_kernel(const PowerFusedArgs a, const Ell A) {
+  constexpr int NE = MD::NE, NS = MD::NS, N = 1 + NE + NS;
+  __shared__ double sh[32];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int G = gridDim.x;
+  const Z* Zs = static_cast<const Z*>(a.Z);
+  int par = 0;
+  auto part = [&](int p) { return a.part + (size_t)p * 4 * G; };
+  auto publish = [&](double v0, double v1, double v2, double v3) {
+    const double t0 = block_sum(v0, sh), t1 = block_sum(v1, sh), t2 = block_sum(v2, sh), t3 = block_sum(v3, sh);
+    if (threadIdx.x == 0) {
+      double* p = part(par) + 4 * blockIdx.x;
+      p[0] = t0;
+      p[1] = t1;
+      p[2] = t2;
+      p[3] = t3;
+    }
+  };
+  // norms of y and of the start iterates; f_S(y) for the FP64 differences
+  {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    for (int64_t i = i0; i < a.n; i += stride) {
+      double y[N];
+      y[0] = a.V[i];
+#pragma unroll
+      for (int k = 1; k < N; ++k) y[k] = (double)Zs[(k - 1) * a.ld + i];
+      s0 += y[0] * y[0];
+      s1 += a.vF[0][i] * a.vF[0][i];
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        s2 += y[k] * y[k];
+        const double v = a.vS[0][k * a.ld + i];
+        s3 += v * v;
+      }
+      if constexpr (!MIXED) {
+        double f[N];
+        const double Istim = (a.mask != nullptr && a.mask[i]) ? a.stim : 0.0;
+        fS_full<MD>(y, Istim, a.Cm, f);
+#pragma unroll
+        for (int k = 0; k < N; ++k) a.fy[k * a.ld + i] = f[k];
+      }
+    }
+    publish(s0, s1, s2, s3);
+  }
+  if (!grid_barrier(a.bar, a.flags, a.spin_limit)) return;
+  const double nyF = sqrt(sum_partials(part(par), G, 0, sh));
+  double nvF = sqrt(sum_partials(part(par), G, 1, sh));
+  const double nyS = sqrt(sum_partials(part(par), G, 2, sh));
+  double nvS = sqrt(sum_partials(part(par), G, 3, sh));
+  par ^= 1;
+
+  // rho_F on the V block
+  double rhoF = a.rhoF_warm;
+  int itF = 0, curF = 0;
+  {
+    const double delta = nyF > 0.0 ? nyF * a.eps : a.eps;
+    if (nvF == 0.0) {
+      rhoF = 0.0;
+    } else {
+      double q = delta / nvF, rho_old = 0.0;
+      while (fabs(rhoF - rho_old) >= a.tol * rhoF && itF < a.max_iter) {
+        rho_old = rhoF;
+        const double* vo = a.vF[curF];
+        double* vn = a.vF[curF ^ 1];
+        double acc = 0.0;
+        for (int64_t i = i0; i < a.n; i += stride) {
+          const int64_t b = i >> 5;
+          const int w = __ldg(A.width + b);
+          int64_t p = __ldg(A.slice_ptr + b) + (i & 31);
+          double wv;
+          if constexpr (MIXED) {
+            const float vi = (float)__ldcg(vo + i);
+            float s32 = 0.0f;
+            for (int k = 0; k < w; ++k, p += 32) s32 += __ldg(A.val32 + p) * ((float)__ldcg(vo + __ldg(A.col + p)) - vi);
+            wv = q * (double)s32;
+          } else {
+            double fz = 0.0, fy = 0.0;
+            for (int k = 0; k < w; ++k, p += 32) {
+              const int32_t c = __ldg(A.col + p);
+              fz += __ldg(A.val + p) * (a.V[c] + q * __ldcg(vo + c));
+              fy += __ldg(A.val + p) * a.V[c];
+            }
+            wv = fz - fy;
+          }
+          vn[i] = wv;
+          acc += wv * wv;
+        }
+        publish(acc, 0.0, 0.0, 0.0);
+        if (!grid_barrier(a.bar, a.flags, a.spin_limit)) return;
+        const double nv = sqrt(sum_partials(part(par), G, 0, sh));
+        par ^= 1;
+        curF ^= 1;
+        ++itF;
+        if (nv == 0.0) {
+          rhoF = 0.0;
+          break;
+        }
+        q = delta / nv;
+        rhoF = nv / delta;
+      }
+    }
+  }
+
+  // rho_S on the full state
+  double rhoS = a.rhoS_warm;
+  int itS = 0, curS = 0;
+  {
+    const double delta = nyS > 0.0 ? nyS * a.eps : a.eps;
+    if (nvS == 0.0) {
+      rhoS = 0.0;
+    } else {
+      double q = delta / nvS, rho_old = 0.0;
+      while (fabs(rhoS - rho_old) >= a.tol * rhoS && itS < a.max_iter) {
+        rho_old = rhoS;
+        const double* vo = a.vS[curS];
+        double* vn = a.vS[curS ^ 1];
+        double acc = 0.0;
+        for (int64_t i = i0; i < a.n; i += stride) {
+          if constexpr (MIXED) {
+            Dual y[N];
+            y[0] = Dual((float)a.V[i], (float)vo[i]);
+#pragma unroll
+            for (int k = 1; k < N; ++k) y[k] = Dual((float)Zs[(k - 1) * a.ld + i], (float)vo[k * a.ld + i]);
+            Dual I;
+            Dual gS[NS > 0 ? NS : 1];
+            MDu::currents(y[0], y + 1, y + 1 + NE, I, gS);
+            const double w0 = q * (double)(-I.d * (float)(1.0 / a.Cm));
+            vn[i] = w0;
+            acc += w0 * w0;
+#pragma unroll
+            for (int k = 0; k < NE; ++k) vn[(1 + k) * a.ld + i] = 0.0;
+#pragma unroll
+            for (int k = 0; k < NS; ++k) {
+              const double w = q * (double)gS[k].d;
+              vn[(1 + NE + k) * a.ld + i] = w;
+              acc += w * w;
+            }
+          } else {
+            double y[N], f[N];
+            y[0] = a.V[i];
+#pragma unroll
+            for (int k = 1; k < N; ++k) y[k] = (double)Zs[(k - 1) * a.ld + i];
+#pragma unroll
+            for (int k = 0; k < N; ++k) y[k] = y[k] + q * vo[k * a.ld + i];
+            const double Istim = (a.mask != nullptr && a.mask[i]) ? a.stim : 0.0;
+            fS_full<MD>(y, Istim, a.Cm, f);
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+              const double w = f[k] - a.fy[k * a.ld + i];
+              vn[k * a.ld + i] = w;
+              acc += w * w;
+            }
+          }
+        }
+        publish(acc, 0.0, 0.0, 0.0);
+        if (!grid_barrier(a.bar, a.flags, a.spin_limit)) return;
+        const double nv = sqrt(sum_partials(part(par), G, 0, sh));
+        par ^= 1;
+        curS ^= 1;
+        ++itS;
+        if (nv == 0.0) {
+          rhoS = 0.0;
+          break;
+        }
+        q = delta / nv;
+        rhoS = nv / delta;
+      }
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.out[0] = rhoF;
+    a.out[1] = rhoS;
+    a.out[2] = (double)itF;
+    a.out[3] = (double)itS;
+    a.out[4] = (double)curF;
+    a.out[5] = (double)curS;
+  }
+}
+
 // Launch with the programmatic-serialisation attribute when pdl is set.
 template <typename... KArgs, typename... Args>
 inline void launch_k(bool pdl, void (*k)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
@@ -856,6 +1092,21 @@ struct Kernels {
     if constexpr (MIXED) powerS_dual_kernel<MDu, Z><<<reduce_grid(a.n), kReduceBlock, 0, st>>>(a, rs);
     else powerS_kernel<MD, Z><<<reduce_grid(a.n), kReduceBlock, 0, st>>>(a, rs);
   }
+  static cudaError_t power_fused(const PowerFusedArgs& a, const Ell& A, int grid, cudaStream_t st) {
+    PowerFusedArgs ac = a;
+    Ell Ac = A;
+    void* args[] = {&ac, &Ac};
+    const int64_t need = (a.n + kReduceBlock - 1) / kReduceBlock;
+    const int g = (int)std::min<int64_t>(grid, std::max<int64_t>(need, 1));
+    return cudaLaunchCooperativeKernel((const void*)power_fused_kernel<MD, MDu, Z, MIXED>, dim3(g),
+                                       dim3(kReduceBlock), args, 0, st);
+  }
+  static int power_fused_grid(int device) {
+    int per_sm = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, power_fused_kernel<MD, MDu, Z, MIXED>, kReduceBlock, 0);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    return per_sm * sms;
+  }
   static void fS_eval(const PowerSArgs& a, double* out, cudaStream_t st) {
     if (a.n == 0) return;
     fS_kernel<MD, Z><<<reduce_grid(a.n), kReduceBlock, 0, st>>>(a, out);
@@ -898,6 +1149,8 @@ struct Kernels {
     ks->state_sumsq = &state_sumsq;
     ks->convert_z = &convert_z;
     ks->tma_grid = &tma_grid;
+    ks->power_fused = &power_fused;
+    ks->power_fused_grid = &power_fused_grid;
   }
 };
 

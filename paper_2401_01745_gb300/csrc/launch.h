@@ -149,6 +149,26 @@ struct PowerSArgs {
   int slot = 0;
 };
 
+// Algorithm 5 for rho_F and rho_S in one cooperative launch.
+struct PowerFusedArgs {
+  int64_t n = 0, ld = 0;
+  const double* V = nullptr;
+  const void* Z = nullptr;
+  double* vF[2] = {nullptr, nullptr};  // iterate on V: current in [0] at entry
+  double* vS[2] = {nullptr, nullptr};  // iterate on the full state (N x ld)
+  double* fy = nullptr;                // FP64 path: f_S(y), N x ld
+  const uint8_t* mask = nullptr;
+  double stim = 0, Cm = 1;
+  double eps = 1e-8, tol = 1e-2;
+  int max_iter = 50;
+  double rhoF_warm = 0, rhoS_warm = 0;
+  double* part = nullptr;              // 2 x 4 x grid partial sums
+  unsigned int* bar = nullptr;         // grid barrier
+  int* flags = nullptr;
+  long long spin_limit = 0;
+  double* out = nullptr;               // rho_F, rho_S, it_F, it_S, last buffer of v_F, of v_S
+};
+
 struct Launchers;  // per precision mode
 
 // Kernel launchers, implemented per precision (FP64 / mixed) and per model.
@@ -164,6 +184,8 @@ struct KernelSet {
                       const ReduceScratch&, int slot, cudaStream_t) = nullptr;
   void (*convert_z)(int64_t count, const void* src, double* dst, int to_double, cudaStream_t) = nullptr;
   int (*tma_grid)(int device, int wmax) = nullptr;  // grid of the persistent stage kernel (0: not used)
+  cudaError_t (*power_fused)(const PowerFusedArgs&, const Ell&, int grid, cudaStream_t) = nullptr;
+  int (*power_fused_grid)(int device) = nullptr;
 };
 
 // mRKC (mrkc.cu, FP64): one outer stage (stage kernel, inner stage 1) or

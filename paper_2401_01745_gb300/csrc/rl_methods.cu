@@ -16,8 +16,6 @@
 // system M B x = M c with its diagonal as preconditioner.  The solve stops
 // when ||r||_M <= rtol ||c||_M or after max_iter iterations, warm started
 // from x_0 = V_n.
-#include <cooperative_groups.h>
-#include <cuda/atomic>
 
 #include "kernels.cuh"
 
@@ -123,51 +121,6 @@ __global__ void __launch_bounds__(kReduceBlock) imex_rl_setup_kernel(const RlArg
   }
 }
 
-// Grid-wide barrier of the cooperative PCG launch (all CTAs co-resident).
-// Bounded: after spin_limit polls it records error bit 4 and returns false.
-__device__ __forceinline__ bool grid_barrier(const PcgArgs& a) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> gen(a.bar[1]);
-    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> cnt(a.bar[0]);
-    const unsigned int my = gen.load(cuda::memory_order_acquire);
-    s_ok = 1;
-    __threadfence();  // the CTA's writes (ordered by the bar.sync above) before the arrival
-    if (cnt.fetch_add(1u, cuda::memory_order_acq_rel) == gridDim.x - 1) {
-      cnt.store(0u, cuda::memory_order_relaxed);
-      gen.store(my + 1u, cuda::memory_order_release);
-    } else {
-      long long k = 0;
-      while (gen.load(cuda::memory_order_acquire) == my) {
-        if (++k > a.spin_limit) {
-          atomicOr(a.flags, 4);
-          s_ok = 0;
-          break;
-        }
-        __nanosleep(32);
-      }
-    }
-    __threadfence();
-    if (s_ok && (cuda::atomic_ref<int, cuda::thread_scope_device>(*a.flags).load(cuda::memory_order_relaxed) & 4))
-      s_ok = 0;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
-// Sum of column c (stride 4) of nb per-CTA partials, in the same fixed order
-// in every CTA, so that every CTA takes the same scalar.
-__device__ __forceinline__ double sum_partials(const double* part, int nb, int c, double* sh) {
-  double acc = 0.0;
-  for (int k = threadIdx.x; k < nb; k += blockDim.x) acc += __ldcg(part + 4 * k + c);
-  const double t = block_sum(acc, sh);
-  __shared__ double s_t;
-  if (threadIdx.x == 0) s_t = t;
-  __syncthreads();
-  return s_t;
-}
-
 // The PCG iterations of the implicit diffusion step, one cooperative launch.
 // Loads of vectors written by other CTAs within the launch go through L2.
 __global__ void __launch_bounds__(kPcgBlock) imex_pcg_kernel(const PcgArgs a, const Ell A) {
@@ -206,7 +159,7 @@ __global__ void __launch_bounds__(kPcgBlock) imex_pcg_kernel(const PcgArgs a, co
       const double t = block_sum(pq, sh);
       if (threadIdx.x == 0) a.part[4 * blockIdx.x + 0] = t;
     }
-    if (!grid_barrier(a)) return;
+    if (!grid_barrier(a.bar, a.flags, a.spin_limit)) return;
     const double alpha = rz / sum_partials(a.part, gridDim.x, 0, sh);
     // x += alpha p; r -= alpha q; z = P^-1 r; <r, z>_M, <r, r>_M
     double s_rz = 0.0, s_rr = 0.0;
@@ -229,7 +182,7 @@ __global__ void __launch_bounds__(kPcgBlock) imex_pcg_kernel(const PcgArgs a, co
         a.part[4 * blockIdx.x + 2] = t2;
       }
     }
-    if (!grid_barrier(a)) return;
+    if (!grid_barrier(a.bar, a.flags, a.spin_limit)) return;
     rz_prev = rz;
     rz = sum_partials(a.part, gridDim.x, 1, sh);
     rr = sum_partials(a.part, gridDim.x, 2, sh);

@@ -51,7 +51,8 @@ void free_all(emrkc_solver* s) {
                   s->rs.partials, s->rs.ticket, s->rs.result, s->d_V32[0], s->d_V32[1], s->d_V32[2],
                   s->d_D[0], s->d_D[1], s->d_D[2], s->d_LV, s->d_Vlo[0], s->d_Vlo[1], s->d_Vlo[2],
                   s->d_Vn32, s->d_mass, s->d_cg[0], s->d_cg[1], s->d_cg[2], s->d_cg[3], s->d_cg[4],
-                  s->d_cg[5], s->d_part, s->d_bar, s->d_iters, s->d_res, s->d_Um[0], s->d_Um[1], s->d_Um[2]};
+                  s->d_cg[5], s->d_part, s->d_bar, s->d_iters, s->d_res, s->d_Um[0], s->d_Um[1], s->d_Um[2],
+                  s->d_ppart, s->d_pbar};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (s->h_pin) cudaFreeHost(s->h_pin);
@@ -296,6 +297,59 @@ int do_step_rl(emrkc_solver* s, double dt) {
   return EMRKC_OK;
 }
 
+// Algorithm 5 for rho_F and rho_S in one cooperative launch (emRKC): the
+// iteration loops run on the device; one read of the results.
+int power_fused(emrkc_solver* s) {
+  materialise_V(s);
+  PowerFusedArgs a;
+  a.n = s->n;
+  a.ld = s->ld;
+  a.V = s->d_V[s->cur];
+  a.Z = s->d_Z[s->cur];
+  a.vF[0] = s->d_vF;
+  a.vF[1] = s->d_vF2;
+  a.vS[0] = s->d_vS;
+  a.vS[1] = s->d_vS2;
+  a.fy = s->d_fy;
+  a.mask = s->d_mask;
+  a.stim = stim_at(s, s->t);
+  a.Cm = s->Cm;
+  a.eps = s->opt.pow_eps;
+  a.tol = s->opt.pow_tol;
+  a.max_iter = s->opt.pow_max_iter;
+  a.rhoF_warm = s->rhoF_raw;
+  a.rhoS_warm = s->rhoS_raw;
+  a.part = s->d_ppart;
+  a.bar = s->d_pbar;
+  a.flags = s->d_flags;
+  a.spin_limit = 1ll << 26;
+  a.out = s->rs.result;
+  cudaError_t e = cudaMemsetAsync(s->d_pbar, 0, 2 * sizeof(unsigned int), s->stream);
+  if (e != cudaSuccess) return s->cuda_fail(e, "barrier reset");
+  s->launch(EMRKC_PHASE_POWER_S, [&] { e = s->ks.power_fused(a, s->ell, s->pfused_grid, s->stream); });
+  if (e != cudaSuccess) return s->cuda_fail(e, "cooperative power-iteration launch");
+  int rc = read_results(s, 0, 6);
+  if (rc) return rc;
+  if ((rc = check_flags(s))) return rc;
+  s->rhoF_raw = s->h_pin[0];
+  s->rhoS_raw = s->h_pin[1];
+  s->itF = (int)s->h_pin[2];
+  s->itS = (int)s->h_pin[3];
+  s->total_it += s->itF + s->itS;
+  if (s->h_pin[4] != 0.0) std::swap(s->d_vF, s->d_vF2);
+  if (s->h_pin[5] != 0.0) std::swap(s->d_vS, s->d_vS2);
+  return EMRKC_OK;
+}
+
+// Both spectral radii now: one cooperative launch for emRKC, the host-driven
+// loops for mRKC (whose f~_F and f~_S have their own kernels).
+int update_rho_now(emrkc_solver* s) {
+  if (s->method == EMRKC_METHOD_EMRKC && s->pfused_grid > 0) return power_fused(s);
+  int rc = power_F(s);
+  if (!rc) rc = power_S(s);
+  return rc;
+}
+
 // rho policy shared by emRKC and mRKC: (rho_F, rho_S) with the safety factor
 int step_rho(emrkc_solver* s, double* rhoF, double* rhoS) {
   int rc;
@@ -307,8 +361,7 @@ int step_rho(emrkc_solver* s, double* rhoF, double* rhoS) {
   }
   const bool due = (s->opt.rho_every == EMRKC_RHO_ONCE) ? !s->rho_done : (s->steps % s->opt.rho_every == 0);
   if (due) {
-    if ((rc = power_F(s))) return rc;
-    if ((rc = power_S(s))) return rc;
+    if ((rc = update_rho_now(s))) return rc;
     s->rho_done = true;
   }
   *rhoF = s->opt.safety * s->rhoF_raw;
@@ -706,8 +759,7 @@ int state_copy(emrkc_solver* s, int var, double* buf, int64_t len, bool to_host,
 
 namespace emrkc {
 int solver_update_rho(emrkc_solver* s) {
-  int rc = power_F(s);
-  if (!rc) rc = power_S(s);
+  int rc = update_rho_now(s);
   if (!rc) s->rho_done = true;
   return rc;
 }
@@ -900,6 +952,13 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
   fail |= dalloc(&s->d_tmp, (int64_t)std::max(1, s->N - 1) * ld) != cudaSuccess;
   fail |= dalloc(&s->d_rest, 64) != cudaSuccess;
   fail |= dalloc(&s->d_flags, 4) != cudaSuccess;
+  if (s->method == EMRKC_METHOD_EMRKC) {
+    s->pfused_grid = s->ks.power_fused_grid(s->device);
+    if (s->pfused_grid > 0) {
+      fail |= dalloc(&s->d_ppart, 8 * (int64_t)s->pfused_grid) != cudaSuccess;
+      fail |= dalloc(&s->d_pbar, 2) != cudaSuccess;
+    }
+  }
   fail |= dalloc(&s->rs.partials, kReduceMaxBlocks) != cudaSuccess;
   fail |= dalloc(&s->rs.ticket, 4) != cudaSuccess;
   fail |= dalloc(&s->rs.result, 16) != cudaSuccess;
@@ -1021,8 +1080,8 @@ int emrkc_get_activation_times(emrkc_solver* s, double* host_out, int64_t n) {
 int emrkc_estimate_rho(emrkc_solver* s, double* rho_F, double* rho_S, int* it_F, int* it_S) {
   if (!s) return EMRKC_ERR_ARG;
   cudaSetDevice(s->device);
-  int rc = power_F(s);
-  if (!rc) rc = power_S(s);
+  s->itF = s->itS = 0;
+  int rc = update_rho_now(s);
   if (rc) return rc;
   if (rho_F) *rho_F = s->rhoF_raw;
   if (rho_S) *rho_S = s->rhoS_raw;

@@ -148,6 +148,10 @@ struct emrkc_solver {
   int64_t mat_entries = 0, mat_slots = 0;
   int tma_grid = 0;  // persistent bulk-copy stage kernel grid (mixed path), 0 = off
   int pdl = 0;             // mixed path: programmatic dependent launch of the step kernels
+  // Algorithm 5 in one cooperative launch (emRKC)
+  int pfused_grid = 0;
+  double* d_ppart = nullptr;      // 2 x 4 x grid partial sums
+  unsigned int* d_pbar = nullptr; // grid barrier
   // EXEX-RL / IMEX-RL (rl_methods.cu)
   int method = 0;
   double* d_mass = nullptr;     // lumped mass (IMEX-RL)
