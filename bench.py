@@ -177,6 +177,35 @@ def _sum_over_ranks(x, world, device):
     return float(t.item())
 
 
+def step_bytes_mixed(N, s, m, offd):
+    """Compulsory bytes per node of one mixed-precision emRKC step (neighbour
+    gathers assumed to hit in cache): per outer stage j the stage item reads V
+    hi, z, the stimulus mask and the row of L (FP32 value + int32 column) and
+    writes z; with m = 1 it also reads V lo and writes V hi/lo, otherwise it
+    writes delta_1 (and L V + F when m >= 4); j >= 2 adds g_{j-2} (z, V hi/lo);
+    each inner item k reads delta_{k-1} (delta_{k-2} for k >= 3, L V + F for
+    m >= 4) and the row of L and writes delta_k, the last one reading g_{j-1}
+    (and g_{j-2}) V hi/lo and writing V hi/lo; the last stage of the step
+    reads V_n hi for the activation test, and with s >= 2 stage 1 keeps a
+    copy of it."""
+    z = (N - 1) * 4
+    L = offd * 8
+    total = 0.0
+    for j in range(1, s + 1):
+        st = 4 + z + 1 + L + z
+        st += (4 + 8) if m == 1 else (4 + (4 if m >= 4 else 0))
+        if j >= 2:
+            st += z + 8
+        if j == 1 and s >= 2:
+            st += 4
+        total += st
+        for k in range(2, m + 1):
+            inn = 4 + (4 if k >= 3 else 0) + (4 if m >= 4 else 0) + L
+            inn += (8 + (8 if j >= 2 else 0) + 8) if k == m else 4
+            total += inn
+    return total + 4
+
+
 def _aggregate(units, ms, world, device):
     """Whole-job throughput of N replicas: the units all ranks processed over
     the slowest rank's time (weak scaling).  Returns (value, max ms)."""
@@ -268,16 +297,12 @@ def run_batched(args):
             b.step(0.05)
     b.sync()
     tile, block, tune_ms = b.autotune(0.05, reps=3)
-    # algorithmic bytes per step (mixed path, per instance: stage + (m-1) inner stages)
+    # algorithmic bytes per step (mixed path, per instance: s outer stages of
+    # one stage item and m - 1 inner items each)
     for iid in b.ids():
         info = b.info(iid)
-        n, N, m = info["n"], info["N"], info["m"]
         offd = 6 if len(specs[iid - 1]["dims"]) == 3 else 4  # stored off-diagonals per row
-        mat_b = offd * 8
-        # V (hi, or hi+lo when m = 1), z in and out, mask, L, and 16 B of V / delta_1, LV, F
-        stage = 2 * (N - 1) * 4 + 1 + mat_b + 16
-        inner = 4 + 4 + 4 + 8 + mat_b + 8
-        bytes_step += n * (stage + (m - 1) * inner)
+        bytes_step += info["n"] * step_bytes_mixed(info["N"], info["s"], info["m"], offd)
     torch.cuda.synchronize()
     _barrier(world)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

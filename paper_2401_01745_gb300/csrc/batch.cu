@@ -5,7 +5,7 @@
 // Work is a phase-major list of items (instance, phase, tile); phase p of an
 // instance is stage j = p / m + 1 with inner stage k = p % m + 1 (k = 1: the
 // fused stage work, k >= 2: an inner SpMV stage).  Persistent CTAs take items
-// in list order from an atomic ticket.  An item of phase p > 0 waits until all
+// in list order from an atomic ticket, one item ahead.  An item of phase p > 0 waits until all
 // tiles of phase p - 1 of its instance are done (per-instance counters).
 // Because items are taken in order and an item only waits on items earlier in
 // the list, every awaited item is already held by a running CTA: the schedule
@@ -37,15 +37,24 @@ template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) batch_step_kernel(const BatchCtl c) {
   __shared__ unsigned int s_item;
   __shared__ int s_abort;
+  // Thread 0 takes the next ticket while the CTA works on the current item
+  // (its value is first used one item later, so the atomic's round trip is
+  // hidden).  A CTA processes its tickets in increasing order, so the
+  // smallest unfinished item is always the current item of some CTA: the
+  // in-order argument above still holds.
+  unsigned int next_ticket = 0;
+  if (threadIdx.x == 0) next_ticket = atomicAdd(c.ticket, 1u);
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) {
       s_abort = 0;
       // stop early if another CTA gave up on a wait
-      if (cuda::atomic_ref<int, cuda::thread_scope_device>(*c.err).load(cuda::memory_order_relaxed) != 0)
+      if (cuda::atomic_ref<int, cuda::thread_scope_device>(*c.err).load(cuda::memory_order_relaxed) != 0) {
         s_item = 0xffffffffu;
-      else
-        s_item = atomicAdd(c.ticket, 1u);
+      } else {
+        s_item = next_ticket;
+        next_ticket = atomicAdd(c.ticket, 1u);
+      }
     }
     __syncthreads();
     const unsigned int it = s_item;

@@ -515,7 +515,7 @@ int emrkc_batch_autotune(emrkc_batch* b, double dt, int reps, int* tile_out, int
   if (rc) return rc;
   for (auto& mb : b->members)
     if (mb.S >= 3) return b->fail(EMRKC_ERR_STATE, "an instance has s >= 3: dry steps would overwrite its state");
-  const int tiles[] = {512, 1024, 2048, 4096};
+  const int tiles[] = {512, 1024, 2048, 4096, 8192};
   const int blocks[] = {128, 256};
   const int keep_tile = b->tile, keep_block = b->block;
   int best_tile = keep_tile, best_block = keep_block;

@@ -346,6 +346,64 @@ __host__ __device__ constexpr int tma_stage_bytes(int nz, int wmax) {
   return tma_fixed_bytes(nz) + (wmax <= kTmaStageEllWidth ? 2 * 4 * wmax * 32 * 4 : 0);
 }
 
+// One node of an outer stage (mixed path) from a shared-memory stage buffer
+// holding the tile's z rows, V hi and stimulus mask (kTmaTile entries each):
+// the body of the bulk-copy stage kernels.  scol/sval/base locate the row in
+// a staged sliced-ELL tile, or scol = nullptr to read the row from global.
+template <class Model, bool HAS_M2>
+__device__ __forceinline__ void stage_node_staged(const StageArgs& a, const Ell& A, const int64_t i, const int tid,
+                                                  const float* sz, const int32_t* scol, const float* sval,
+                                                  const int base) {
+  constexpr int NE = Model::NE, NS = Model::NS, NZ = NE + NS;
+  float z[NZ > 0 ? NZ : 1];
+#pragma unroll
+  for (int k = 0; k < NZ; ++k) z[k] = sz[k * kTmaTile + tid];
+  const float V = sz[NZ * kTmaTile + tid];
+  const unsigned char mk = reinterpret_cast<const unsigned char*>(sz + (NZ + 1) * kTmaTile)[tid];
+  float zE1[NE > 0 ? NE : 1];
+  float Iion;
+  float gS[NS > 0 ? NS : 1];
+  ionic_mixed<Model>(a.f_eta, V, z, zE1, Iion, gS);
+  const float Istim = mk ? a.f_stim : 0.0f;
+  const float F = (Istim - Iion) * a.f_inv_Cm;
+  float* __restrict__ Zout = static_cast<float*>(a.Zout);
+  const float* __restrict__ Zm2 = static_cast<const float*>(a.Zm2);
+  const int64_t ld = a.ld;
+  if constexpr (NZ > 0) {
+#pragma unroll
+    for (int k = 0; k < NZ; ++k) {
+      const float fbar = (k < NE) ? (zE1[k < NE ? k : 0] - z[k]) * a.f_inv_eta : a.f_cm * gS[k >= NE ? k - NE : 0];
+      float out;
+      if constexpr (HAS_M2) out = a.f_nu * z[k] + a.f_kappa * __ldg(Zm2 + k * ld + i) + a.f_mudt * fbar;
+      else out = z[k] + a.f_mudt * fbar;
+      Zout[k * ld + i] = out;
+    }
+  }
+  // sparse row: slot k of row i at base + 32 k in the staged tile
+  float LV = 0.0f;
+  if (scol == nullptr) {
+    LV = ell_diff32<false>(A, i, a.V32m1);
+  } else {
+    const int w = __ldg(A.width + (i >> 5));
+    for (int k = 0; k < w; ++k) LV += sval[base + 32 * k] * (__ldg(a.V32m1 + scol[base + 32 * k]) - V);
+  }
+  if (a.Vn32_copy != nullptr) a.Vn32_copy[i] = V;
+  if (a.m == 1) {
+    const float fbarV = a.f_mu1 * (LV + F);
+    const float lo1 = __ldg(a.Vlo_m1 + i);
+    float inc = a.f_mudt * fbarV;
+    if constexpr (HAS_M2) inc += a.f_kappa * ((__ldg(a.Vhi_m2 + i) - V) + (__ldg(a.Vlo_m2 + i) - lo1));
+    float hi, lo;
+    ff_add(V, lo1, inc, hi, lo);
+    a.V32out[i] = hi;
+    a.Vlo_out[i] = lo;
+    if (a.final_stage) step_epilogue_ff(i, __ldg(a.Vn32 + i), hi, a.act, a.t_n, a.dt, a.f_th, a.flags);
+  } else {
+    a.D1[i] = a.f_mu1eta * (LV + F);
+    if (a.LV != nullptr) a.LV[i] = LV + F;  // kept for inner stages k >= 4 only
+  }
+}
+
 template <class Model, bool HAS_M2>
 __global__ void __launch_bounds__(kTmaTile) stage_kernel_mixed_tma(const StageArgs a, const Ell A) {
   constexpr int NE = Model::NE, NS = Model::NS, NZ = NE + NS;
@@ -423,57 +481,15 @@ __global__ void __launch_bounds__(kTmaTile) stage_kernel_mixed_tma(const StageAr
     const float* sz = reinterpret_cast<const float*>(tma_smem + buf * SB);
     const int64_t i = tile * kTmaTile + tid;
     if (i < a.n) {
-      float z[NZ > 0 ? NZ : 1];
-#pragma unroll
-      for (int k = 0; k < NZ; ++k) z[k] = sz[k * kTmaTile + tid];
-      const float V = sz[NZ * kTmaTile + tid];
-      const unsigned char mk = reinterpret_cast<const unsigned char*>(sz + (NZ + 1) * kTmaTile)[tid];
-      float zE1[NE > 0 ? NE : 1];
-      float Iion;
-      float gS[NS > 0 ? NS : 1];
-      ionic_mixed<Model>(a.f_eta, V, z, zE1, Iion, gS);
-      const float Istim = mk ? a.f_stim : 0.0f;
-      const float F = (Istim - Iion) * a.f_inv_Cm;
-      float* __restrict__ Zout = static_cast<float*>(a.Zout);
-      const float* __restrict__ Zm2 = static_cast<const float*>(a.Zm2);
-      const int64_t ld = a.ld;
-      if constexpr (NZ > 0) {
-#pragma unroll
-        for (int k = 0; k < NZ; ++k) {
-          const float fbar = (k < NE) ? (zE1[k < NE ? k : 0] - z[k]) * a.f_inv_eta : a.f_cm * gS[k >= NE ? k - NE : 0];
-          float out;
-          if constexpr (HAS_M2) out = a.f_nu * z[k] + a.f_kappa * __ldg(Zm2 + k * ld + i) + a.f_mudt * fbar;
-          else out = z[k] + a.f_mudt * fbar;
-          Zout[k * ld + i] = out;
-        }
+      const int32_t* scol = nullptr;
+      const float* sval = nullptr;
+      int base = 0;
+      if (stage_ell) {
+        base = (int)(__ldg(A.slice_ptr + (i >> 5)) - __ldg(A.slice_ptr + tile * (kTmaTile / 32))) + (tid & 31);
+        scol = reinterpret_cast<const int32_t*>(tma_smem + buf * SB + FB);
+        sval = reinterpret_cast<const float*>(tma_smem + buf * SB + FB + 4 * a.ell_wmax * 32 * 4);
       }
-      // sparse row from the staged tile: slot k of row i at (slice offset) + 32 k + lane
-      float LV = 0.0f;
-      if (!stage_ell) {
-        LV = ell_diff32<false>(A, i, a.V32m1);
-      } else {
-        const int64_t b = i >> 5;
-        const int w = __ldg(A.width + b);
-        const int base = (int)(__ldg(A.slice_ptr + b) - __ldg(A.slice_ptr + tile * (kTmaTile / 32))) + (tid & 31);
-        const int32_t* scol = reinterpret_cast<const int32_t*>(tma_smem + buf * SB + FB);
-        const float* sval = reinterpret_cast<const float*>(tma_smem + buf * SB + FB + 4 * a.ell_wmax * 32 * 4);
-        for (int k = 0; k < w; ++k) LV += sval[base + 32 * k] * (__ldg(a.V32m1 + scol[base + 32 * k]) - V);
-      }
-      if (a.Vn32_copy != nullptr) a.Vn32_copy[i] = V;
-      if (a.m == 1) {
-        const float fbarV = a.f_mu1 * (LV + F);
-        const float lo1 = __ldg(a.Vlo_m1 + i);
-        float inc = a.f_mudt * fbarV;
-        if constexpr (HAS_M2) inc += a.f_kappa * ((__ldg(a.Vhi_m2 + i) - V) + (__ldg(a.Vlo_m2 + i) - lo1));
-        float hi, lo;
-        ff_add(V, lo1, inc, hi, lo);
-        a.V32out[i] = hi;
-        a.Vlo_out[i] = lo;
-        if (a.final_stage) step_epilogue_ff(i, __ldg(a.Vn32 + i), hi, a.act, a.t_n, a.dt, a.f_th, a.flags);
-      } else {
-        a.D1[i] = a.f_mu1eta * (LV + F);
-        if (a.LV != nullptr) a.LV[i] = LV + F;  // kept for inner stages k >= 4 only
-      }
+      stage_node_staged<Model, HAS_M2>(a, A, i, tid, sz, scol, sval, base);
     }
     __syncthreads();  // every thread is done with this stage buffer
     if (tid == 0 && tile + 2 * G < ntiles) {
