@@ -13,21 +13,30 @@
 // spin_limit polls the kernel records an error and every CTA returns.
 //
 // The per-node arithmetic is the mixed-precision stage / inner code of the
-// single-instance kernels (stage_node_mixed, inner_node_mixed), with loads of
-// data produced within the launch taken through L2 (ld.cg).
+// single-instance kernels (stage_node_mixed, inner_node_mixed); see
+// batch_stage_rows for when loads may go through L1.
 #include <cuda/atomic>
 
 #include "kernels.cuh"
 
 namespace emrkc {
 
-// Stage j = 1 reads only what earlier launches wrote (read-only cached loads
-// are safe); stage j >= 2 reads g_{j-1}, written earlier in this launch
-// (loads through L2).
+// Which loads may use the non-coherent (L1) path.  L1 holds no line of a
+// buffer from an earlier launch, so a load can go through L1 unless this
+// launch rewrites a buffer after reading it: the three state buffers rotate
+// with period 3 over the s outer stages and the three increment buffers over
+// the m inner stages, so with s <= 2 and m <= 3 every buffer is written at
+// most once and only read after its write (or only read) within a launch.
+// Otherwise data produced within the launch are loaded through L2 (ld.cg).
 template <class Model>
-__device__ __forceinline__ void batch_stage_rows(const StageArgs& a, const Ell& A, int64_t r0, int64_t r1, bool has_m2) {
+__device__ __forceinline__ void batch_stage_rows(const StageArgs& a, const Ell& A, int64_t r0, int64_t r1, bool has_m2,
+                                                 bool cg) {
   if (has_m2) {
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) stage_node_mixed<Model, true, true>(a, A, i);
+    if (cg) {
+      for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) stage_node_mixed<Model, true, true>(a, A, i);
+    } else {
+      for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) stage_node_mixed<Model, true, false>(a, A, i);
+    }
   } else {
     for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) stage_node_mixed<Model, false, false>(a, A, i);
   }
@@ -126,11 +135,12 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) batch_step_kernel(const B
       a.f_mu1eta = I->f_mu1eta;
       a.f_eta = I->f_eta;
       const bool has_m2 = j >= 2;
+      const bool cg = (s >= 3 || m >= 4);
       switch (I->model) {
-        case 0: batch_stage_rows<ModelNone<float>>(a, I->ell, r0, r1, has_m2); break;
-        case 1: batch_stage_rows<ModelPassive<float>>(a, I->ell, r0, r1, has_m2); break;
-        case 2: batch_stage_rows<ModelHH<float>>(a, I->ell, r0, r1, has_m2); break;
-        default: batch_stage_rows<ModelTTP06<float>>(a, I->ell, r0, r1, has_m2); break;
+        case 0: batch_stage_rows<ModelNone<float>>(a, I->ell, r0, r1, has_m2, cg); break;
+        case 1: batch_stage_rows<ModelPassive<float>>(a, I->ell, r0, r1, has_m2, cg); break;
+        case 2: batch_stage_rows<ModelHH<float>>(a, I->ell, r0, r1, has_m2, cg); break;
+        default: batch_stage_rows<ModelTTP06<float>>(a, I->ell, r0, r1, has_m2, cg); break;
       }
     } else {
       InnerArgs b;
@@ -162,7 +172,11 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) batch_step_kernel(const B
       b.f_inv_eta = I->f_inv_eta;
       b.f_okappa = I->o_kappa[j];
       b.f_omu_dt = I->o_mudt[j];
-      for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) inner_node_mixed<true>(b, I->ell, i);
+      if (s >= 3 || m >= 4) {
+        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) inner_node_mixed<true>(b, I->ell, i);
+      } else {
+        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) inner_node_mixed<false>(b, I->ell, i);
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -123,7 +123,7 @@ def test_autotune_keeps_state():
     b.sync()
     before = [b.get_state(i) for i in ids]
     tile, block, ms = b.autotune(dt, reps=2)
-    assert tile in (512, 1024, 2048, 4096) and block in (128, 256) and ms > 0
+    assert tile in (512, 1024, 2048, 4096, 8192) and block in (128, 256) and ms > 0
     after = [b.get_state(i) for i in ids]
     for x, y in zip(before, after):
         np.testing.assert_array_equal(x, y)
