@@ -130,3 +130,40 @@ def test_create_validates_arguments(lib):
     with pytest.raises(pkg.EmrkcError) as ei:
         pkg.Solver(rp, col, K, M, method=pkg.METHOD_IMEX_RL, lin_max_iter=-1)
     assert ei.value.code == 1
+
+
+def _raw_create(lib, n, rp, col, K, M):
+    import ctypes as C
+
+    from paper_2401_01745_gb300._ffi import Matrix, Tissue
+
+    mat = Matrix(n, K.size, rp.ctypes.data_as(C.POINTER(C.c_int64)), col.ctypes.data_as(C.POINTER(C.c_int32)),
+                 K.ctypes.data_as(C.POINTER(C.c_double)), M.ctypes.data_as(C.POINTER(C.c_double)))
+    h = C.c_void_p()
+    rc = lib.emrkc_create(C.byref(mat), C.byref(Tissue(1400.0, 1.0)), 2, None, None, C.byref(h))
+    return rc, lib.emrkc_last_error(None).decode()
+
+
+def test_create_edge_cases_rejected_on_host(lib):
+    """Degenerate and out-of-range matrices are rejected before any device
+    work: no nodes, a row pointer that does not end at nnz or is not
+    monotone, a non-finite entry, and more rows than int32 columns address
+    (checked before the row pointer is read)."""
+    w = make_workload("square5x5_hh")
+    rp, col, K, M = pkg.assemble_p1(w.coords, w.cells, w.D)
+    rc, msg = _raw_create(lib, 0, rp, col, K, M)
+    assert rc == 1 and "size" in msg
+    bad = rp.copy()
+    bad[-1] += 1
+    rc, msg = _raw_create(lib, w.n, bad, col, K, M)
+    assert rc == 1 and "row_ptr" in msg
+    bad = rp.copy()
+    bad[3], bad[4] = bad[4], bad[3]
+    rc, msg = _raw_create(lib, w.n, bad, col, K, M)
+    assert rc == 1
+    Kn = K.copy()
+    Kn[5] = np.nan
+    rc, msg = _raw_create(lib, w.n, rp, col, Kn, M)
+    assert rc == 1 and "non-finite" in msg
+    rc, msg = _raw_create(lib, 2 ** 31, rp, col, K, M)
+    assert rc == 1 and "rows" in msg
