@@ -186,7 +186,7 @@ def step_bytes_mixed(N, s, m, offd):
     each inner item k reads delta_{k-1} (delta_{k-2} for k >= 3, L V + F for
     m >= 4) and the row of L and writes delta_k, the last one reading g_{j-1}
     (and g_{j-2}) V hi/lo and writing V hi/lo; the last stage of the step
-    reads V_n hi for the activation test, and with s >= 2 stage 1 keeps a
+    reads V_n hi for the activation test, and with s >= 3 stage 1 keeps a
     copy of it."""
     z = (N - 1) * 4
     L = offd * 8
@@ -196,14 +196,15 @@ def step_bytes_mixed(N, s, m, offd):
         st += (4 + 8) if m == 1 else (4 + (4 if m >= 4 else 0))
         if j >= 2:
             st += z + 8
-        if j == 1 and s >= 2:
+        if j == 1 and s >= 3:
             st += 4
         total += st
         for k in range(2, m + 1):
             inn = 4 + (4 if k >= 3 else 0) + (4 if m >= 4 else 0) + L
             inn += (8 + (8 if j >= 2 else 0) + 8) if k == m else 4
             total += inn
-    return total + 4
+    # V_n hi for the activation test (for s = 2 it is g_{j-2}, already read)
+    return total + (0 if s == 2 else 4)
 
 
 def _aggregate(units, ms, world, device):

@@ -95,7 +95,9 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) batch_step_kernel(const B
     const int bm1 = (cur + j - 1) % 3, bm2 = (cur + j + 1) % 3, bo = (cur + j) % 3;
     const int64_t r0 = (int64_t)tile * c.tile;
     const int64_t r1 = (r0 + c.tile < I->n) ? r0 + c.tile : I->n;
-    float* const Vn32 = (s == 1) ? I->Vhi[cur] : I->Vn32;
+    // V_n hi for the activation test: its own buffer survives the step while
+    // s <= 2 (stage j writes buffer cur + j); a copy is kept for s >= 3
+    float* const Vn32 = (s <= 2) ? I->Vhi[cur] : I->Vn32;
     double* const act = c.dry ? nullptr : I->act;
     if (k == 1) {
       StageArgs a;
@@ -117,7 +119,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) batch_step_kernel(const B
       a.dt = I->dt;
       a.f_th = I->f_th;
       a.flags = I->flags;
-      a.Vn32_copy = (j == 1 && s >= 2) ? I->Vn32 : nullptr;
+      a.Vn32_copy = (j == 1 && s >= 3) ? I->Vn32 : nullptr;
       a.V32m1 = I->Vhi[bm1];
       a.Vlo_m1 = I->Vlo[bm1];
       a.Vhi_m2 = j >= 2 ? I->Vhi[bm2] : nullptr;

@@ -382,8 +382,9 @@ int do_step_mrkc(emrkc_solver* s, double dt) {
   const Coeffs ci = s->coeffs(Mi);
   const int b0 = s->cur;
   const int ks = s->mk.stiff_gate;
-  const double* Vn = (S == 1) ? s->d_V[b0] : s->d_Vn;
-  if (S >= 2) cudaMemcpyAsync(s->d_Vn, s->d_V[b0], s->n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
+  // V_n for the activation test: buffer b0 survives the step while S <= 2
+  const double* Vn = (S <= 2) ? s->d_V[b0] : s->d_Vn;
+  if (S >= 3) cudaMemcpyAsync(s->d_Vn, s->d_V[b0], s->n * sizeof(double), cudaMemcpyDeviceToDevice, s->stream);
   for (int j = 1; j <= S; ++j) {
     const int bm1 = (b0 + j - 1) % 3, bm2 = (b0 + j - 2 + 3) % 3, bo = (b0 + j) % 3;
     MrkcArgs a;
@@ -460,7 +461,9 @@ int do_step(emrkc_solver* s, double dt) {
   const Coeffs co = s->coeffs(S);
   const Coeffs ci = s->coeffs(Mi);
   const int b0 = s->cur;
-  const double* Vn = (S == 1) ? s->d_V[b0] : s->d_Vn;
+  // V_n for the activation test: buffer b0 survives the step while S <= 2
+  // (stage j writes buffer b0 + j); a copy is kept for S >= 3
+  const double* Vn = (S <= 2) ? s->d_V[b0] : s->d_Vn;
   for (int j = 1; j <= S; ++j) {
     const int bm1 = (b0 + j - 1) % 3, bm2 = (b0 + j - 2 + 3) % 3, bo = (b0 + j) % 3;
     StageArgs a;
@@ -492,7 +495,7 @@ int do_step(emrkc_solver* s, double dt) {
     a.dt = dt;
     a.threshold = s->opt.act_threshold;
     a.flags = s->d_flags;
-    a.Vn_copy = (j == 1 && S >= 2) ? s->d_Vn : nullptr;
+    a.Vn_copy = (j == 1 && S >= 3) ? s->d_Vn : nullptr;
     a.inv_eta = 1.0 / eta;
     a.mu1 = ci.mu[1];
     a.V32m1 = s->d_V32[bm1];
@@ -501,8 +504,8 @@ int do_step(emrkc_solver* s, double dt) {
     a.Vhi_m2 = j >= 2 ? s->d_V32[bm2] : nullptr;
     a.Vlo_m2 = j >= 2 ? s->d_Vlo[bm2] : nullptr;
     a.Vlo_out = s->d_Vlo[bo];
-    a.Vn32 = (S == 1) ? s->d_V32[b0] : s->d_Vn32;
-    a.Vn32_copy = (j == 1 && S >= 2) ? s->d_Vn32 : nullptr;
+    a.Vn32 = (S <= 2) ? s->d_V32[b0] : s->d_Vn32;
+    a.Vn32_copy = (j == 1 && S >= 3) ? s->d_Vn32 : nullptr;
     a.f_th = (float)s->opt.act_threshold;
     a.D1 = s->d_D[0];
     a.LV = (Mi >= 4) ? s->d_LV : nullptr;  // L V + F, kept for inner stages k >= 4
