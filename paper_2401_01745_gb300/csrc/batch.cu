@@ -28,9 +28,45 @@ namespace emrkc {
 // the m inner stages, so with s <= 2 and m <= 3 every buffer is written at
 // most once and only read after its write (or only read) within a launch.
 // Otherwise data produced within the launch are loaded through L2 (ld.cg).
+// Light models (at most 3 z rows): V and z of the thread's next node are
+// loaded before the current node's work, one node ahead.
+template <class Model, bool HAS_M2, bool CG>
+__device__ __forceinline__ void light_rows(const StageArgs& a, const Ell& A, int64_t r0, int64_t r1) {
+  constexpr int NZ = Model::NE + Model::NS;
+  const float* __restrict__ Zm1 = static_cast<const float*>(a.Zm1);
+  const int64_t B = blockDim.x, ld = a.ld;
+  int64_t i = r0 + threadIdx.x;
+  if (i >= r1) return;
+  float Vn = ldm<CG>(a.V32m1 + i);
+  float zn[NZ > 0 ? NZ : 1];
+#pragma unroll
+  for (int k = 0; k < NZ; ++k) zn[k] = ldm<CG>(Zm1 + k * ld + i);
+  for (; i < r1; i += B) {
+    const float V = Vn;
+    float z[NZ > 0 ? NZ : 1];
+#pragma unroll
+    for (int k = 0; k < NZ; ++k) z[k] = zn[k];
+    if (i + B < r1) {
+      Vn = ldm<CG>(a.V32m1 + i + B);
+#pragma unroll
+      for (int k = 0; k < NZ; ++k) zn[k] = ldm<CG>(Zm1 + k * ld + i + B);
+    }
+    stage_node_mixed_with<Model, HAS_M2, CG>(a, A, i, V, z);
+  }
+}
+
 template <class Model>
 __device__ __forceinline__ void batch_stage_rows(const StageArgs& a, const Ell& A, int64_t r0, int64_t r1, bool has_m2,
                                                  bool cg) {
+  if constexpr (Model::NE + Model::NS <= 3) {
+    if (has_m2) {
+      if (cg) light_rows<Model, true, true>(a, A, r0, r1);
+      else light_rows<Model, true, false>(a, A, r0, r1);
+    } else {
+      light_rows<Model, false, false>(a, A, r0, r1);
+    }
+    return;
+  }
   if (has_m2) {
     if (cg) {
       for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) stage_node_mixed<Model, true, true>(a, A, i);

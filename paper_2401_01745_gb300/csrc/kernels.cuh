@@ -227,20 +227,15 @@ __global__ void __launch_bounds__(128) stage_kernel_fp64(const StageArgs a, cons
 // exponentials and L V in FP32 (on the FP32 mirror of V); V itself is only
 // updated in FP64 (m == 1).  For m >= 2 the inner stages carry the FP32
 // increments delta_k = u_k - V_{j-1}; this kernel writes delta_1, L V and F.
-template <class Model, bool HAS_M2, bool CG = false>
-__device__ __forceinline__ void stage_node_mixed(const StageArgs& a, const Ell& A, const int64_t i) {
+// The node's work after its V and z have been loaded (by the caller, possibly
+// one node ahead).
+template <class Model, bool HAS_M2, bool CG>
+__device__ __forceinline__ void stage_node_mixed_with(const StageArgs& a, const Ell& A, const int64_t i, const float V,
+                                                      const float* z) {
   constexpr int NE = Model::NE, NS = Model::NS, NZ = NE + NS;
-  using M = Math<float>;
   const int64_t ld = a.ld;
-  const float* __restrict__ Zm1 = static_cast<const float*>(a.Zm1);
   const float* __restrict__ Zm2 = static_cast<const float*>(a.Zm2);
   float* __restrict__ Zout = static_cast<float*>(a.Zout);
-
-  const float V = ldm<CG>(a.V32m1 + i);
-  float z[NZ > 0 ? NZ : 1];
-#pragma unroll
-  for (int k = 0; k < NZ; ++k) z[k] = ldm<CG>(Zm1 + k * ld + i);
-
   float zE1[NE > 0 ? NE : 1];
   float Iion;
   float gS[NS > 0 ? NS : 1];
@@ -275,6 +270,17 @@ __device__ __forceinline__ void stage_node_mixed(const StageArgs& a, const Ell& 
     a.D1[i] = a.f_mu1eta * (LV + F);
     if (a.LV != nullptr) a.LV[i] = LV + F;  // kept for inner stages k >= 4 only
   }
+}
+
+template <class Model, bool HAS_M2, bool CG = false>
+__device__ __forceinline__ void stage_node_mixed(const StageArgs& a, const Ell& A, const int64_t i) {
+  constexpr int NZ = Model::NE + Model::NS;
+  const float* __restrict__ Zm1 = static_cast<const float*>(a.Zm1);
+  const float V = ldm<CG>(a.V32m1 + i);
+  float z[NZ > 0 ? NZ : 1];
+#pragma unroll
+  for (int k = 0; k < NZ; ++k) z[k] = ldm<CG>(Zm1 + k * a.ld + i);
+  stage_node_mixed_with<Model, HAS_M2, CG>(a, A, i, V, z);
 }
 
 template <class Model, bool HAS_M2>
