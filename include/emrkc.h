@@ -262,6 +262,16 @@ int emrkc_estimate_rho_F_noalloc(emrkc_solver* s, double* d_v, double* d_w, int6
 /* Set the time and step counter (checkpoint/resume together with set_state). */
 int emrkc_set_time(emrkc_solver* s, double t, int64_t steps);
 
+/* Replace the applied stimulus (the I_stim of Eq. monodomain, nodal as in
+ * Sec. 2.1) for the following steps: node_mask (n host bytes, nonzero =
+ * stimulated; NULL = no stimulus), amplitude in uA/cm^2, active for
+ * t_on <= t <= t_off (ms, inclusive).  Stimulation protocols (pacing trains,
+ * moving sites) change it between steps.  The mask is copied on the
+ * solver's stream before the call returns; the host buffer may be reused at
+ * once.  Errors: EMRKC_ERR_ARG (n does not match), EMRKC_ERR_CUDA. */
+int emrkc_set_stimulus(emrkc_solver* s, const uint8_t* node_mask, int64_t n, double amplitude, double t_on,
+                       double t_off);
+
 int emrkc_get_stats(emrkc_solver* s, emrkc_stats* out);
 
 /* Message of the last error on this solver, or of the last failed create

@@ -186,6 +186,15 @@ class Solver:
     def set_time(self, t, steps):
         self._check(self._lib.emrkc_set_time(self._h, t, steps))
 
+    def set_stimulus(self, mask, amplitude=50.0, t_on=0.0, t_off=1.0):
+        """Replace the applied stimulus (mask of n bytes or None) for the following steps."""
+        if mask is None:
+            ptr = None
+        else:
+            m = np.ascontiguousarray(mask, dtype=np.uint8)
+            ptr = m.ctypes.data_as(C.POINTER(C.c_uint8))
+        self._check(self._lib.emrkc_set_stimulus(self._h, ptr, self.n, amplitude, t_on, t_off))
+
     def stats(self) -> dict:
         st = Stats()
         self._check(self._lib.emrkc_get_stats(self._h, C.byref(st)))

@@ -1093,6 +1093,35 @@ int emrkc_estimate_rho(emrkc_solver* s, double* rho_F, double* rho_S, int* it_F,
   return EMRKC_OK;
 }
 
+int emrkc_set_stimulus(emrkc_solver* s, const uint8_t* node_mask, int64_t n, double amplitude, double t_on,
+                       double t_off) {
+  if (!s) return EMRKC_ERR_ARG;
+  if (n != s->n) return s->fail(EMRKC_ERR_ARG, "mask length does not match the node count");
+  if (!std::isfinite(amplitude) || std::isnan(t_on) || std::isnan(t_off))
+    return s->fail(EMRKC_ERR_ARG, "stimulus amplitude and window must be numbers");
+  cudaSetDevice(s->device);
+  if (!node_mask) {
+    // no stimulus: an empty window keeps the kernels' mask reads harmless
+    s->amp = 0.0;
+    s->t_on = 0.0;
+    s->t_off = -1.0;
+    return EMRKC_OK;
+  }
+  cudaError_t e;
+  if (!s->d_mask) {
+    if ((e = dalloc(&s->d_mask, s->ld)) != cudaSuccess) return s->fail(EMRKC_ERR_OOM, "device allocation failed");
+    if ((e = cudaMemsetAsync(s->d_mask, 0, s->ld, s->stream)) != cudaSuccess) return s->cuda_fail(e, "mask clear");
+  }
+  // synchronous with respect to the caller's buffer: it may be reused at once
+  if ((e = cudaMemcpyAsync(s->d_mask, node_mask, s->n, cudaMemcpyHostToDevice, s->stream)) != cudaSuccess)
+    return s->cuda_fail(e, "mask copy");
+  if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return s->cuda_fail(e, "mask copy");
+  s->amp = amplitude;
+  s->t_on = t_on;
+  s->t_off = t_off;
+  return EMRKC_OK;
+}
+
 int emrkc_set_time(emrkc_solver* s, double t, int64_t steps) {
   if (!s) return EMRKC_ERR_ARG;
   if (!std::isfinite(t) || steps < 0) return s->fail(EMRKC_ERR_ARG, "invalid time or step count");

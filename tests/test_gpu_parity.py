@@ -327,6 +327,49 @@ def test_mixed_vs_fp64_many_stages(fixed, m):
         assert np.max(np.abs(a64[fin] - a32[fin])) <= 0.05
 
 
+def test_stimulus_protocol_parity():
+    """emrkc_set_stimulus between steps (a second site paced after 3 ms) against
+    the oracle with the same protocol; and a solver created without stimulus
+    that receives it through set_stimulus equals one created with it."""
+    w = make_workload("square17x13_hh", h=1.0 / 32)
+    dt, steps, switch = 0.02, 300, 150
+    x, y = w.coords[:, 0], w.coords[:, 1]
+    site2 = ((x >= x.max() - 0.1) & (y >= y.max() - 0.1)).astype(np.uint8)
+    prob = Monodomain.from_workload(w)
+    ref = OracleRun(prob, rho_every=1)
+    sol = pkg.Solver.from_workload(w, precision=pkg.PREC_FP64, rho_every=1)
+    for k in range(steps):
+        if k == switch:
+            sol.set_stimulus(site2, amplitude=60.0, t_on=3.0, t_off=4.0)
+            prob.stim_mask = site2.astype(np.float64)
+            prob.stim_amp, prob.t_on, prob.t_off = 60.0, 3.0, 4.0
+        sol.step(dt)
+        ref.step(dt)
+    sol.sync()
+    Y, act = sol.get_state(), sol.activation_times()
+    sol.close()
+    assert np.isfinite(act[site2 == 1]).all()
+    _assert_parity(Y, act, prob, ref)
+    outs = []
+    rp, col, K, M = pkg.assemble_p1(w.coords, w.cells, w.D)
+    for via_set in (False, True):
+        kw = dict(chi=w.chi, Cm=w.Cm, model=w.model, precision=pkg.PREC_MIXED, rho_every=0)
+        if via_set:  # no stimulus at create: the mask is allocated by set_stimulus
+            s2 = pkg.Solver(rp, col, K, M, mask=None, **kw)
+            s2.set_stimulus(w.stim_mask, amplitude=w.stim_amp, t_on=w.t_on, t_off=w.t_off)
+        else:
+            s2 = pkg.Solver(rp, col, K, M, mask=w.stim_mask, amplitude=w.stim_amp, t_on=w.t_on, t_off=w.t_off,
+                            **kw)
+        for _ in range(100):
+            s2.step(dt)
+        s2.sync()
+        outs.append(s2.get_state())
+        s2.close()
+    for k in range(outs[0].shape[0]):
+        scale = max(np.max(np.abs(outs[0][k])), 1e-12)
+        assert np.max(np.abs(outs[0][k] - outs[1][k])) <= 1e-6 * scale
+
+
 def test_state_roundtrip_and_errors():
     w = make_workload("square9x7_ttp", h=0.01)
     sol = pkg.Solver.from_workload(w)
