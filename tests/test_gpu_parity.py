@@ -285,6 +285,36 @@ def test_full_size_slab_ttp_parity_first_steps():
     _assert_parity(Y, act, prob, ref)
 
 
+def test_full_size_shell_one_step_from_gpu_state():
+    """The ventricle-like shell at full size (4,193,408 nodes, 24.2M tetrahedra):
+    the FP64 GPU path runs 20 steps through the apical stimulus; from its state
+    the oracle (its own assembly of the same mesh) takes one step with the same
+    rho and must agree with the GPU's next step."""
+    w = make_workload("shell_ttp")
+    sol = pkg.Solver.from_workload(w, precision=pkg.PREC_FP64, rho_every=pkg.RHO_ONCE)
+    for _ in range(20):
+        sol.step(w.dt)
+    sol.sync()
+    st = sol.stats()
+    Y20 = sol.get_state()
+    sol.step(w.dt)
+    sol.sync()
+    Y21 = sol.get_state()
+    st21 = sol.stats()
+    sol.close()
+    assert np.max(Y20[0]) > -20.0  # the stimulated apex has depolarised
+    prob = Monodomain.from_workload(w)
+    ref = OracleRun(prob, Y0=Y20, fixed_rho=(st["rho_F"], st["rho_S"]))
+    ref.t = 20 * w.dt
+    s_ref, m_ref = ref.step(w.dt)
+    assert (s_ref, m_ref) == (st21["s"], st21["m"])
+    err = prob.l2_norm(Y21[0] - ref.Y[0]) / prob.l2_norm(ref.Y[0])
+    assert err <= 1e-10, f"rel L2 error in V {err:.3e}"
+    for k in range(1, prob.N):
+        scale = max(np.max(np.abs(ref.Y[k])), 1e-12)
+        assert np.max(np.abs(Y21[k] - ref.Y[k])) / scale <= 1e-9, f"variable {k}"
+
+
 @pytest.mark.parametrize("name,dt,steps,h,amp_scale", [
     ("slab41x15x7_ttp", 0.05, 300, 0.01, 1.0),
     ("square33x33_hh", 0.02, 300, 1.0 / 64, 1.0),
