@@ -139,7 +139,11 @@ typedef struct {
   void* cuda_stream;  /* cudaStream_t to order work on, or NULL            */
   int device;         /* CUDA device ordinal                                */
   int profile;        /* 1: time every kernel class with CUDA events        */
-  int use_graphs;     /* 1: replay each fixed (s, m) step as a CUDA graph  */
+  int use_graphs;     /* batch API: 1 = replay each step's persistent launch
+                         as a CUDA graph (re-captured when the plan
+                         changes).  The single-instance solver launches its
+                         step kernels directly, chained by programmatic
+                         dependent launch; the option has no effect there */
   double rho_S_min;   /* known bound on rho(f_S): the step uses
                          max(safety * estimate, rho_S_min) (Sec. 3.1: rho is
                          known or estimated); 0 = estimate only            */
@@ -179,7 +183,8 @@ typedef struct {
 } emrkc_stats;
 
 /* Fill *opt with the defaults listed above (FP64, rho every step, seed 0,
- * threshold -20 mV, NULL stream, device 0, no profiling, graphs on). */
+ * threshold -20 mV, NULL stream, device 0, no profiling, graphs on,
+ * rho_S_min 0, method EMRKC_METHOD_EMRKC, lin_rtol 1e-10, lin_max_iter 1000). */
 int emrkc_default_options(emrkc_options* opt);
 
 /* Number of state variables N (V included) of an ionic model, or -1. */

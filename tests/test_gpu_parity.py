@@ -285,6 +285,28 @@ def test_full_size_slab_ttp_parity_first_steps():
     _assert_parity(Y, act, prob, ref)
 
 
+def test_full_size_slab_mixed_vs_fp64():
+    """The headline configuration (442,401-node slab, rho once at t = 0, the
+    benchmark's launch configuration) over T = 20 ms: the mixed path within
+    1e-3 relative L2 in V and 0.05 ms in activation times of the FP64 path."""
+    w = make_workload("slab_ttp")
+    out = {}
+    for prec in (pkg.PREC_FP64, pkg.PREC_MIXED):
+        sol = pkg.Solver.from_workload(w, precision=prec, rho_every=0)
+        for _ in range(400):
+            sol.step(w.dt)
+        sol.sync()
+        out[prec] = (sol.get_state(var=0), sol.activation_times())
+        sol.close()
+    (V64, a64), (V32, a32) = out[pkg.PREC_FP64], out[pkg.PREC_MIXED]
+    prob_M = pkg.assemble_p1(w.coords, w.cells, w.D)[3]
+    err = np.sqrt(prob_M @ (V32 - V64) ** 2) / np.sqrt(prob_M @ (V64 * V64))
+    assert err <= 1e-3, f"mixed vs FP64 rel L2 error in V {err:.3e}"
+    fin = np.isfinite(a64)
+    assert fin.sum() > 1000 and np.array_equal(fin, np.isfinite(a32))
+    assert np.max(np.abs(a64[fin] - a32[fin])) <= 0.05
+
+
 def test_full_size_shell_one_step_from_gpu_state():
     """The ventricle-like shell at full size (4,193,408 nodes, 24.2M tetrahedra):
     the FP64 GPU path runs 20 steps through the apical stimulus; from its state
