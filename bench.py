@@ -528,6 +528,13 @@ def run_compare(args):
     spmv_ms = se["phase_ms"]["inner"] / n_inner
     fF_est = se["s"] * se["m"] * spmv_ms
     cg_ms = si["phase_ms"]["inner"] / Hi
+    # CG iteration bytes per node (FP64): q = B p with p = z + beta p gathered
+    # (z, p, M, the row of L with its diagonal: 12 B per stored entry; p, q
+    # out), then x, r, z updated (p, x, r, q, P^-1, M in; x, r, z out)
+    ell_entries = si["matrix_entries"] / w.n
+    cg_bytes = 8 * 3 + 12 * ell_entries + 16 + 8 * 6 + 8 * 3
+    iters = max(si["total_lin_iters"], 1)
+    cg_gbs = cg_bytes * w.n * iters / (si["phase_ms"]["inner"] / 1e3) / 1e9
     wedge = {"dt": dtw, "emrkc_s_m": [se["s"], se["m"]],
              "emrkc_ms_per_inner_spmv_stage": spmv_ms,
              "emrkc_fF_ms_per_step_estimate": fF_est,
@@ -536,6 +543,8 @@ def run_compare(args):
              "imex_cg_iters_per_step": si["total_lin_iters"] / Hi,
              "imex_ionic_setup_ms_per_step": si["phase_ms"]["stage"] / Hi,
              "ratio_imex_solve_to_emrkc_fF": cg_ms / fF_est if fF_est > 0 else None,
+             "imex_cg_bytes_per_node_per_iteration": cg_bytes,
+             "imex_cg_achieved_gbs": cg_gbs, "imex_cg_frac_of_hbm": cg_gbs / _peaks()[0],
              "note": ("emRKC f_F per step estimated as s * m inner-SpMV-stage times (the first evaluation of each "
                       "outer stage is fused into the stage kernel)")}
     best = {}
@@ -675,6 +684,60 @@ def run_latency(args):
     return 0
 
 
+def run_fibrosis(args):
+    """Fibrosis robustness workload (Sec. 5.4 with fibrosis): the 201 x 71 x 31
+    slab with sigma_t = 0 on the cells where a seeded smooth random field
+    exceeds its median; mixed vs FP64 throughput and error over T = 20 ms."""
+    import torch
+
+    import paper_2401_01745_gb300 as pkg
+    from workloads import make_workload
+
+    world, rank, local = _dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pkg.build()
+    w = make_workload("fibslab201x71x31_ttp", h=0.01)
+    rp, col, K, M = pkg.assemble_p1(w.coords, w.cells, w.D)
+    stream = torch.cuda.Stream(device=dev)
+    H = int(round(20.0 / w.dt))
+    res = {}
+    with ClockSampler(local) as clk:
+        for name, prec in (("mixed", pkg.PREC_MIXED), ("fp64", pkg.PREC_FP64)):
+            sol = pkg.Solver(rp, col, K, M, chi=w.chi, Cm=w.Cm, model=w.model, mask=w.stim_mask,
+                             amplitude=w.stim_amp, t_on=w.t_on, t_off=w.t_off, precision=prec, rho_every=0,
+                             stream=stream.cuda_stream, device=local)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                for _ in range(H):
+                    sol.step(w.dt)
+                e1.record(stream)
+            sol.sync()
+            st = sol.stats()
+            res[name] = dict(ms=e0.elapsed_time(e1), V=sol.get_state(var=0), act=sol.activation_times(),
+                             s=st["s"], m=st["m"], rho_F=st["rho_F"])
+            sol.close()
+    Va, Vb = res["fp64"]["V"], res["mixed"]["V"]
+    ta, tb = res["fp64"]["act"], res["mixed"]["act"]
+    both = np.isfinite(ta) & np.isfinite(tb)
+    out = {"metric": METRIC, "value": w.n * H / (res["mixed"]["ms"] / 1e3), "unit": UNIT, "n_gpus": 1,
+           "steps": H, "ms_per_step": res["mixed"]["ms"] / H, "higher_is_better": True, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": "fibrosis slab: 201x71x31 Kuhn-tet slab, fibres along x (1.33/0.18 mS/cm), "
+                                  "sigma_t = 0 above the median of a seeded smooth field (corr. length 0.05 cm), "
+                                  "TTP06, dt 0.05 ms, T 20 ms, rho once at t = 0 (timed)", "nodes": w.n,
+                      "fibrotic_cells": float(w.extra["fibrotic_cells"].mean()),
+                      "s": res["mixed"]["s"], "m": res["mixed"]["m"], "rho_F": res["mixed"]["rho_F"]},
+           "fp64": {"value": w.n * H / (res["fp64"]["ms"] / 1e3), "ms_per_step": res["fp64"]["ms"] / H},
+           "accuracy": {"rel_l2_err_V_vs_fp64": float(np.sqrt(np.sum(M * (Va - Vb) ** 2) / np.sum(M * Va * Va))),
+                        "max_activation_diff_ms": float(np.max(np.abs(ta[both] - tb[both]))) if both.any() else None,
+                        "activated_nodes": int(both.sum())},
+           "clocks": clk.summary()}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -703,6 +766,7 @@ def main():
     ap.add_argument("--lin-rtol", type=float, default=1e-8)
     ap.add_argument("--stability", action="store_true", help="Sec. 5.1 practical-stability sweep on the 1-D cable")
     ap.add_argument("--latency", action="store_true", help="65x65 HH square, rho every step, us/step")
+    ap.add_argument("--fibrosis", action="store_true", help="fibrosis slab: mixed vs FP64 over T = 20 ms")
     ap.add_argument("--stability-dts", type=float, nargs="+",
                     default=[0.05, 0.1, 0.25, 0.5, 1.0, 2.0, 3.0, 4.0, 4.5, 5.0, 6.0, 8.0])
     args = ap.parse_args()
@@ -718,6 +782,8 @@ def main():
         return run_stability(args)
     if args.latency:
         return run_latency(args)
+    if args.fibrosis:
+        return run_fibrosis(args)
     if args.served:
         return run_served(args)
     if args.batched:
