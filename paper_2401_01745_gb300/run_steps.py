@@ -30,21 +30,27 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=6)
     ap.add_argument("--rho-every", type=int, default=0)
     ap.add_argument("--h", type=float, default=None, help="mesh size for parametrised workload names")
+    ap.add_argument("--method", default="emrkc", choices=["emrkc", "exex", "imex", "mrkc"])
+    ap.add_argument("--dt", type=float, default=None)
     a = ap.parse_args(argv)
     pkg.build()
     kw = {} if a.h is None else {"h": a.h}
     w = make_workload(a.workload, **kw)
     prec = pkg.PREC_MIXED if a.precision == "mixed" else pkg.PREC_FP64
-    sol = pkg.Solver.from_workload(w, precision=prec, rho_every=a.rho_every)
+    method = {"emrkc": pkg.METHOD_EMRKC, "exex": pkg.METHOD_EXEX_RL, "imex": pkg.METHOD_IMEX_RL,
+              "mrkc": pkg.METHOD_MRKC}[a.method]
+    dt = w.dt if a.dt is None else a.dt
+    sol = pkg.Solver.from_workload(w, precision=prec, rho_every=a.rho_every, method=method)
     t0 = time.perf_counter()
     for _ in range(a.steps):
-        sol.step(w.dt)
+        sol.step(dt)
     sol.sync()
     el = time.perf_counter() - t0
     st = sol.stats()
     V = sol.get_state(var=0)
     sol.close()
-    print(json.dumps({"workload": a.workload, "nodes": w.n, "precision": a.precision, "steps": a.steps,
+    print(json.dumps({"workload": a.workload, "nodes": w.n, "precision": a.precision, "method": a.method,
+                      "steps": a.steps,
                       "s": st["s"], "m": st["m"], "launches": st["launches"], "wall_s": el,
                       "V_min": float(V.min()), "V_max": float(V.max())}))
     return 0
