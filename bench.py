@@ -857,8 +857,11 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec == pkg.PREC_MIXED else "f64", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: 201x71x31-node Kuhn-tet slab 2.0x0.7x0.3 cm, TTP06 epi, "
-                               "dt 0.05 ms, 50 uA/cm^2 corner stimulus; timed from rest (t = 0)",
+        "config": {"workload": (f"{args.workload}: 201x71x31-node Kuhn-tet slab 2.0x0.7x0.3 cm, TTP06 epi, "
+                                "dt 0.05 ms, 50 uA/cm^2 corner stimulus; timed from rest (t = 0)"
+                                if args.workload == "slab_ttp" else
+                                f"{args.workload}: {w.n}-node synthetic mesh, dt {w.dt} ms, corner stimulus; "
+                                "timed from rest (t = 0)"),
                    "nodes": w.n, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "precision": ("mixed: FP32 z, ionic model, gating, SpMV, inner increments; FP64 V "
                                  "recurrence, stage coefficients, rho" if prec == pkg.PREC_MIXED else "fp64"),

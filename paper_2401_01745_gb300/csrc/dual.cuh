@@ -41,6 +41,7 @@ template <> struct Math<Dual> {
     return Dual(r, 0.5f * x.d / r);
   }
   static __device__ __forceinline__ Dual dv(Dual a, Dual b) { return a / b; }
+  static __device__ __forceinline__ Dual ex_aff(Dual x, double c, double s) { return ex((x - Dual(c)) * Dual(s)); }
   // g(x) = x / (e^x - 1), g'(x) = (e^x - 1 - x e^x) / (e^x - 1)^2 (-1/2 + x/6 near 0)
   static __device__ __forceinline__ Dual x_em1(Dual x) {
     const float g = Math<float>::x_em1(x.v);

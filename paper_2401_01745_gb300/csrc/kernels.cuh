@@ -60,13 +60,11 @@ __device__ __forceinline__ float ell_diff32(const Ell& A, int64_t i, const float
 // issues every column, value and neighbour load of the row up front (into
 // registers), ell_reduce sums them later, so the loads can be in flight
 // while the caller does other work (the ionic model).  Same sum, same order.
-template <int W, bool CG = false>
-__device__ __forceinline__ int ell_gather(const Ell& A, int64_t i, const float* __restrict__ x, float (&xv)[W],
-                                          float (&lv)[W]) {
+template <int W>
+__device__ __forceinline__ int ell_row(const Ell& A, int64_t i, int32_t (&c)[W], float (&lv)[W]) {
   const int64_t b = i >> 5;
   const int w = __ldg(A.width + b);
   const int64_t p = __ldg(A.slice_ptr + b) + (i & 31);
-  int32_t c[W];
 #pragma unroll
   for (int k = 0; k < W; ++k) {
     if (k < w) {
@@ -74,9 +72,23 @@ __device__ __forceinline__ int ell_gather(const Ell& A, int64_t i, const float* 
       lv[k] = __ldg(A.val32 + p + 32 * k);
     }
   }
+  return w;
+}
+
+template <int W, bool CG = false>
+__device__ __forceinline__ void ell_gather_x(const int32_t (&c)[W], int w, const float* __restrict__ x,
+                                             float (&xv)[W]) {
 #pragma unroll
   for (int k = 0; k < W; ++k)
     if (k < w) xv[k] = ldm<CG>(x + c[k]);
+}
+
+template <int W, bool CG = false>
+__device__ __forceinline__ int ell_gather(const Ell& A, int64_t i, const float* __restrict__ x, float (&xv)[W],
+                                          float (&lv)[W]) {
+  int32_t c[W];
+  const int w = ell_row<W>(A, i, c, lv);
+  ell_gather_x<W, CG>(c, w, x, xv);
   return w;
 }
 
@@ -150,16 +162,21 @@ __device__ __forceinline__ void step_epilogue_ff(int64_t i, float Vn, float Vnew
 }
 
 // Exponential step (Algorithm 3, Exponential_Euler) and f_S at one node,
-// mixed path (FP32).
+// mixed path (FP32).  dz receives the gate increments y_E - y =
+// (e^{eta Lambda} - 1)(z - z_inf); f_S is evaluated at the gates y_E = z + dz.
 template <class Model>
-__device__ __forceinline__ void ionic_mixed(float eta, float V, const float* z, float* zE1, float& Iion, float* gS) {
+__device__ __forceinline__ void ionic_mixed(float eta, float V, const float* z, float* dz, float& Iion, float* gS) {
   constexpr int NE = Model::NE;
   using M = Math<float>;
+  float zE1[NE > 0 ? NE : 1];
   if constexpr (NE > 0) {
     float lam[NE], zinf[NE];
     Model::gating(V, z, z + NE, lam, zinf);
 #pragma unroll
-    for (int k = 0; k < NE; ++k) zE1[k] = z[k] + M::em1(eta * lam[k]) * (z[k] - zinf[k]);
+    for (int k = 0; k < NE; ++k) {
+      dz[k] = M::em1(eta * lam[k]) * (z[k] - zinf[k]);
+      zE1[k] = z[k] + dz[k];
+    }
   }
   Model::currents(V, zE1, z + NE, Iion, gS);
 }
@@ -236,20 +253,22 @@ __device__ __forceinline__ void stage_node_mixed_with(const StageArgs& a, const 
   const int64_t ld = a.ld;
   const float* __restrict__ Zm2 = static_cast<const float*>(a.Zm2);
   float* __restrict__ Zout = static_cast<float*>(a.Zout);
-  float zE1[NE > 0 ? NE : 1];
+  float dz[NE > 0 ? NE : 1];
   float Iion;
   float gS[NS > 0 ? NS : 1];
-  ionic_mixed<Model>(a.f_eta, V, z, zE1, Iion, gS);
+  ionic_mixed<Model>(a.f_eta, V, z, dz, Iion, gS);
+  const float mudt_eta = a.f_mudt * a.f_inv_eta;
   const float Istim = (a.mask != nullptr && a.mask[i]) ? a.f_stim : 0.0f;
   const float F = (Istim - Iion) * a.f_inv_Cm;
 
   if constexpr (NZ > 0) {
 #pragma unroll
     for (int k = 0; k < NZ; ++k) {
-      const float fbar = (k < NE) ? (zE1[k < NE ? k : 0] - z[k]) * a.f_inv_eta : a.f_cm * gS[k >= NE ? k - NE : 0];
+      // mu dt f_bar: f_bar = (y_E - y) / eta on the gates, c_m g_S on z_S
+      const float mfbar = (k < NE) ? mudt_eta * dz[k < NE ? k : 0] : a.f_mudt * (a.f_cm * gS[k >= NE ? k - NE : 0]);
       float out;
-      if constexpr (HAS_M2) out = a.f_nu * z[k] + a.f_kappa * ldm<CG>(Zm2 + k * ld + i) + a.f_mudt * fbar;
-      else out = z[k] + a.f_mudt * fbar;
+      if constexpr (HAS_M2) out = a.f_nu * z[k] + a.f_kappa * ldm<CG>(Zm2 + k * ld + i) + mfbar;
+      else out = z[k] + mfbar;
       Zout[k * ld + i] = out;
     }
   }
@@ -322,6 +341,11 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
+// add to the expected transaction bytes of the current phase without arriving
+__device__ __forceinline__ void mbar_expect_tx_only(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
   unsigned ok;
   asm volatile(
@@ -351,6 +375,10 @@ __host__ __device__ constexpr int tma_fixed_bytes(int nz) {
 __host__ __device__ constexpr int tma_stage_bytes(int nz, int wmax) {
   return tma_fixed_bytes(nz) + (wmax <= kTmaStageEllWidth ? 2 * 4 * wmax * 32 * 4 : 0);
 }
+// one stage buffer, with the ELL slices staged (ell != 0) or read from global
+__host__ __device__ constexpr int tma_smem_bytes(int nz, int wmax, int ell) {
+  return ell ? tma_stage_bytes(nz, wmax) : tma_fixed_bytes(nz);
+}
 
 // One node of an outer stage (mixed path) from a shared-memory stage buffer
 // holding the tile's z rows, V hi and stimulus mask (kTmaTile entries each):
@@ -366,10 +394,11 @@ __device__ __forceinline__ void stage_node_staged(const StageArgs& a, const Ell&
   for (int k = 0; k < NZ; ++k) z[k] = sz[k * kTmaTile + tid];
   const float V = sz[NZ * kTmaTile + tid];
   const unsigned char mk = reinterpret_cast<const unsigned char*>(sz + (NZ + 1) * kTmaTile)[tid];
-  float zE1[NE > 0 ? NE : 1];
+  float dz[NE > 0 ? NE : 1];
   float Iion;
   float gS[NS > 0 ? NS : 1];
-  ionic_mixed<Model>(a.f_eta, V, z, zE1, Iion, gS);
+  ionic_mixed<Model>(a.f_eta, V, z, dz, Iion, gS);
+  const float mudt_eta = a.f_mudt * a.f_inv_eta;
   const float Istim = mk ? a.f_stim : 0.0f;
   const float F = (Istim - Iion) * a.f_inv_Cm;
   float* __restrict__ Zout = static_cast<float*>(a.Zout);
@@ -378,10 +407,11 @@ __device__ __forceinline__ void stage_node_staged(const StageArgs& a, const Ell&
   if constexpr (NZ > 0) {
 #pragma unroll
     for (int k = 0; k < NZ; ++k) {
-      const float fbar = (k < NE) ? (zE1[k < NE ? k : 0] - z[k]) * a.f_inv_eta : a.f_cm * gS[k >= NE ? k - NE : 0];
+      // mu dt f_bar: f_bar = (y_E - y) / eta on the gates, c_m g_S on z_S
+      const float mfbar = (k < NE) ? mudt_eta * dz[k < NE ? k : 0] : a.f_mudt * (a.f_cm * gS[k >= NE ? k - NE : 0]);
       float out;
-      if constexpr (HAS_M2) out = a.f_nu * z[k] + a.f_kappa * __ldg(Zm2 + k * ld + i) + a.f_mudt * fbar;
-      else out = z[k] + a.f_mudt * fbar;
+      if constexpr (HAS_M2) out = a.f_nu * z[k] + a.f_kappa * __ldg(Zm2 + k * ld + i) + mfbar;
+      else out = z[k] + mfbar;
       Zout[k * ld + i] = out;
     }
   }
@@ -414,8 +444,9 @@ template <class Model, bool HAS_M2>
 __global__ void __launch_bounds__(kTmaTile) stage_kernel_mixed_tma(const StageArgs a, const Ell A) {
   constexpr int NE = Model::NE, NS = Model::NS, NZ = NE + NS;
   constexpr int FB = tma_fixed_bytes(NZ);
-  const int SB = tma_stage_bytes(NZ, a.ell_wmax);
-  const bool stage_ell = a.ell_wmax <= kTmaStageEllWidth;
+  const bool stage_ell = a.tma_ell && a.ell_wmax <= kTmaStageEllWidth;
+  const int SB = stage_ell ? tma_stage_bytes(NZ, a.ell_wmax) : FB;
+  const int nb = a.tma_nbuf;  // stage buffers per CTA: 1 or 2
   const int64_t nslices = A.n_slices;
   extern __shared__ __align__(128) unsigned char tma_smem[];
   __shared__ __align__(8) unsigned long long bars[2];
@@ -426,25 +457,33 @@ __global__ void __launch_bounds__(kTmaTile) stage_kernel_mixed_tma(const StageAr
   const unsigned bar0 = smem_u32(&bars[0]), bar1 = smem_u32(&bars[1]);
   const unsigned stage_base = smem_u32(tma_smem);
 
-  auto issue = [&](int64_t tile, int buf) {
+  // A tile's copies in two parts on the buffer's barrier: the ELL slices (L is
+  // constant, so this part may be issued before the predecessor kernel has
+  // finished) and the state (z rows, V hi, mask), whose arrival closes the phase.
+  auto issue_ell = [&](int64_t tile, int buf) {
+    if (!stage_ell) return;
     const unsigned bar = buf ? bar1 : bar0;
     const unsigned dst = stage_base + buf * SB;
-    const int64_t off = tile * kTmaTile;
     const int64_t s0 = tile * (kTmaTile / 32);
     const int64_t s1 = (s0 + kTmaTile / 32 < nslices) ? s0 + kTmaTile / 32 : nslices;
     const int64_t e0 = __ldg(A.slice_ptr + s0), e1 = __ldg(A.slice_ptr + s1);
-    const unsigned ell_bytes = stage_ell ? (unsigned)((e1 - e0) * 4) : 0u;
-    mbar_expect_tx(bar, (unsigned)FB + 2u * ell_bytes);
+    const unsigned ell_bytes = (unsigned)((e1 - e0) * 4);
+    if (ell_bytes == 0) return;
+    const unsigned half = (unsigned)(4 * a.ell_wmax * 32 * 4);
+    mbar_expect_tx_only(bar, 2u * ell_bytes);
+    bulk_g2s(dst + FB, A.col + e0, ell_bytes, bar);
+    bulk_g2s(dst + FB + half, A.val32 + e0, ell_bytes, bar);
+  };
+  auto issue_state = [&](int64_t tile, int buf) {
+    const unsigned bar = buf ? bar1 : bar0;
+    const unsigned dst = stage_base + buf * SB;
+    const int64_t off = tile * kTmaTile;
+    mbar_expect_tx(bar, (unsigned)FB);
     const float* Zm1 = static_cast<const float*>(a.Zm1);
 #pragma unroll 1
     for (int k = 0; k < NZ; ++k) bulk_g2s(dst + k * kTmaTile * 4, Zm1 + k * a.ld + off, kTmaTile * 4, bar);
     bulk_g2s(dst + NZ * kTmaTile * 4, a.V32m1 + off, kTmaTile * 4, bar);
     bulk_g2s(dst + (NZ + 1) * kTmaTile * 4, a.mask + off, kTmaTile, bar);
-    if (stage_ell && ell_bytes > 0) {
-      const unsigned half = (unsigned)(4 * a.ell_wmax * 32 * 4);
-      bulk_g2s(dst + FB, A.col + e0, ell_bytes, bar);
-      bulk_g2s(dst + FB + half, A.val32 + e0, ell_bytes, bar);
-    }
   };
 
   if (tid == 0) {
@@ -455,21 +494,24 @@ __global__ void __launch_bounds__(kTmaTile) stage_kernel_mixed_tma(const StageAr
   }
   __syncthreads();
   pdl_trigger();
-  pdl_wait();
-  if (a.mask == nullptr) {
-    // the stage copies the mask with the rest: a solver without stimulus has no
-    // mask array, so this variant is only launched with one
-    return;
-  }
+  // the stage copies the mask with the rest: a solver without stimulus has no
+  // mask array, so this variant is only launched with one
+  const bool run = a.mask != nullptr;
   const int64_t first = blockIdx.x;
+  if (tid == 0 && run) {
+    if (first < ntiles) issue_ell(first, 0);
+    if (nb == 2 && first + G < ntiles) issue_ell(first + G, 1);
+  }
+  pdl_wait();
+  if (!run) return;
   if (tid == 0) {
-    if (first < ntiles) issue(first, 0);
-    if (first + G < ntiles) issue(first + G, 1);
+    if (first < ntiles) issue_state(first, 0);
+    if (nb == 2 && first + G < ntiles) issue_state(first + G, 1);
   }
   unsigned phase[2] = {0u, 0u};
   int it = 0;
   for (int64_t tile = first; tile < ntiles; tile += G, ++it) {
-    const int buf = it & 1;
+    const int buf = (nb == 2) ? (it & 1) : 0;
     const unsigned bar = buf ? bar1 : bar0;
     long long spins = 0;
     bool ok = true;
@@ -498,15 +540,16 @@ __global__ void __launch_bounds__(kTmaTile) stage_kernel_mixed_tma(const StageAr
       stage_node_staged<Model, HAS_M2>(a, A, i, tid, sz, scol, sval, base);
     }
     __syncthreads();  // every thread is done with this stage buffer
-    if (tid == 0 && tile + 2 * G < ntiles) {
+    if (tid == 0 && tile + nb * G < ntiles) {
       fence_proxy_async();
-      issue(tile + 2 * G, buf);
+      issue_ell(tile + nb * G, buf);
+      issue_state(tile + nb * G, buf);
     }
   }
   // on abort: give copies already in flight a bounded chance to land (a
   // buffer whose wait gave up, and the other one if its tile was issued)
   if (s_abort && tid == 0) {
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < nb; ++b) {
       long long spins = 0;
       while (!mbar_try_wait(b ? bar1 : bar0, phase[b]) && ++spins < kTmaSpinLimit) {
       }
@@ -577,11 +620,13 @@ static __global__ void __launch_bounds__(256) inner_kernel_mixed(const InnerArgs
   inner_node_mixed<false>(a, A, i);
 }
 
-// Same stage with the row's loads issued up front (rows of at most W entries).
+// Same stage with the row's loads issued up front (rows of at most W entries);
+// c, lv, w: the row of L, already loaded (ell_row).
 template <int W, bool CG = false>
-__device__ __forceinline__ void inner_node_mixed_w(const InnerArgs& a, const Ell& A, const int64_t i) {
-  float xv[W], lv[W];
-  const int w = ell_gather<W, CG>(A, i, a.d1, xv, lv);
+__device__ __forceinline__ void inner_node_mixed_row(const InnerArgs& a, const int64_t i, const int32_t (&c)[W],
+                                                     const float (&lv)[W], const int w) {
+  float xv[W];
+  ell_gather_x<W, CG>(c, w, a.d1, xv);
   const float d1 = ldm<CG>(a.d1 + i);
   const float d2 = (a.d2 != nullptr) ? ldm<CG>(a.d2 + i) : 0.0f;
   const float LF = inner_lf<CG>(a, i, d1, d2);
@@ -611,12 +656,16 @@ __device__ __forceinline__ void inner_node_mixed_w(const InnerArgs& a, const Ell
 }
 
 template <int W>
-__global__ void __launch_bounds__(256) inner_kernel_mixed_w(const InnerArgs a, const Ell A) {
+__global__ void __launch_bounds__(256, 8) inner_kernel_mixed_w(const InnerArgs a, const Ell A) {
   pdl_trigger();
-  pdl_wait();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // L is constant: load the row while the kernel that writes delta_1 drains
+  int32_t c[W];
+  float lv[W];
+  const int w = (i < a.n) ? ell_row<W>(A, i, c, lv) : 0;
+  pdl_wait();
   if (i >= a.n) return;
-  inner_node_mixed_w<W, false>(a, A, i);
+  inner_node_mixed_row<W, false>(a, i, c, lv, w);
 }
 
 // ---------------------------------------------------------------------------
@@ -1085,9 +1134,9 @@ struct Kernels {
     if constexpr (MIXED) {
       const bool pdl = a.pdl != 0;
       if (a.mask != nullptr && a.tma_grid > 0) {
-        const int SB = tma_stage_bytes(MR::NE + MR::NS, a.ell_wmax);
-        if (has_m2) launch_k(pdl, stage_kernel_mixed_tma<MR, true>, a.tma_grid, kTmaTile, 2 * SB, st, a, A);
-        else launch_k(pdl, stage_kernel_mixed_tma<MR, false>, a.tma_grid, kTmaTile, 2 * SB, st, a, A);
+        const int smem = a.tma_nbuf * tma_smem_bytes(MR::NE + MR::NS, a.ell_wmax, a.tma_ell);
+        if (has_m2) launch_k(pdl, stage_kernel_mixed_tma<MR, true>, a.tma_grid, kTmaTile, smem, st, a, A);
+        else launch_k(pdl, stage_kernel_mixed_tma<MR, false>, a.tma_grid, kTmaTile, smem, st, a, A);
       } else if (has_m2) {
         launch_k(pdl, stage_kernel_mixed<MR, true>, g, 128, 0, st, a, A);
       } else {
@@ -1145,15 +1194,15 @@ struct Kernels {
     convert_kernel<Z><<<g, 256, 0, st>>>(count, src, dst, to_double);
   }
   // CTAs of the persistent bulk-copy stage kernel: all SMs x resident CTAs
-  static int tma_grid(int device, int wmax) {
+  static int tma_grid(int device, int wmax, int nbuf, int ell) {
     if constexpr (!MIXED) {
       return 0;
     } else {
-      const int SB = tma_stage_bytes(MR::NE + MR::NS, wmax);
+      const int smem = nbuf * tma_smem_bytes(MR::NE + MR::NS, wmax, ell);
       int per_sm = 0, sms = 0;
-      cudaFuncSetAttribute(stage_kernel_mixed_tma<MR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * SB);
-      cudaFuncSetAttribute(stage_kernel_mixed_tma<MR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * SB);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel_mixed_tma<MR, false>, kTmaTile, 2 * SB);
+      cudaFuncSetAttribute(stage_kernel_mixed_tma<MR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      cudaFuncSetAttribute(stage_kernel_mixed_tma<MR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel_mixed_tma<MR, false>, kTmaTile, smem);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
       return per_sm * sms;
     }

@@ -79,6 +79,8 @@ struct StageArgs {
   float* Vn32_copy = nullptr;   // store hi of V_n (first stage when s >= 2)
   float f_th = -20;
   int tma_grid = 0;             // > 0: persistent bulk-copy variant with this grid
+  int tma_nbuf = 1;             // stage buffers per CTA of the bulk-copy variant (1 or 2)
+  int tma_ell = 1;              // bulk-copy variant stages the tile's ELL slices (1) or reads them (0)
   int pdl = 0;                  // 1: programmatic dependent launch
   int ell_wmax = 1 << 30;       // widest sliced-ELL slice (selects unrolled row variants)
 };
@@ -183,7 +185,7 @@ struct KernelSet {
   void (*state_sumsq)(int64_t n, int64_t ld, int nz, const double* V, const void* Z,
                       const ReduceScratch&, int slot, cudaStream_t) = nullptr;
   void (*convert_z)(int64_t count, const void* src, double* dst, int to_double, cudaStream_t) = nullptr;
-  int (*tma_grid)(int device, int wmax) = nullptr;  // grid of the persistent stage kernel (0: not used)
+  int (*tma_grid)(int device, int wmax, int nbuf, int ell) = nullptr;  // grid of the persistent stage kernel (0: not used)
   cudaError_t (*power_fused)(const PowerFusedArgs&, const Ell&, int grid, cudaStream_t) = nullptr;
   int (*power_fused_grid)(int device) = nullptr;
 };

@@ -28,6 +28,8 @@ template <> struct Math<double> {
   static __device__ __forceinline__ double ln(double x) { return log(x); }
   static __device__ __forceinline__ double sq(double x) { return sqrt(x); }
   static __device__ __forceinline__ double dv(double a, double b) { return a / b; }
+  // e^{s (x - c)} for constants c, s, evaluated as written
+  static __device__ __forceinline__ double ex_aff(double x, double c, double s) { return exp((x - c) * s); }
   // x / (e^x - 1) with the removable singularity at 0 (1 - x/2 for |x| < 1e-7)
   static __device__ __forceinline__ double x_em1(double x) {
     return fabs(x) < 1e-7 ? 1.0 - 0.5 * x : x / expm1(x);
@@ -45,6 +47,15 @@ template <> struct Math<float> {
   static __device__ __forceinline__ float ln(float x) { return __logf(x); }
   static __device__ __forceinline__ float sq(float x) { return sqrtf(x); }
   static __device__ __forceinline__ float dv(float a, float b) { return __fdividef(a, b); }
+  // e^{s (x - c)} for constants c, s as 2^(x s log2(e) - c s log2(e)): one
+  // fused multiply-add with constants folded at compile time and the hardware
+  // base-2 exponential (ex2.approx, relative error ~2^-22)
+  static __device__ __forceinline__ float ex_aff(float x, double c, double s) {
+    constexpr double kLog2e = 1.4426950408889634074;
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(fmaf(x, (float)(s * kLog2e), (float)(-c * s * kLog2e))));
+    return r;
+  }
   static __device__ __forceinline__ float x_em1(float x) {
     return fabsf(x) < 1e-4f ? 1.0f - 0.5f * x : __fdividef(x, em1(x));
   }
@@ -124,69 +135,71 @@ template <typename R> struct ModelTTP06 {
   static constexpr double Ko = 5.4, Nao = 140.0, Cao = 2.0;
 
   static __device__ __forceinline__ R sig(R x) { return R(1) / (R(1) + M::ex(x)); }
+  // 1 / (1 + e^{s (V - c)})
+  static __device__ __forceinline__ R sg(R V, double c, double s) { return R(1) / (R(1) + M::ex_aff(V, c, s)); }
 
   static __device__ __forceinline__ void gating(R V, const R*, const R* zS, R* lam, R* zinf) {
     const R CaSS = zS[5];
     // I_Na gates
     {
-      const R s = sig((R(-56.86) - V) * R(1.0 / 9.03));
+      const R s = sg(V, -56.86, -(1.0 / 9.03));
       zinf[0] = s * s;
-      const R am = sig((R(-60.0) - V) * R(1.0 / 5.0));
-      const R bm = R(0.1) * sig((V + R(35.0)) * R(1.0 / 5.0)) + R(0.10) * sig((V - R(50.0)) * R(1.0 / 200.0));
+      const R am = sg(V, -60.0, -(1.0 / 5.0));
+      const R bm = R(0.1) * sg(V, -35.0, 1.0 / 5.0) + R(0.10) * sg(V, 50.0, 1.0 / 200.0);
       lam[0] = -R(1) / (am * bm);
     }
-    const R hs = sig((V + R(71.55)) * R(1.0 / 7.43));
+    const R hs = sg(V, -71.55, 1.0 / 7.43);
     zinf[1] = hs * hs;
     zinf[2] = hs * hs;
     if (V >= R(-40.0)) {
-      const R bh = R(0.77) / (R(0.13) * (R(1) + M::ex(-(V + R(10.66)) * R(1.0 / 11.1))));
+      const R bh = R(0.77) / (R(0.13) * (R(1) + M::ex_aff(V, -10.66, -(1.0 / 11.1))));
       lam[1] = -bh;  // alpha_h = 0
-      const R bj = R(0.6) * M::ex(R(0.057) * V) / (R(1) + M::ex(R(-0.1) * (V + R(32.0))));
+      const R bj = R(0.6) * M::ex_aff(V, 0.0, 0.057) / (R(1) + M::ex_aff(V, -32.0, -0.1));
       lam[2] = -bj;  // alpha_j = 0
     } else {
-      const R ah = R(0.057) * M::ex(-(V + R(80.0)) * R(1.0 / 6.8));
-      const R bh = R(2.7) * M::ex(R(0.079) * V) + R(3.1e5) * M::ex(R(0.3485) * V);
+      const R ah = R(0.057) * M::ex_aff(V, -80.0, -(1.0 / 6.8));
+      const R bh = R(2.7) * M::ex_aff(V, 0.0, 0.079) + R(3.1e5) * M::ex_aff(V, 0.0, 0.3485);
       lam[1] = -(ah + bh);
-      const R aj = (R(-2.5428e4) * M::ex(R(0.2444) * V) - R(6.948e-6) * M::ex(R(-0.04391) * V)) *
-                   (V + R(37.78)) / (R(1) + M::ex(R(0.311) * (V + R(79.23))));
-      const R bj = R(0.02424) * M::ex(R(-0.01052) * V) / (R(1) + M::ex(R(-0.1378) * (V + R(40.14))));
+      const R aj = (R(-2.5428e4) * M::ex_aff(V, 0.0, 0.2444) - R(6.948e-6) * M::ex_aff(V, 0.0, -0.04391)) *
+                   (V + R(37.78)) / (R(1) + M::ex_aff(V, -79.23, 0.311));
+      const R bj = R(0.02424) * M::ex_aff(V, 0.0, -0.01052) / (R(1) + M::ex_aff(V, -40.14, -0.1378));
       lam[2] = -(aj + bj);
     }
     // I_Kr gates
-    zinf[3] = sig((R(-26.0) - V) * R(1.0 / 7.0));
-    lam[3] = -R(1) / ((R(450.0) * sig((R(-45.0) - V) * R(1.0 / 10.0))) * (R(6.0) * sig((V + R(30.0)) * R(1.0 / 11.5))));
-    zinf[4] = sig((V + R(88.0)) * R(1.0 / 24.0));
-    lam[4] = -R(1) / ((R(3.0) * sig((R(-60.0) - V) * R(1.0 / 20.0))) * (R(1.12) * sig((V - R(60.0)) * R(1.0 / 20.0))));
+    zinf[3] = sg(V, -26.0, -(1.0 / 7.0));
+    lam[3] = -R(1) / ((R(450.0) * sg(V, -45.0, -(1.0 / 10.0))) * (R(6.0) * sg(V, -30.0, 1.0 / 11.5)));
+    zinf[4] = sg(V, -88.0, 1.0 / 24.0);
+    lam[4] = -R(1) / ((R(3.0) * sg(V, -60.0, -(1.0 / 20.0))) * (R(1.12) * sg(V, 60.0, 1.0 / 20.0)));
     // I_Ks gate
-    zinf[5] = sig((R(-5.0) - V) * R(1.0 / 14.0));
-    lam[5] = -R(1) / ((R(1400.0) / M::sq(R(1) + M::ex((R(5.0) - V) * R(1.0 / 6.0)))) * sig((V - R(35.0)) * R(1.0 / 15.0)) +
+    zinf[5] = sg(V, -5.0, -(1.0 / 14.0));
+    lam[5] = -R(1) / ((R(1400.0) / M::sq(R(1) + M::ex_aff(V, 5.0, -(1.0 / 6.0)))) * sg(V, 35.0, 1.0 / 15.0) +
                       R(80.0));
     // I_to gates (epicardial s)
-    zinf[6] = sig((R(20.0) - V) * R(1.0 / 6.0));
+    zinf[6] = sg(V, 20.0, -(1.0 / 6.0));
     {
       const R d40 = V + R(40.0);
       lam[6] = -R(1) / (R(9.5) * M::ex(-(d40 * d40) * R(1.0 / 1800.0)) + R(0.8));
     }
-    zinf[7] = sig((V + R(20.0)) * R(1.0 / 5.0));
+    zinf[7] = sg(V, -20.0, 1.0 / 5.0);
     {
       const R d45 = V + R(45.0);
-      lam[7] = -R(1) / (R(85.0) * M::ex(-(d45 * d45) * R(1.0 / 320.0)) + R(5.0) * sig((V - R(20.0)) * R(1.0 / 5.0)) + R(3.0));
+      lam[7] = -R(1) / (R(85.0) * M::ex(-(d45 * d45) * R(1.0 / 320.0)) + R(5.0) * sg(V, 20.0, 1.0 / 5.0) + R(3.0));
     }
     // I_CaL gates
-    zinf[8] = sig((R(-8.0) - V) * R(1.0 / 7.5));
-    lam[8] = -R(1) / ((R(1.4) * sig((R(-35.0) - V) * R(1.0 / 13.0)) + R(0.25)) * (R(1.4) * sig((V + R(5.0)) * R(1.0 / 5.0))) +
-                      sig((R(50.0) - V) * R(1.0 / 20.0)));
-    zinf[9] = sig((V + R(20.0)) * R(1.0 / 7.0));
+    zinf[8] = sg(V, -8.0, -(1.0 / 7.5));
+    lam[8] = -R(1) / ((R(1.4) * sg(V, -35.0, -(1.0 / 13.0)) + R(0.25)) * (R(1.4) * sg(V, -5.0, 1.0 / 5.0)) +
+                      sg(V, 50.0, -(1.0 / 20.0)));
+    zinf[9] = sg(V, -20.0, 1.0 / 7.0);
     {
       const R d27 = V + R(27.0);
-      lam[9] = -R(1) / (R(1102.5) * M::ex(-(d27 * d27) * R(1.0 / 225.0)) + R(200.0) * sig((R(13.0) - V) * R(1.0 / 10.0)) +
-                        R(180.0) * sig((V + R(30.0)) * R(1.0 / 10.0)) + R(20.0));
+      lam[9] = -R(1) / (R(1102.5) * M::ex(-(d27 * d27) * R(1.0 / 225.0)) + R(200.0) * sg(V, 13.0, -(1.0 / 10.0)) +
+                        R(180.0) * sg(V, -30.0, 1.0 / 10.0) + R(20.0));
     }
-    zinf[10] = R(0.67) * sig((V + R(35.0)) * R(1.0 / 7.0)) + R(0.33);
+    zinf[10] = R(0.67) * sg(V, -35.0, 1.0 / 7.0) + R(0.33);
     {
       const R d25 = V + R(25.0);
-      lam[10] = -R(1) / (R(600.0) * M::ex(-(d25 * d25) * R(1.0 / 170.0)) + R(31.0) * sig((R(25.0) - V) * R(1.0 / 10.0)) +
-                         R(16.0) * sig((V + R(30.0)) * R(1.0 / 10.0)));
+      lam[10] = -R(1) / (R(600.0) * M::ex(-(d25 * d25) * R(1.0 / 170.0)) + R(31.0) * sg(V, 25.0, -(1.0 / 10.0)) +
+                         R(16.0) * sg(V, -30.0, 1.0 / 10.0));
     }
     {
       const R c = CaSS * R(1.0 / 0.05);
@@ -208,9 +221,9 @@ template <typename R> struct ModelTTP06 {
     const R E_Ca = R(0.5) * RTF * M::ln(R(Cao) / Cai);
     const R sqko = M::sq(R(Ko) * R(1.0 / 5.4));
     const R VK = V - E_K;
-    const R aK1 = R(0.1) / (R(1) + M::ex(R(0.06) * (VK - R(200.0))));
-    const R bK1 = (R(3.0) * M::ex(R(0.0002) * (VK + R(100.0))) + M::ex(R(0.1) * (VK - R(10.0)))) /
-                  (R(1) + M::ex(R(-0.5) * VK));
+    const R aK1 = R(0.1) / (R(1) + M::ex_aff(VK, 200.0, 0.06));
+    const R bK1 = (R(3.0) * M::ex_aff(VK, -100.0, 0.0002) + M::ex_aff(VK, 10.0, 0.1)) /
+                  (R(1) + M::ex_aff(VK, 0.0, -0.5));
     const R I_K1 = R(5.405) * sqko * (aK1 / (aK1 + bK1)) * VK;
     const R I_to = R(0.294) * r * s * VK;
     const R I_Kr = R(0.153) * sqko * xr1 * xr2 * VK;
@@ -229,7 +242,7 @@ template <typename R> struct ModelTTP06 {
     const R I_NaK = R(2.724) * R(Ko / (Ko + 1.0)) * Nai / (Nai + R(40.0)) /
                     (R(1) + R(0.1245) * M::ex(R(-0.1) * V * iRTF) + R(0.0353) * M::ex(-V * iRTF));
     const R I_pCa = R(0.1238) * Cai / (R(0.0005) + Cai);
-    const R I_pK = R(0.0146) * VK / (R(1) + M::ex((R(25.0) - V) * R(1.0 / 5.98)));
+    const R I_pK = R(0.0146) * VK / (R(1) + M::ex_aff(V, 25.0, -(1.0 / 5.98)));
     Iion = I_Kr + I_Ks + I_K1 + I_to + I_Na + I_bNa + I_CaL + I_bCa + I_NaK + I_NaCa + I_pCa + I_pK;
 
     // calcium dynamics

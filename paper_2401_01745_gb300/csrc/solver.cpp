@@ -520,6 +520,8 @@ int do_step(emrkc_solver* s, double dt) {
     a.f_stim = (float)a.stim;
     a.f_inv_Cm = (float)(1.0 / s->Cm);
     a.tma_grid = s->tma_grid;
+    a.tma_nbuf = s->tma_nbuf;
+    a.tma_ell = s->tma_ell;
     a.pdl = s->pdl;
     a.ell_wmax = s->ell_wmax;
     s->launch(EMRKC_PHASE_STAGE, [&] { s->ks.stage(a, s->ell, j >= 2, s->stream); });
@@ -919,7 +921,11 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
   if (s->precision == EMRKC_PREC_MIXED && s->ks.tma_grid) {
     const char* no_tma = std::getenv("EMRKC_NO_TMA");
     if (!(no_tma && no_tma[0] == '1')) {
-      s->tma_grid = s->ks.tma_grid(s->device, s->ell_wmax);
+      const char* nbuf = std::getenv("EMRKC_TMA_NBUF");
+      const char* ell = std::getenv("EMRKC_TMA_ELL");
+      if (nbuf && nbuf[0] == '2') s->tma_nbuf = 2;
+      if (ell && ell[0] == '0') s->tma_ell = 0;
+      s->tma_grid = s->ks.tma_grid(s->device, s->ell_wmax, s->tma_nbuf, s->tma_ell);
     }
     const char* no_pdl = std::getenv("EMRKC_NO_PDL");
     s->pdl = (no_pdl && no_pdl[0] == '1') ? 0 : 1;
