@@ -387,13 +387,21 @@ __host__ __device__ constexpr int tma_smem_bytes(int nz, int wmax, int ell) {
 template <class Model, bool HAS_M2>
 __device__ __forceinline__ void stage_node_staged(const StageArgs& a, const Ell& A, const int64_t i, const int tid,
                                                   const float* sz, const int32_t* scol, const float* sval,
-                                                  const int base) {
+                                                  const int base, const int w) {
   constexpr int NE = Model::NE, NS = Model::NS, NZ = NE + NS;
   float z[NZ > 0 ? NZ : 1];
 #pragma unroll
   for (int k = 0; k < NZ; ++k) z[k] = sz[k * kTmaTile + tid];
   const float V = sz[NZ * kTmaTile + tid];
   const unsigned char mk = reinterpret_cast<const unsigned char*>(sz + (NZ + 1) * kTmaTile)[tid];
+  // neighbour values of the staged row first: the gathers are in flight
+  // while the ionic model runs
+  float xv[kTmaStageEllWidth];
+  if (scol != nullptr) {
+#pragma unroll
+    for (int k = 0; k < kTmaStageEllWidth; ++k)
+      if (k < w) xv[k] = __ldg(a.V32m1 + scol[base + 32 * k]);
+  }
   float dz[NE > 0 ? NE : 1];
   float Iion;
   float gS[NS > 0 ? NS : 1];
@@ -420,8 +428,9 @@ __device__ __forceinline__ void stage_node_staged(const StageArgs& a, const Ell&
   if (scol == nullptr) {
     LV = ell_diff32<false>(A, i, a.V32m1);
   } else {
-    const int w = __ldg(A.width + (i >> 5));
-    for (int k = 0; k < w; ++k) LV += sval[base + 32 * k] * (__ldg(a.V32m1 + scol[base + 32 * k]) - V);
+#pragma unroll
+    for (int k = 0; k < kTmaStageEllWidth; ++k)
+      if (k < w) LV += sval[base + 32 * k] * (xv[k] - V);
   }
   if (a.Vn32_copy != nullptr) a.Vn32_copy[i] = V;
   if (a.m == 1) {
@@ -451,6 +460,10 @@ __global__ void __launch_bounds__(kTmaTile) stage_kernel_mixed_tma(const StageAr
   extern __shared__ __align__(128) unsigned char tma_smem[];
   __shared__ __align__(8) unsigned long long bars[2];
   __shared__ int s_abort;
+  // per stage buffer: offset (in entries) of each 32-row slice of the tile in
+  // the staged ELL block, and its width; written with the tile's copies
+  __shared__ int s_roff[2][kTmaTile / 32];
+  __shared__ int s_rw[2][kTmaTile / 32];
   const int tid = threadIdx.x;
   const int64_t ntiles = (a.n + kTmaTile - 1) / kTmaTile;
   const int64_t G = gridDim.x;
@@ -467,6 +480,12 @@ __global__ void __launch_bounds__(kTmaTile) stage_kernel_mixed_tma(const StageAr
     const int64_t s0 = tile * (kTmaTile / 32);
     const int64_t s1 = (s0 + kTmaTile / 32 < nslices) ? s0 + kTmaTile / 32 : nslices;
     const int64_t e0 = __ldg(A.slice_ptr + s0), e1 = __ldg(A.slice_ptr + s1);
+#pragma unroll
+    for (int q = 0; q < kTmaTile / 32; ++q) {
+      const bool in = s0 + q < s1;
+      s_roff[buf][q] = in ? (int)(__ldg(A.slice_ptr + s0 + q) - e0) : 0;
+      s_rw[buf][q] = in ? __ldg(A.width + s0 + q) : 0;
+    }
     const unsigned ell_bytes = (unsigned)((e1 - e0) * 4);
     if (ell_bytes == 0) return;
     const unsigned half = (unsigned)(4 * a.ell_wmax * 32 * 4);
@@ -531,13 +550,14 @@ __global__ void __launch_bounds__(kTmaTile) stage_kernel_mixed_tma(const StageAr
     if (i < a.n) {
       const int32_t* scol = nullptr;
       const float* sval = nullptr;
-      int base = 0;
+      int base = 0, w = 0;
       if (stage_ell) {
-        base = (int)(__ldg(A.slice_ptr + (i >> 5)) - __ldg(A.slice_ptr + tile * (kTmaTile / 32))) + (tid & 31);
+        base = s_roff[buf][tid >> 5] + (tid & 31);
+        w = s_rw[buf][tid >> 5];
         scol = reinterpret_cast<const int32_t*>(tma_smem + buf * SB + FB);
         sval = reinterpret_cast<const float*>(tma_smem + buf * SB + FB + 4 * a.ell_wmax * 32 * 4);
       }
-      stage_node_staged<Model, HAS_M2>(a, A, i, tid, sz, scol, sval, base);
+      stage_node_staged<Model, HAS_M2>(a, A, i, tid, sz, scol, sval, base, w);
     }
     __syncthreads();  // every thread is done with this stage buffer
     if (tid == 0 && tile + nb * G < ntiles) {
