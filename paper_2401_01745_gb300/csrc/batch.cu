@@ -172,6 +172,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) batch_step_kernel(const B
       a.f_mu1 = I->f_mu1;
       a.f_mu1eta = I->f_mu1eta;
       a.f_eta = I->f_eta;
+      a.ell_wmax = I->wmax;
       const bool has_m2 = j >= 2;
       const bool cg = (s >= 3 || m >= 4);
       switch (I->model) {

@@ -246,13 +246,29 @@ __global__ void __launch_bounds__(128) stage_kernel_fp64(const StageArgs a, cons
 // increments delta_k = u_k - V_{j-1}; this kernel writes delta_1, L V and F.
 // The node's work after its V and z have been loaded (by the caller, possibly
 // one node ahead).
-template <class Model, bool HAS_M2, bool CG>
+// SPLIT: rows of at most 8 entries (checked at run time) have their
+// neighbour gathers issued before the ionic model.
+template <class Model, bool HAS_M2, bool CG, bool SPLIT = false>
 __device__ __forceinline__ void stage_node_mixed_with(const StageArgs& a, const Ell& A, const int64_t i, const float V,
                                                       const float* z) {
   constexpr int NE = Model::NE, NS = Model::NS, NZ = NE + NS;
   const int64_t ld = a.ld;
   const float* __restrict__ Zm2 = static_cast<const float*>(a.Zm2);
   float* __restrict__ Zout = static_cast<float*>(a.Zout);
+  // the neighbour gathers go out before the ionic model, so their latency
+  // overlaps it; the row's values are read after it
+  const bool split = SPLIT && a.ell_wmax <= 8;
+  float xv[8];
+  int w = 0;
+  int64_t p = 0;
+  if (split) {
+    const int64_t b = i >> 5;
+    w = __ldg(A.width + b);
+    p = __ldg(A.slice_ptr + b) + (i & 31);
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (k < w) xv[k] = ldm<CG>(a.V32m1 + __ldg(A.col + p + 32 * k));
+  }
   float dz[NE > 0 ? NE : 1];
   float Iion;
   float gS[NS > 0 ? NS : 1];
@@ -272,7 +288,14 @@ __device__ __forceinline__ void stage_node_mixed_with(const StageArgs& a, const 
       Zout[k * ld + i] = out;
     }
   }
-  const float LV = ell_diff32<CG>(A, i, a.V32m1);
+  float LV = 0.0f;
+  if (split) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (k < w) LV += __ldg(A.val32 + p + 32 * k) * (xv[k] - V);
+  } else {
+    LV = ell_diff32<CG>(A, i, a.V32m1);
+  }
   if (a.Vn32_copy != nullptr) a.Vn32_copy[i] = V;
   if (a.m == 1) {
     // V_j = V_{j-1} + kappa (V_{j-2} - V_{j-1}) + mu dt f_bar  (nu + kappa = 1)
@@ -291,7 +314,7 @@ __device__ __forceinline__ void stage_node_mixed_with(const StageArgs& a, const 
   }
 }
 
-template <class Model, bool HAS_M2, bool CG = false>
+template <class Model, bool HAS_M2, bool CG = false, bool SPLIT = false>
 __device__ __forceinline__ void stage_node_mixed(const StageArgs& a, const Ell& A, const int64_t i) {
   constexpr int NZ = Model::NE + Model::NS;
   const float* __restrict__ Zm1 = static_cast<const float*>(a.Zm1);
@@ -299,7 +322,7 @@ __device__ __forceinline__ void stage_node_mixed(const StageArgs& a, const Ell& 
   float z[NZ > 0 ? NZ : 1];
 #pragma unroll
   for (int k = 0; k < NZ; ++k) z[k] = ldm<CG>(Zm1 + k * a.ld + i);
-  stage_node_mixed_with<Model, HAS_M2, CG>(a, A, i, V, z);
+  stage_node_mixed_with<Model, HAS_M2, CG, SPLIT>(a, A, i, V, z);
 }
 
 template <class Model, bool HAS_M2>
@@ -308,7 +331,7 @@ __global__ void __launch_bounds__(128) stage_kernel_mixed(const StageArgs a, con
   pdl_wait();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
-  stage_node_mixed<Model, HAS_M2, false>(a, A, i);
+  stage_node_mixed<Model, HAS_M2, false, true>(a, A, i);
 }
 
 // ---------------------------------------------------------------------------
