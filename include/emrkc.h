@@ -221,8 +221,10 @@ int emrkc_step(emrkc_solver* s, double dt);
  * Synchronises at the end and reports non-finite values. */
 int emrkc_run(emrkc_solver* s, double T, double dt);
 
-/* Wait for all enqueued work; returns EMRKC_ERR_NONFINITE if any step
- * produced a non-finite V since the last check. */
+/* Wait for all enqueued work (steps and the asynchronous copies of
+ * emrkc_set_stimulus_async / emrkc_get_state_async); returns
+ * EMRKC_ERR_NONFINITE if any step produced a non-finite V since the last
+ * check. */
 int emrkc_sync(emrkc_solver* s);
 
 /* Copy variable var (0..N-1) or the whole state (var = -1, SoA: var-major,
@@ -276,6 +278,32 @@ int emrkc_set_time(emrkc_solver* s, double t, int64_t steps);
  * once.  Errors: EMRKC_ERR_ARG (n does not match), EMRKC_ERR_CUDA. */
 int emrkc_set_stimulus(emrkc_solver* s, const uint8_t* node_mask, int64_t n, double amplitude, double t_on,
                        double t_off);
+
+/* Pipelined host I/O (not in the paper: the host side of a time-stepping
+ * service).  Both calls enqueue work and return without waiting, so a caller
+ * can feed each step's input and read each step's result while later steps
+ * compute; the copies run on the copy engines, on a second stream of the
+ * solver, ordered against the steps by events.
+ *
+ * emrkc_set_stimulus_async: as emrkc_set_stimulus (same arguments, errors
+ * and immediate effect on the amplitude and window), but the n-byte mask is
+ * copied into a second device mask buffer that no enqueued step reads; the
+ * steps enqueued after the call use it.  node_mask must stay valid and
+ * unchanged until emrkc_sync returns (pinned host memory makes the copy
+ * asynchronous; pageable memory works but the copy is staged by the driver).
+ *
+ * emrkc_get_state_async: variable var (0..N-1; not the whole state) of the
+ * state after the steps enqueued so far, as n doubles (len must equal n), to
+ * host_out.  The variable is first converted into one of two device staging
+ * buffers on the solver's stream (a float-float V is joined, FP32 rows are
+ * widened); the device-to-host copy then overlaps the following steps.
+ * host_out is complete once emrkc_sync returns; it must stay valid until
+ * then.  Errors: EMRKC_ERR_ARG (var out of range, null buffer),
+ * EMRKC_ERR_STATE (len), EMRKC_ERR_OOM, EMRKC_ERR_CUDA.  emrkc_sync waits for
+ * both streams. */
+int emrkc_set_stimulus_async(emrkc_solver* s, const uint8_t* node_mask, int64_t n, double amplitude, double t_on,
+                             double t_off);
+int emrkc_get_state_async(emrkc_solver* s, int var, double* host_out, int64_t len);
 
 int emrkc_get_stats(emrkc_solver* s, emrkc_stats* out);
 

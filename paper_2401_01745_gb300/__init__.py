@@ -144,6 +144,7 @@ class Solver:
 
     def sync(self):
         self._check(self._lib.emrkc_sync(self._h))
+        self._pending = {}
 
     def get_state(self, var=-1, out=None):
         shape = (self.N, self.n) if var == -1 else (self.n,)
@@ -194,6 +195,36 @@ class Solver:
             m = np.ascontiguousarray(mask, dtype=np.uint8)
             ptr = m.ctypes.data_as(C.POINTER(C.c_uint8))
         self._check(self._lib.emrkc_set_stimulus(self._h, ptr, self.n, amplitude, t_on, t_off))
+
+    def set_stimulus_async(self, mask, amplitude=50.0, t_on=0.0, t_off=1.0):
+        """set_stimulus without waiting: mask (a C-contiguous uint8 array of n
+        bytes, pinned for a truly asynchronous copy) is read by a copy engine
+        after the call returns and is kept referenced here until sync()."""
+        if mask is None:
+            return self.set_stimulus(None, amplitude, t_on, t_off)
+        if not (isinstance(mask, np.ndarray) and mask.dtype == np.uint8 and mask.flags.c_contiguous
+                and mask.size == self.n):
+            raise ValueError("mask must be a C-contiguous uint8 array of n bytes")
+        self._check(self._lib.emrkc_set_stimulus_async(self._h, mask.ctypes.data_as(C.POINTER(C.c_uint8)), self.n,
+                                                       amplitude, t_on, t_off))
+        self._keep(mask)
+
+    def get_state_async(self, var, out):
+        """Variable var of the current state into out (a C-contiguous float64
+        array of n entries, pinned for a truly asynchronous copy); out is
+        complete after sync() and is kept referenced here until then."""
+        if not (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags.c_contiguous
+                and out.size == self.n):
+            raise ValueError("out must be a C-contiguous float64 array of n entries")
+        self._check(self._lib.emrkc_get_state_async(self._h, var, _dp(out), out.size))
+        self._keep(out)
+        return out
+
+    def _keep(self, arr):
+        # buffers of asynchronous copies stay referenced until the next sync()
+        if not hasattr(self, "_pending"):
+            self._pending = {}
+        self._pending[id(arr)] = arr
 
     def stats(self) -> dict:
         st = Stats()

@@ -79,6 +79,9 @@ SIGNATURES = {
     "emrkc_free_matrix": (None, [C.POINTER(OwnedMatrix)]),
     "emrkc_set_stimulus": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint8), C.c_int64, C.c_double, C.c_double,
                                      C.c_double]),
+    "emrkc_set_stimulus_async": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint8), C.c_int64, C.c_double, C.c_double,
+                                           C.c_double]),
+    "emrkc_get_state_async": (C.c_int, [_P, C.c_int, _PD, C.c_int64]),
     "emrkc_create": (C.c_int, [C.POINTER(Matrix), C.POINTER(Tissue), C.c_int, C.POINTER(Stimulus),
                                C.POINTER(Options), C.POINTER(_P)]),
     "emrkc_step": (C.c_int, [_P, C.c_double]),

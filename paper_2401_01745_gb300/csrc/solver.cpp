@@ -52,9 +52,17 @@ void free_all(emrkc_solver* s) {
                   s->d_D[0], s->d_D[1], s->d_D[2], s->d_LV, s->d_Vlo[0], s->d_Vlo[1], s->d_Vlo[2],
                   s->d_Vn32, s->d_mass, s->d_cg[0], s->d_cg[1], s->d_cg[2], s->d_cg[3], s->d_cg[4],
                   s->d_cg[5], s->d_part, s->d_bar, s->d_iters, s->d_res, s->d_Um[0], s->d_Um[1], s->d_Um[2],
-                  s->d_ppart, s->d_pbar};
+                  s->d_ppart, s->d_pbar, s->d_mask_alt, s->d_stage[0], s->d_stage[1]};
+  if (s->copy_stream) cudaStreamSynchronize(s->copy_stream);
+  if (s->h2d_stream) cudaStreamSynchronize(s->h2d_stream);
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  cudaEvent_t evs[] = {s->ev_mask_free[0], s->ev_mask_free[1], s->ev_mask_ready, s->ev_stage_ready[0],
+                       s->ev_stage_ready[1], s->ev_stage_free[0], s->ev_stage_free[1]};
+  for (cudaEvent_t e : evs)
+    if (e) cudaEventDestroy(e);
+  if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+  if (s->h2d_stream) cudaStreamDestroy(s->h2d_stream);
   if (s->h_pin) cudaFreeHost(s->h_pin);
   for (cudaEvent_t e : s->event_pool) cudaEventDestroy(e);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
@@ -1054,6 +1062,11 @@ int emrkc_run(emrkc_solver* s, double T, double dt) {
 int emrkc_sync(emrkc_solver* s) {
   if (!s) return EMRKC_ERR_ARG;
   cudaSetDevice(s->device);
+  for (cudaStream_t cs : {s->copy_stream, s->h2d_stream}) {
+    if (!cs) continue;
+    const cudaError_t e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) return s->cuda_fail(e, "copy stream synchronisation");
+  }
   int rc = sync_and_check(s);
   s->harvest();
   return rc;
@@ -1125,6 +1138,115 @@ int emrkc_set_stimulus(emrkc_solver* s, const uint8_t* node_mask, int64_t n, dou
   s->amp = amplitude;
   s->t_on = t_on;
   s->t_off = t_off;
+  return EMRKC_OK;
+}
+
+namespace {
+// Two copy streams, one per direction, so that a mask upload never queues
+// behind a state download (each direction has its own copy engine).
+int ensure_copy_stream(emrkc_solver* s) {
+  if (s->copy_stream) return EMRKC_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&s->h2d_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    s->h2d_stream = nullptr;
+    return s->cuda_fail(e, "copy stream creation");
+  }
+  e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    s->copy_stream = nullptr;
+    return s->cuda_fail(e, "copy stream creation");
+  }
+  cudaEvent_t* evs[] = {&s->ev_mask_free[0], &s->ev_mask_free[1], &s->ev_mask_ready, &s->ev_stage_ready[0],
+                        &s->ev_stage_ready[1], &s->ev_stage_free[0], &s->ev_stage_free[1]};
+  for (cudaEvent_t* ev : evs) {
+    if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess)
+      return s->cuda_fail(e, "event creation");
+  }
+  return EMRKC_OK;
+}
+}  // namespace
+
+int emrkc_set_stimulus_async(emrkc_solver* s, const uint8_t* node_mask, int64_t n, double amplitude, double t_on,
+                             double t_off) {
+  if (!s) return EMRKC_ERR_ARG;
+  if (n != s->n) return s->fail(EMRKC_ERR_ARG, "mask length does not match the node count");
+  if (!std::isfinite(amplitude) || std::isnan(t_on) || std::isnan(t_off))
+    return s->fail(EMRKC_ERR_ARG, "stimulus amplitude and window must be numbers");
+  cudaSetDevice(s->device);
+  if (!node_mask) return emrkc_set_stimulus(s, nullptr, n, amplitude, t_on, t_off);
+  int rc = ensure_copy_stream(s);
+  if (rc) return rc;
+  cudaError_t e;
+  if (!s->d_mask || !s->d_mask_alt) {
+    // first use: both buffers zeroed (the padding of the last tile is read)
+    for (uint8_t** m : {&s->d_mask, &s->d_mask_alt}) {
+      if (*m) continue;
+      if ((e = dalloc(m, s->ld)) != cudaSuccess) return s->fail(EMRKC_ERR_OOM, "device allocation failed");
+      if ((e = cudaMemsetAsync(*m, 0, s->ld, s->stream)) != cudaSuccess) return s->cuda_fail(e, "mask clear");
+    }
+    if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return s->cuda_fail(e, "mask clear");
+  }
+  const int ti = s->mask_idx ^ 1;
+  uint8_t* tgt = s->d_mask_alt;
+  // the copy waits until no enqueued step reads the target buffer any more
+  if (s->mask_free_rec[ti] && (e = cudaStreamWaitEvent(s->h2d_stream, s->ev_mask_free[ti], 0)) != cudaSuccess)
+    return s->cuda_fail(e, "mask copy ordering");
+  if ((e = cudaMemcpyAsync(tgt, node_mask, s->n, cudaMemcpyHostToDevice, s->h2d_stream)) != cudaSuccess)
+    return s->cuda_fail(e, "mask copy");
+  if ((e = cudaEventRecord(s->ev_mask_ready, s->h2d_stream)) != cudaSuccess) return s->cuda_fail(e, "mask copy");
+  // steps enqueued from now on read the new buffer, after its copy
+  if ((e = cudaStreamWaitEvent(s->stream, s->ev_mask_ready, 0)) != cudaSuccess)
+    return s->cuda_fail(e, "mask copy ordering");
+  if ((e = cudaEventRecord(s->ev_mask_free[s->mask_idx], s->stream)) != cudaSuccess)
+    return s->cuda_fail(e, "mask copy ordering");
+  s->mask_free_rec[s->mask_idx] = true;
+  s->d_mask_alt = s->d_mask;
+  s->d_mask = tgt;
+  s->mask_idx = ti;
+  s->amp = amplitude;
+  s->t_on = t_on;
+  s->t_off = t_off;
+  return EMRKC_OK;
+}
+
+int emrkc_get_state_async(emrkc_solver* s, int var, double* host_out, int64_t len) {
+  if (!s) return EMRKC_ERR_ARG;
+  if (!host_out) return s->fail(EMRKC_ERR_ARG, "null buffer");
+  if (var < 0 || var >= s->N) return s->fail(EMRKC_ERR_ARG, "variable index out of range (one variable)");
+  if (len != s->n) return s->fail(EMRKC_ERR_STATE, "buffer length must equal the number of nodes");
+  cudaSetDevice(s->device);
+  int rc = ensure_copy_stream(s);
+  if (rc) return rc;
+  cudaError_t e;
+  const int k = s->stage_k;
+  if (!s->d_stage[k] && (e = dalloc(&s->d_stage[k], s->ld)) != cudaSuccess)
+    return s->fail(EMRKC_ERR_OOM, "device allocation failed");
+  // the staging buffer is refilled only after its previous copy-out
+  if (s->stage_used[k] && (e = cudaStreamWaitEvent(s->stream, s->ev_stage_free[k], 0)) != cudaSuccess)
+    return s->cuda_fail(e, "state copy ordering");
+  const size_t row = (size_t)s->n * sizeof(double);
+  if (var == 0) {
+    if (s->d_V32[s->cur]) {
+      launch_ff_join(s->d_V32[s->cur], s->d_Vlo[s->cur], s->d_stage[k], s->n, s->stream);
+      e = cudaGetLastError();
+    } else {
+      e = cudaMemcpyAsync(s->d_stage[k], s->d_V[s->cur], row, cudaMemcpyDeviceToDevice, s->stream);
+    }
+  } else if (s->zsize == 8) {
+    e = cudaMemcpyAsync(s->d_stage[k], s->zrow(s->cur, var - 1), row, cudaMemcpyDeviceToDevice, s->stream);
+  } else {
+    s->ks.convert_z(s->n, s->zrow(s->cur, var - 1), s->d_stage[k], 1, s->stream);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return s->cuda_fail(e, "state staging");
+  if ((e = cudaEventRecord(s->ev_stage_ready[k], s->stream)) != cudaSuccess) return s->cuda_fail(e, "state staging");
+  if ((e = cudaStreamWaitEvent(s->copy_stream, s->ev_stage_ready[k], 0)) != cudaSuccess)
+    return s->cuda_fail(e, "state copy ordering");
+  if ((e = cudaMemcpyAsync(host_out, s->d_stage[k], row, cudaMemcpyDeviceToHost, s->copy_stream)) != cudaSuccess)
+    return s->cuda_fail(e, "state copy");
+  if ((e = cudaEventRecord(s->ev_stage_free[k], s->copy_stream)) != cudaSuccess) return s->cuda_fail(e, "state copy");
+  s->stage_used[k] = true;
+  s->stage_k = k ^ 1;
   return EMRKC_OK;
 }
 

@@ -123,6 +123,20 @@ struct emrkc_solver {
   float* d_LV = nullptr;                          // mixed: L V_{j-1}
   void* d_F = nullptr;
   uint8_t* d_mask = nullptr;
+  // pipelined host I/O: a copy stream, a second mask buffer (the one no
+  // enqueued step reads) and two staging buffers for state reads
+  cudaStream_t copy_stream = nullptr;  // device-to-host copies (state reads)
+  cudaStream_t h2d_stream = nullptr;   // host-to-device copies (stimulus masks)
+  uint8_t* d_mask_alt = nullptr;
+  int mask_idx = 0;                       // which of the two mask buffers d_mask is
+  bool mask_free_rec[2] = {false, false};
+  cudaEvent_t ev_mask_free[2] = {nullptr, nullptr};  // main stream: last use of mask buffer k
+  cudaEvent_t ev_mask_ready = nullptr;                 // h2d stream: mask copy done
+  double* d_stage[2] = {nullptr, nullptr};
+  bool stage_used[2] = {false, false};
+  int stage_k = 0;
+  cudaEvent_t ev_stage_ready[2] = {nullptr, nullptr};  // main stream: staging buffer k filled
+  cudaEvent_t ev_stage_free[2] = {nullptr, nullptr};   // copy stream: staging buffer k copied out
   double* d_vF = nullptr;
   double* d_vF2 = nullptr;
   double* d_vS = nullptr;
