@@ -12,6 +12,7 @@
 
 #include <cstdint>
 #include <utility>
+#include <type_traits>
 
 #include <cuda/atomic>
 
@@ -789,9 +790,38 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* flags, long
   return s_ok != 0;
 }
 
+// FP32 block sum (valid in thread 0), for per-thread sums of the mixed path.
+__device__ __forceinline__ float block_sum_f(float v, float* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  float t = (threadIdx.x < (blockDim.x >> 5)) ? sh[l] : 0.0f;
+  if (w == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  return t;
+}
+
 // Sum of column c (stride 4) of nb per-CTA partials, in the same fixed order
-// in every CTA, so that every CTA takes the same scalar.
+// in every CTA, so that every CTA takes the same scalar.  Up to 32 partials
+// (a single cluster, small grids) one warp adds them.
 __device__ __forceinline__ double sum_partials(const double* part, int nb, int c, double* sh) {
+  if (nb <= 32) {
+    __shared__ double s_w;
+    if (threadIdx.x < 32) {
+      double v = (int)threadIdx.x < nb ? __ldcg(part + 4 * threadIdx.x + c) : 0.0;
+      v = warp_sum(v);
+      if (threadIdx.x == 0) s_w = v;
+    }
+    __syncthreads();
+    const double r = s_w;
+    __syncthreads();
+    return r;
+  }
   double acc = 0.0;
   for (int k = threadIdx.x; k < nb; k += blockDim.x) acc += __ldcg(part + 4 * k + c);
   const double t = block_sum(acc, sh);
@@ -967,18 +997,50 @@ inline unsigned blocks_for(int64_t n, int block) { return (unsigned)((n + block 
 // 5; mixed path: q J v (q L v for f_F, dual numbers for f_S).  Iterates
 // ping-pong between two buffers per estimate; out[4], out[5] say which holds
 // the last one.
-template <class MD, class MDu, typename Z, bool MIXED>
+// Barrier between the phases of power_fused_kernel.  CLUSTER: the grid is
+// one thread-block cluster, and the hardware cluster barrier (release /
+// acquire at cluster scope, which covers the partial sums in global memory)
+// replaces the atomic grid barrier; for problems small enough that one
+// cluster holds them, the iteration is then bound by its loads, not by
+// device-scope atomics.
+template <bool CLUSTER>
+__device__ __forceinline__ bool power_barrier(const PowerFusedArgs& a) {
+  if constexpr (CLUSTER) {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    return true;
+  } else {
+    return grid_barrier(a.bar, a.flags, a.spin_limit);
+  }
+}
+
+template <class MD, class MDu, typename Z, bool MIXED, bool CLUSTER = false>
 __global__ void __launch_bounds__(kReduceBlock) power_fused_kernel(const PowerFusedArgs a, const Ell A) {
   constexpr int NE = MD::NE, NS = MD::NS, N = 1 + NE + NS;
+  // Mixed path: iterates and per-thread sums in FP32 (GB300's FP64 pipe is a
+  // small fraction of its FP32 rate), block and grid sums and the scalars
+  // of Algorithm 5 in FP64.  FP64 path: everything in FP64.
+  using VT = typename std::conditional<MIXED, float, double>::type;
   __shared__ double sh[32];
+  __shared__ float shf[32];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int G = gridDim.x;
   const Z* Zs = static_cast<const Z*>(a.Z);
+  VT* const vF[2] = {reinterpret_cast<VT*>(a.vF[0]), reinterpret_cast<VT*>(a.vF[1])};
+  VT* const vS[2] = {reinterpret_cast<VT*>(a.vS[0]), reinterpret_cast<VT*>(a.vS[1])};
   int par = 0;
   auto part = [&](int p) { return a.part + (size_t)p * 4 * G; };
-  auto publish = [&](double v0, double v1, double v2, double v3) {
-    const double t0 = block_sum(v0, sh), t1 = block_sum(v1, sh), t2 = block_sum(v2, sh), t3 = block_sum(v3, sh);
+  // block sums of the first cnt values into this CTA's partials (FP32 sums
+  // of FP32 per-thread sums on the mixed path)
+  auto bsum = [&](VT v) -> double {
+    if constexpr (MIXED) return (double)block_sum_f(v, shf);
+    else return block_sum(v, sh);
+  };
+  auto publish = [&](int cnt, VT v0, VT v1, VT v2, VT v3) {
+    const double t0 = bsum(v0);
+    const double t1 = cnt > 1 ? bsum(v1) : 0.0;
+    const double t2 = cnt > 2 ? bsum(v2) : 0.0;
+    const double t3 = cnt > 3 ? bsum(v3) : 0.0;
     if (threadIdx.x == 0) {
       double* p = part(par) + 4 * blockIdx.x;
       p[0] = t0;
@@ -989,18 +1051,19 @@ __global__ void __launch_bounds__(kReduceBlock) power_fused_kernel(const PowerFu
   };
   // norms of y and of the start iterates; f_S(y) for the FP64 differences
   {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    VT s0 = 0, s1 = 0, s2 = 0, s3 = 0;
     for (int64_t i = i0; i < a.n; i += stride) {
-      double y[N];
-      y[0] = a.V[i];
+      VT y[N];
+      if constexpr (MIXED) y[0] = a.Vhi[i];
+      else y[0] = a.V[i];
 #pragma unroll
-      for (int k = 1; k < N; ++k) y[k] = (double)Zs[(k - 1) * a.ld + i];
+      for (int k = 1; k < N; ++k) y[k] = (VT)Zs[(k - 1) * a.ld + i];
       s0 += y[0] * y[0];
-      s1 += a.vF[0][i] * a.vF[0][i];
+      s1 += vF[0][i] * vF[0][i];
 #pragma unroll
       for (int k = 0; k < N; ++k) {
         s2 += y[k] * y[k];
-        const double v = a.vS[0][k * a.ld + i];
+        const VT v = vS[0][k * a.ld + i];
         s3 += v * v;
       }
       if constexpr (!MIXED) {
@@ -1011,133 +1074,155 @@ __global__ void __launch_bounds__(kReduceBlock) power_fused_kernel(const PowerFu
         for (int k = 0; k < N; ++k) a.fy[k * a.ld + i] = f[k];
       }
     }
-    publish(s0, s1, s2, s3);
+    publish(4, s0, s1, s2, s3);
   }
-  if (!grid_barrier(a.bar, a.flags, a.spin_limit)) return;
-  const double nyF = sqrt(sum_partials(part(par), G, 0, sh));
-  double nvF = sqrt(sum_partials(part(par), G, 1, sh));
-  const double nyS = sqrt(sum_partials(part(par), G, 2, sh));
-  double nvS = sqrt(sum_partials(part(par), G, 3, sh));
+  if (!power_barrier<CLUSTER>(a)) return;
+  // The scalars of Algorithm 5 (norms, q, rho, the stopping test) are
+  // computed by thread 0 and shared: they are FP64, and GB300's FP64 pipe is
+  // narrow, so the other threads must not repeat them.
+  __shared__ double s_q, s_rho, s_delta;
+  __shared__ int s_go, s_it;
+  // squared norms of y_F, v_F, y_S, v_S (the same value in every thread)
+  const double nsum[4] = {sum_partials(part(par), G, 0, sh), sum_partials(part(par), G, 1, sh),
+                          sum_partials(part(par), G, 2, sh), sum_partials(part(par), G, 3, sh)};
   par ^= 1;
 
-  // rho_F on the V block
-  double rhoF = a.rhoF_warm;
-  int itF = 0, curF = 0;
-  {
-    const double delta = nyF > 0.0 ? nyF * a.eps : a.eps;
-    if (nvF == 0.0) {
-      rhoF = 0.0;
-    } else {
-      double q = delta / nvF, rho_old = 0.0;
-      while (fabs(rhoF - rho_old) >= a.tol * rhoF && itF < a.max_iter) {
-        rho_old = rhoF;
-        const double* vo = a.vF[curF];
-        double* vn = a.vF[curF ^ 1];
-        double acc = 0.0;
-        for (int64_t i = i0; i < a.n; i += stride) {
-          const int64_t b = i >> 5;
-          const int w = __ldg(A.width + b);
-          int64_t p = __ldg(A.slice_ptr + b) + (i & 31);
-          double wv;
-          if constexpr (MIXED) {
-            const float vi = (float)__ldcg(vo + i);
-            float s32 = 0.0f;
-            for (int k = 0; k < w; ++k, p += 32) s32 += __ldg(A.val32 + p) * ((float)__ldcg(vo + __ldg(A.col + p)) - vi);
-            wv = q * (double)s32;
-          } else {
-            double fz = 0.0, fy = 0.0;
-            for (int k = 0; k < w; ++k, p += 32) {
-              const int32_t c = __ldg(A.col + p);
-              fz += __ldg(A.val + p) * (a.V[c] + q * __ldcg(vo + c));
-              fy += __ldg(A.val + p) * a.V[c];
-            }
-            wv = fz - fy;
-          }
-          vn[i] = wv;
-          acc += wv * wv;
-        }
-        publish(acc, 0.0, 0.0, 0.0);
-        if (!grid_barrier(a.bar, a.flags, a.spin_limit)) return;
-        const double nv = sqrt(sum_partials(part(par), G, 0, sh));
-        par ^= 1;
-        curF ^= 1;
-        ++itF;
-        if (nv == 0.0) {
-          rhoF = 0.0;
-          break;
-        }
-        q = delta / nv;
-        rhoF = nv / delta;
+  // one power iteration per loop trip: v_new = f(y + q v) - f(y) (FP64 path)
+  // or q J v (mixed path), rho = |v_new| / delta, until the relative change
+  // of rho is below tol or max_iter iterations
+  auto start = [&](double ny2, double nv2, double warm) {
+    if (threadIdx.x == 0) {
+      const double ny = sqrt(ny2), nv = sqrt(nv2);
+      s_delta = ny > 0.0 ? ny * a.eps : a.eps;
+      s_rho = warm;
+      s_it = 0;
+      if (nv == 0.0) {
+        s_rho = 0.0;
+        s_go = 0;
+      } else {
+        s_q = s_delta / nv;
+        s_go = (fabs(warm) >= a.tol * warm && a.max_iter > 0) ? 1 : 0;
       }
     }
+    __syncthreads();
+  };
+  auto advance = [&](double nv2) {
+    if (threadIdx.x == 0) {
+      const double nv = sqrt(nv2);
+      ++s_it;
+      if (nv == 0.0) {
+        s_rho = 0.0;
+        s_go = 0;
+      } else {
+        const double rho_old = s_rho;
+        s_q = s_delta / nv;
+        s_rho = nv / s_delta;
+        s_go = (fabs(s_rho - rho_old) >= a.tol * s_rho && s_it < a.max_iter) ? 1 : 0;
+      }
+    }
+    __syncthreads();
+  };
+
+  // rho_F on the V block
+  int curF = 0;
+  start(nsum[0], nsum[1], a.rhoF_warm);
+  while (s_go) {
+    const double q = s_q;
+    const VT* vo = vF[curF];
+    VT* vn = vF[curF ^ 1];
+    VT acc = 0;
+    const float qf = (float)q;
+    for (int64_t i = i0; i < a.n; i += stride) {
+      const int64_t b = i >> 5;
+      const int w = __ldg(A.width + b);
+      int64_t p = __ldg(A.slice_ptr + b) + (i & 31);
+      VT wv;
+      if constexpr (MIXED) {
+        // q L v in FP32: f_F is linear, so f_F(V + q v) - f_F(V) = q L v
+        const float vi = __ldcg(vo + i);
+        float s32 = 0.0f;
+        for (int k = 0; k < w; ++k, p += 32) s32 += __ldg(A.val32 + p) * (__ldcg(vo + __ldg(A.col + p)) - vi);
+        wv = qf * s32;
+      } else {
+        double fz = 0.0, fy = 0.0;
+        for (int k = 0; k < w; ++k, p += 32) {
+          const int32_t c = __ldg(A.col + p);
+          fz += __ldg(A.val + p) * (a.V[c] + q * __ldcg(vo + c));
+          fy += __ldg(A.val + p) * a.V[c];
+        }
+        wv = fz - fy;
+      }
+      vn[i] = wv;
+      acc += wv * wv;
+    }
+    publish(1, acc, 0, 0, 0);
+    if (!power_barrier<CLUSTER>(a)) return;
+    const double nv2 = sum_partials(part(par), G, 0, sh);
+    par ^= 1;
+    curF ^= 1;
+    advance(nv2);
   }
+  const double rhoF = s_rho;
+  const int itF = s_it;
+  __syncthreads();
 
   // rho_S on the full state
-  double rhoS = a.rhoS_warm;
-  int itS = 0, curS = 0;
-  {
-    const double delta = nyS > 0.0 ? nyS * a.eps : a.eps;
-    if (nvS == 0.0) {
-      rhoS = 0.0;
-    } else {
-      double q = delta / nvS, rho_old = 0.0;
-      while (fabs(rhoS - rho_old) >= a.tol * rhoS && itS < a.max_iter) {
-        rho_old = rhoS;
-        const double* vo = a.vS[curS];
-        double* vn = a.vS[curS ^ 1];
-        double acc = 0.0;
-        for (int64_t i = i0; i < a.n; i += stride) {
-          if constexpr (MIXED) {
-            Dual y[N];
-            y[0] = Dual((float)a.V[i], (float)vo[i]);
+  int curS = 0;
+  start(nsum[2], nsum[3], a.rhoS_warm);
+  while (s_go) {
+    const double q = s_q;
+    const VT* vo = vS[curS];
+    VT* vn = vS[curS ^ 1];
+    VT acc = 0;
+    const float qf = (float)q;
+    const float inv_Cm = (float)(1.0 / a.Cm);
+    for (int64_t i = i0; i < a.n; i += stride) {
+      if constexpr (MIXED) {
+        // q J v by forward-mode dual numbers in FP32
+        Dual y[N];
+        y[0] = Dual(a.Vhi[i], vo[i]);
 #pragma unroll
-            for (int k = 1; k < N; ++k) y[k] = Dual((float)Zs[(k - 1) * a.ld + i], (float)vo[k * a.ld + i]);
-            Dual I;
-            Dual gS[NS > 0 ? NS : 1];
-            MDu::currents(y[0], y + 1, y + 1 + NE, I, gS);
-            const double w0 = q * (double)(-I.d * (float)(1.0 / a.Cm));
-            vn[i] = w0;
-            acc += w0 * w0;
+        for (int k = 1; k < N; ++k) y[k] = Dual((float)Zs[(k - 1) * a.ld + i], vo[k * a.ld + i]);
+        Dual I;
+        Dual gS[NS > 0 ? NS : 1];
+        MDu::currents(y[0], y + 1, y + 1 + NE, I, gS);
+        const float w0 = qf * (-I.d * inv_Cm);
+        vn[i] = w0;
+        acc += w0 * w0;
 #pragma unroll
-            for (int k = 0; k < NE; ++k) vn[(1 + k) * a.ld + i] = 0.0;
+        for (int k = 0; k < NE; ++k) vn[(1 + k) * a.ld + i] = 0.0f;
 #pragma unroll
-            for (int k = 0; k < NS; ++k) {
-              const double w = q * (double)gS[k].d;
-              vn[(1 + NE + k) * a.ld + i] = w;
-              acc += w * w;
-            }
-          } else {
-            double y[N], f[N];
-            y[0] = a.V[i];
-#pragma unroll
-            for (int k = 1; k < N; ++k) y[k] = (double)Zs[(k - 1) * a.ld + i];
-#pragma unroll
-            for (int k = 0; k < N; ++k) y[k] = y[k] + q * vo[k * a.ld + i];
-            const double Istim = (a.mask != nullptr && a.mask[i]) ? a.stim : 0.0;
-            fS_full<MD>(y, Istim, a.Cm, f);
-#pragma unroll
-            for (int k = 0; k < N; ++k) {
-              const double w = f[k] - a.fy[k * a.ld + i];
-              vn[k * a.ld + i] = w;
-              acc += w * w;
-            }
-          }
+        for (int k = 0; k < NS; ++k) {
+          const float w = qf * gS[k].d;
+          vn[(1 + NE + k) * a.ld + i] = w;
+          acc += w * w;
         }
-        publish(acc, 0.0, 0.0, 0.0);
-        if (!grid_barrier(a.bar, a.flags, a.spin_limit)) return;
-        const double nv = sqrt(sum_partials(part(par), G, 0, sh));
-        par ^= 1;
-        curS ^= 1;
-        ++itS;
-        if (nv == 0.0) {
-          rhoS = 0.0;
-          break;
+      } else {
+        double y[N], f[N];
+        y[0] = a.V[i];
+#pragma unroll
+        for (int k = 1; k < N; ++k) y[k] = (double)Zs[(k - 1) * a.ld + i];
+#pragma unroll
+        for (int k = 0; k < N; ++k) y[k] = y[k] + q * vo[k * a.ld + i];
+        const double Istim = (a.mask != nullptr && a.mask[i]) ? a.stim : 0.0;
+        fS_full<MD>(y, Istim, a.Cm, f);
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          const double w = f[k] - a.fy[k * a.ld + i];
+          vn[k * a.ld + i] = w;
+          acc += w * w;
         }
-        q = delta / nv;
-        rhoS = nv / delta;
       }
     }
+    publish(1, acc, 0, 0, 0);
+    if (!power_barrier<CLUSTER>(a)) return;
+    const double nv2 = sum_partials(part(par), G, 0, sh);
+    par ^= 1;
+    curS ^= 1;
+    advance(nv2);
   }
+  const double rhoS = s_rho;
+  const int itS = s_it;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.out[0] = rhoF;
     a.out[1] = rhoS;
@@ -1178,8 +1263,11 @@ struct Kernels {
       const bool pdl = a.pdl != 0;
       if (a.mask != nullptr && a.tma_grid > 0) {
         const int smem = a.tma_nbuf * tma_smem_bytes(MR::NE + MR::NS, a.ell_wmax, a.tma_ell);
-        if (has_m2) launch_k(pdl, stage_kernel_mixed_tma<MR, true>, a.tma_grid, kTmaTile, smem, st, a, A);
-        else launch_k(pdl, stage_kernel_mixed_tma<MR, false>, a.tma_grid, kTmaTile, smem, st, a, A);
+        // no more CTAs than tiles (small problems)
+        const int64_t ntiles = (a.n + kTmaTile - 1) / kTmaTile;
+        const unsigned g2 = (unsigned)std::min<int64_t>(a.tma_grid, ntiles);
+        if (has_m2) launch_k(pdl, stage_kernel_mixed_tma<MR, true>, g2, kTmaTile, smem, st, a, A);
+        else launch_k(pdl, stage_kernel_mixed_tma<MR, false>, g2, kTmaTile, smem, st, a, A);
       } else if (has_m2) {
         launch_k(pdl, stage_kernel_mixed<MR, true>, g, 128, 0, st, a, A);
       } else {
@@ -1206,14 +1294,59 @@ struct Kernels {
     if constexpr (MIXED) powerS_dual_kernel<MDu, Z><<<reduce_grid(a.n), kReduceBlock, 0, st>>>(a, rs);
     else powerS_kernel<MD, Z><<<reduce_grid(a.n), kReduceBlock, 0, st>>>(a, rs);
   }
+  // grid > 0: cooperative launch of that many CTAs (at most) with the atomic
+  // grid barrier; grid < 0: one cluster of -grid CTAs with the hardware
+  // cluster barrier.
   static cudaError_t power_fused(const PowerFusedArgs& a, const Ell& A, int grid, cudaStream_t st) {
     PowerFusedArgs ac = a;
     Ell Ac = A;
+    if (grid < 0) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(-grid);
+      cfg.blockDim = dim3(kReduceBlock);
+      cfg.stream = st;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = -grid;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      return cudaLaunchKernelEx(&cfg, power_fused_kernel<MD, MDu, Z, MIXED, true>, ac, Ac);
+    }
+    cudaError_t e = cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
     void* args[] = {&ac, &Ac};
     const int64_t need = (a.n + kReduceBlock - 1) / kReduceBlock;
     const int g = (int)std::min<int64_t>(grid, std::max<int64_t>(need, 1));
     return cudaLaunchCooperativeKernel((const void*)power_fused_kernel<MD, MDu, Z, MIXED>, dim3(g),
                                        dim3(kReduceBlock), args, 0, st);
+  }
+  // CTAs of one cluster for the single-cluster variant: 16 where the device
+  // takes clusters of 16 (non-portable size), else 8, else 0
+  static int power_cluster_size(int device) {
+    (void)device;
+    auto k = power_fused_kernel<MD, MDu, Z, MIXED, true>;
+    for (int cl : {16, 8}) {
+      if (cl > 8 && cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(cl);
+      cfg.blockDim = dim3(kReduceBlock);
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = cl;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, k, &cfg) == cudaSuccess && nclusters > 0) return cl;
+      cudaGetLastError();
+    }
+    return 0;
   }
   static int power_fused_grid(int device) {
     int per_sm = 0, sms = 0;
@@ -1265,6 +1398,7 @@ struct Kernels {
     ks->tma_grid = &tma_grid;
     ks->power_fused = &power_fused;
     ks->power_fused_grid = &power_fused_grid;
+    ks->power_cluster_size = &power_cluster_size;
   }
 };
 

@@ -155,6 +155,8 @@ struct PowerSArgs {
 struct PowerFusedArgs {
   int64_t n = 0, ld = 0;
   const double* V = nullptr;
+  const float* Vhi = nullptr;          // mixed path: V = hi + lo (then V is not read)
+  const float* Vlo = nullptr;
   const void* Z = nullptr;
   double* vF[2] = {nullptr, nullptr};  // iterate on V: current in [0] at entry
   double* vS[2] = {nullptr, nullptr};  // iterate on the full state (N x ld)
@@ -188,6 +190,7 @@ struct KernelSet {
   int (*tma_grid)(int device, int wmax, int nbuf, int ell) = nullptr;  // grid of the persistent stage kernel (0: not used)
   cudaError_t (*power_fused)(const PowerFusedArgs&, const Ell&, int grid, cudaStream_t) = nullptr;
   int (*power_fused_grid)(int device) = nullptr;
+  int (*power_cluster_size)(int device) = nullptr;  // CTAs of the single-cluster variant (0: unavailable)
 };
 
 // mRKC (mrkc.cu, FP64): one outer stage (stage kernel, inner stage 1) or

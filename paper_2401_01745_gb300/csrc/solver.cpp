@@ -308,11 +308,12 @@ int do_step_rl(emrkc_solver* s, double dt) {
 // Algorithm 5 for rho_F and rho_S in one cooperative launch (emRKC): the
 // iteration loops run on the device; one read of the results.
 int power_fused(emrkc_solver* s) {
-  materialise_V(s);
   PowerFusedArgs a;
   a.n = s->n;
   a.ld = s->ld;
   a.V = s->d_V[s->cur];
+  a.Vhi = s->d_V32[s->cur];  // mixed path: the kernel reads hi + lo (no join launch)
+  a.Vlo = s->d_Vlo[s->cur];
   a.Z = s->d_Z[s->cur];
   a.vF[0] = s->d_vF;
   a.vF[1] = s->d_vF2;
@@ -332,10 +333,13 @@ int power_fused(emrkc_solver* s) {
   a.flags = s->d_flags;
   a.spin_limit = 1ll << 26;
   a.out = s->rs.result;
-  cudaError_t e = cudaMemsetAsync(s->d_pbar, 0, 2 * sizeof(unsigned int), s->stream);
-  if (e != cudaSuccess) return s->cuda_fail(e, "barrier reset");
-  s->launch(EMRKC_PHASE_POWER_S, [&] { e = s->ks.power_fused(a, s->ell, s->pfused_grid, s->stream); });
-  if (e != cudaSuccess) return s->cuda_fail(e, "cooperative power-iteration launch");
+  // problems one cluster holds (at most 4 nodes per thread) take the
+  // single-cluster variant; the others the cooperative grid
+  const int grid = (s->pcluster > 0 && s->n <= (int64_t)4 * s->pcluster * kReduceBlock) ? -s->pcluster
+                                                                                         : s->pfused_grid;
+  cudaError_t e = cudaSuccess;
+  s->launch(EMRKC_PHASE_POWER_S, [&] { e = s->ks.power_fused(a, s->ell, grid, s->stream); });
+  if (e != cudaSuccess) return s->cuda_fail(e, "power-iteration launch");
   int rc = read_results(s, 0, 6);
   if (rc) return rc;
   if ((rc = check_flags(s))) return rc;
@@ -971,6 +975,7 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
   fail |= dalloc(&s->d_flags, 4) != cudaSuccess;
   if (s->method == EMRKC_METHOD_EMRKC) {
     s->pfused_grid = s->ks.power_fused_grid(s->device);
+    s->pcluster = s->ks.power_cluster_size ? s->ks.power_cluster_size(s->device) : 0;
     if (s->pfused_grid > 0) {
       fail |= dalloc(&s->d_ppart, 8 * (int64_t)s->pfused_grid) != cudaSuccess;
       fail |= dalloc(&s->d_pbar, 2) != cudaSuccess;
@@ -1028,6 +1033,14 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
   launch_fill(s->d_act, ld, std::nan(""), s->stream);
   launch_start_vector(o.seed, s->n, ld, (int)rowsF, s->d_vF, s->stream);
   launch_start_vector(~o.seed, s->n, ld, s->N, s->d_vS, s->stream);
+  if (s->precision == EMRKC_PREC_MIXED && s->method == EMRKC_METHOD_EMRKC && s->pfused_grid > 0) {
+    // the fused power iteration of the mixed path keeps its iterates in FP32:
+    // the start vectors rounded into the spare buffers, which become current
+    s->ks.convert_z(rowsF * ld, s->d_vF2, s->d_vF, 0, s->stream);
+    s->ks.convert_z((int64_t)s->N * ld, s->d_vS2, s->d_vS, 0, s->stream);
+    std::swap(s->d_vF, s->d_vF2);
+    std::swap(s->d_vS, s->d_vS2);
+  }
   if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess)
     return bail(EMRKC_ERR_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));
   if ((e = cudaGetLastError()) != cudaSuccess)

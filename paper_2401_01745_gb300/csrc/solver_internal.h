@@ -166,6 +166,7 @@ struct emrkc_solver {
   int pdl = 0;             // mixed path: programmatic dependent launch of the step kernels
   // Algorithm 5 in one cooperative launch (emRKC)
   int pfused_grid = 0;
+  int pcluster = 0;  // CTAs of the single-cluster power iteration (0: not available)
   double* d_ppart = nullptr;      // 2 x 4 x grid partial sums
   unsigned int* d_pbar = nullptr; // grid barrier
   // EXEX-RL / IMEX-RL (rl_methods.cu)
