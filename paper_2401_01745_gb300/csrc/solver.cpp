@@ -47,7 +47,7 @@ void free_all(emrkc_solver* s) {
   s->harvest();
   void* ptrs[] = {s->d_slice_ptr, s->d_width, s->d_col, s->d_val, s->d_val32, s->d_V[0], s->d_V[1], s->d_V[2],
                   s->d_Z[0], s->d_Z[1], s->d_Z[2], s->d_U[0], s->d_U[1], s->d_U[2], s->d_F, s->d_mask, s->d_vF,
-                  s->d_vF2, s->d_vS, s->d_vS2, s->d_fy, s->d_act, s->d_Vn, s->d_tmp, s->d_rest, s->d_flags,
+                  s->d_vF2, s->d_vS, s->d_vS2, s->d_fy, s->d_act, s->d_Vn, s->d_tmp, s->d_rest,
                   s->rs.partials, s->rs.ticket, s->rs.result, s->d_V32[0], s->d_V32[1], s->d_V32[2],
                   s->d_D[0], s->d_D[1], s->d_D[2], s->d_LV, s->d_Vlo[0], s->d_Vlo[1], s->d_Vlo[2],
                   s->d_Vn32, s->d_mass, s->d_cg[0], s->d_cg[1], s->d_cg[2], s->d_cg[3], s->d_cg[4],
@@ -68,13 +68,13 @@ void free_all(emrkc_solver* s) {
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
 }
 
-// Read back reduction results [first, first+count) and the flags word.
+// Read back reduction results [first, first+count) and the flags word in one
+// copy: the flags live right after the 16 result slots (kFlagsSlot).
 int read_results(emrkc_solver* s, int first, int count) {
-  cudaError_t e = cudaMemcpyAsync(s->h_pin + first, s->rs.result + first, count * sizeof(double),
+  (void)count;
+  cudaError_t e = cudaMemcpyAsync(s->h_pin + first, s->rs.result + first, (kFlagsSlot + 1 - first) * sizeof(double),
                                   cudaMemcpyDeviceToHost, s->stream);
   if (e != cudaSuccess) return s->cuda_fail(e, "copy of reduction results");
-  e = cudaMemcpyAsync(s->h_pin + 8, s->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
-  if (e != cudaSuccess) return s->cuda_fail(e, "copy of flags");
   e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return s->cuda_fail(e, "stream synchronisation");
   return EMRKC_OK;
@@ -82,7 +82,7 @@ int read_results(emrkc_solver* s, int first, int count) {
 
 int check_flags(emrkc_solver* s) {
   int flags = 0;
-  std::memcpy(&flags, s->h_pin + 8, sizeof(int));
+  std::memcpy(&flags, s->h_pin + kFlagsSlot, sizeof(int));
   if (flags & 1) {
     int zero = 0;
     cudaMemcpyAsync(s->d_flags, &zero, sizeof(int), cudaMemcpyHostToDevice, s->stream);
@@ -602,7 +602,7 @@ int do_step(emrkc_solver* s, double dt) {
 }
 
 int sync_and_check(emrkc_solver* s) {
-  cudaError_t e = cudaMemcpyAsync(s->h_pin + 8, s->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+  cudaError_t e = cudaMemcpyAsync(s->h_pin + kFlagsSlot, s->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
   if (e != cudaSuccess) return s->cuda_fail(e, "copy of flags");
   e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return s->cuda_fail(e, "stream synchronisation");
@@ -972,7 +972,6 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
   fail |= dalloc(&s->d_Vn, ld) != cudaSuccess;
   fail |= dalloc(&s->d_tmp, (int64_t)std::max(1, s->N - 1) * ld) != cudaSuccess;
   fail |= dalloc(&s->d_rest, 64) != cudaSuccess;
-  fail |= dalloc(&s->d_flags, 4) != cudaSuccess;
   if (s->method == EMRKC_METHOD_EMRKC) {
     s->pfused_grid = s->ks.power_fused_grid(s->device);
     s->pcluster = s->ks.power_cluster_size ? s->ks.power_cluster_size(s->device) : 0;
@@ -983,7 +982,9 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
   }
   fail |= dalloc(&s->rs.partials, kReduceMaxBlocks) != cudaSuccess;
   fail |= dalloc(&s->rs.ticket, 4) != cudaSuccess;
-  fail |= dalloc(&s->rs.result, 16) != cudaSuccess;
+  // 16 result slots, then the flags words (kFlagsSlot): one copy reads both
+  fail |= dalloc(&s->rs.result, kFlagsSlot + 2) != cudaSuccess;
+  if (s->rs.result) s->d_flags = reinterpret_cast<int*>(s->rs.result + kFlagsSlot);
   if (s->method == EMRKC_METHOD_IMEX_RL) {
     s->pcg_grid = pcg_grid(s->device);
     fail |= s->pcg_grid <= 0;
@@ -1003,8 +1004,8 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
     cudaMemsetAsync(s->d_iters, 0, 2 * sizeof(unsigned long long), s->stream);
     cudaMemsetAsync(s->d_res, 0, 2 * sizeof(double), s->stream);
   }
-  if ((e = cudaMallocHost(&s->h_pin, 16 * sizeof(double))) != cudaSuccess) return bail(EMRKC_ERR_OOM, "pinned allocation failed");
-  std::memset(s->h_pin, 0, 16 * sizeof(double));
+  if ((e = cudaMallocHost(&s->h_pin, 32 * sizeof(double))) != cudaSuccess) return bail(EMRKC_ERR_OOM, "pinned allocation failed");
+  std::memset(s->h_pin, 0, 32 * sizeof(double));
   if (stim && stim->node_mask) {
     if ((e = dalloc(&s->d_mask, ld)) != cudaSuccess) return bail(EMRKC_ERR_OOM, "device allocation failed");
     cudaMemsetAsync(s->d_mask, 0, ld, s->stream);

@@ -88,6 +88,9 @@ inline std::vector<double> rest_state(int model) {
   }
 }
 
+// slot of rs.result (in doubles) where the flags words start
+constexpr int kFlagsSlot = 16;
+
 struct Timing {
   int cls;
   cudaEvent_t a, b;
