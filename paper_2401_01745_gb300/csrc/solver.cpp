@@ -613,27 +613,36 @@ int sync_and_check(emrkc_solver* s) {
 int build_matrix(emrkc_solver* s, const emrkc_matrix* m) {
   const int64_t n = m->n;
   const bool mixed = s->precision == EMRKC_PREC_MIXED;
-  std::vector<std::vector<std::pair<int32_t, double>>> rows(n);
-  for (int64_t i = 0; i < n; ++i) {
+  // L = -(chi Cm M)^-1 K row by row; entries at or below 1e-14 |K_ii| off the
+  // diagonal are dropped, the diagonal is dropped in the mixed path (its
+  // rows sum to zero).  Two passes over the CSR rows (count, then fill the
+  // sliced ELL in CSR order), parallel over rows and slices.
+  auto keep = [&](int64_t i, int64_t p, double drop) {
+    const int32_t c = m->col[p];
+    if (c != i && std::fabs(m->K[p]) <= drop) return false;
+    if (mixed && c == i) return false;
+    return true;
+  };
+  auto drop_of = [&](int64_t i) {
     double kii = 0.0;
     for (int64_t p = m->row_ptr[i]; p < m->row_ptr[i + 1]; ++p)
       if (m->col[p] == i) kii += m->K[p];
-    const double scale = -1.0 / (s->chi * s->Cm * m->lumped_mass[i]);
-    const double drop = 1e-14 * std::fabs(kii);
-    for (int64_t p = m->row_ptr[i]; p < m->row_ptr[i + 1]; ++p) {
-      const int32_t c = m->col[p];
-      const double k = m->K[p];
-      if (c != i && std::fabs(k) <= drop) continue;
-      if (mixed && c == i) continue;
-      rows[i].push_back({c, k * scale});
-    }
+    return 1e-14 * std::fabs(kii);
+  };
+  std::vector<int32_t> cnt(n, 0);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    const double drop = drop_of(i);
+    int c = 0;
+    for (int64_t p = m->row_ptr[i]; p < m->row_ptr[i + 1]; ++p) c += keep(i, p, drop) ? 1 : 0;
+    cnt[i] = c;
   }
   const int64_t ns = (n + 31) / 32;
   std::vector<int64_t> sptr(ns + 1, 0);
   std::vector<int32_t> width(ns, 0);
   for (int64_t b = 0; b < ns; ++b) {
     int w = 0;
-    for (int64_t i = b * 32; i < std::min<int64_t>(n, b * 32 + 32); ++i) w = std::max<int>(w, (int)rows[i].size());
+    for (int64_t i = b * 32; i < std::min<int64_t>(n, b * 32 + 32); ++i) w = std::max<int>(w, cnt[i]);
     width[b] = w;
     sptr[b + 1] = sptr[b] + (int64_t)w * 32;
   }
@@ -642,24 +651,29 @@ int build_matrix(emrkc_solver* s, const emrkc_matrix* m) {
   s->ell_wmax = 0;
   for (int64_t b = 0; b < ns; ++b) s->ell_wmax = std::max<int>(s->ell_wmax, width[b]);
   s->mat_entries = 0;
-  for (int64_t i = 0; i < n; ++i) s->mat_entries += (int64_t)rows[i].size();
+  for (int64_t i = 0; i < n; ++i) s->mat_entries += cnt[i];
   std::vector<int32_t> col(std::max<int64_t>(total, 1), 0);
   std::vector<double> val(mixed ? 0 : std::max<int64_t>(total, 1), 0.0);
   std::vector<float> val32(mixed ? std::max<int64_t>(total, 1) : 0, 0.0f);
+#pragma omp parallel for schedule(static)
   for (int64_t b = 0; b < ns; ++b) {
     for (int l = 0; l < 32; ++l) {
       const int64_t i = b * 32 + l;
       const int32_t pad_col = (int32_t)std::min<int64_t>(i, n - 1);
-      for (int k = 0; k < width[b]; ++k) {
-        const int64_t p = sptr[b] + (int64_t)k * 32 + l;
-        if (i < n && k < (int)rows[i].size()) {
-          col[p] = rows[i][k].first;
-          if (mixed) val32[p] = (float)rows[i][k].second;
-          else val[p] = rows[i][k].second;
-        } else {
-          col[p] = pad_col;
+      int k = 0;
+      if (i < n) {
+        const double drop = drop_of(i);
+        const double scale = -1.0 / (s->chi * s->Cm * m->lumped_mass[i]);
+        for (int64_t q = m->row_ptr[i]; q < m->row_ptr[i + 1]; ++q) {
+          if (!keep(i, q, drop)) continue;
+          const int64_t p = sptr[b] + (int64_t)k * 32 + l;
+          col[p] = m->col[q];
+          if (mixed) val32[p] = (float)(m->K[q] * scale);
+          else val[p] = m->K[q] * scale;
+          ++k;
         }
       }
+      for (; k < width[b]; ++k) col[sptr[b] + (int64_t)k * 32 + l] = pad_col;
     }
   }
   cudaError_t e;
@@ -711,15 +725,19 @@ int validate_matrix(const emrkc_matrix* m, std::string* why) {
       return EMRKC_ERR_ARG;
     }
   }
+  int64_t bad_col = 0, bad_val = 0;
+#pragma omp parallel for schedule(static) reduction(+ : bad_col, bad_val)
   for (int64_t p = 0; p < m->nnz; ++p) {
-    if (m->col[p] < 0 || m->col[p] >= m->n) {
-      *why = "matrix: column index out of range";
-      return EMRKC_ERR_ARG;
-    }
-    if (!std::isfinite(m->K[p])) {
-      *why = "matrix: non-finite entry";
-      return EMRKC_ERR_ARG;
-    }
+    bad_col += (m->col[p] < 0 || m->col[p] >= m->n) ? 1 : 0;
+    bad_val += std::isfinite(m->K[p]) ? 0 : 1;
+  }
+  if (bad_col) {
+    *why = "matrix: column index out of range";
+    return EMRKC_ERR_ARG;
+  }
+  if (bad_val) {
+    *why = "matrix: non-finite entry";
+    return EMRKC_ERR_ARG;
   }
   return EMRKC_OK;
 }
