@@ -993,6 +993,8 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
   if (s->method == EMRKC_METHOD_EMRKC) {
     s->pfused_grid = s->ks.power_fused_grid(s->device);
     s->pcluster = s->ks.power_cluster_size ? s->ks.power_cluster_size(s->device) : 0;
+    const char* no_cluster = std::getenv("EMRKC_NO_CLUSTER");
+    if (no_cluster && no_cluster[0] == '1') s->pcluster = 0;
     if (s->pfused_grid > 0) {
       fail |= dalloc(&s->d_ppart, 8 * (int64_t)s->pfused_grid) != cudaSuccess;
       fail |= dalloc(&s->d_pbar, 2) != cudaSuccess;

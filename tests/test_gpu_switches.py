@@ -62,3 +62,30 @@ def test_switches_same_result(case, monkeypatch, env):
     assert (st1["s"], st1["m"]) == (st0["s"], st0["m"])
     assert np.linalg.norm(V1 - V0) <= 1e-6 * np.linalg.norm(V0)
     assert np.linalg.norm(V1 - Vo) <= 1e-3 * np.linalg.norm(Vo)
+
+
+@pytest.mark.parametrize("prec", [pkg.PREC_MIXED, pkg.PREC_FP64])
+def test_power_iteration_cluster_matches_grid(monkeypatch, prec):
+    """Problems of at most 16k nodes run Algorithm 5 in one thread-block
+    cluster (hardware cluster barrier); EMRKC_NO_CLUSTER=1 forces the
+    cooperative grid.  The two differ only in how partial sums are grouped."""
+    w = make_workload("slab41x15x7_ttp")
+    out = []
+    for env in ({}, {"EMRKC_NO_CLUSTER": "1"}):
+        for k, v in env.items():
+            monkeypatch.setenv(k, v)
+        sol = pkg.Solver.from_workload(w, precision=prec, rho_every=1, seed=5)
+        for _ in range(10):
+            sol.step(w.dt)
+        rF, rS, itF, itS = sol.estimate_rho()
+        V = sol.get_state(var=0)
+        sol.close()
+        out.append((rF, rS, itF, itS, V))
+    (a, b) = out
+    # FP64 path: FP64 sums, grouping changes the last bits; mixed path: FP32
+    # per-thread and per-CTA sums, grouping changes ~1e-7 of each sum
+    tol = 1e-9 if prec == pkg.PREC_FP64 else 1e-4
+    assert abs(a[2] - b[2]) <= 1 and abs(a[3] - b[3]) <= 1
+    assert a[0] == pytest.approx(b[0], rel=tol)
+    assert a[1] == pytest.approx(b[1], rel=tol)
+    assert np.linalg.norm(a[4] - b[4]) <= 1e-12 * np.linalg.norm(b[4])
