@@ -19,10 +19,14 @@
  *    code.  A human-readable message is available from emrkc_last_error().
  *  - Host pointers passed in are read during the call only; the library
  *    copies what it keeps (ownership stays with the caller).  Host output
- *    buffers are allocated by the caller.
+ *    buffers are allocated by the caller.  Exception: the buffers of
+ *    emrkc_set_stimulus_async and emrkc_get_state_async stay in use until
+ *    emrkc_sync returns.
  *  - The solver owns all device memory it allocates and frees it in
  *    emrkc_destroy().  All device work is ordered on the solver's CUDA
- *    stream (options.cuda_stream, or a stream the solver creates).
+ *    stream (options.cuda_stream, or a stream the solver creates); the
+ *    copies of the *_async calls run on two copy streams of the solver,
+ *    ordered against that stream by events.
  *  - Units: cm, ms, mV, mS/cm, uF/cm^2, uA/cm^2.
  *  - The state is structure-of-arrays: variable 0 is V, variables 1..nE the
  *    gating variables z_E, the remaining ones z_S (see emrkc_num_vars()).
