@@ -807,28 +807,22 @@ __device__ __forceinline__ float block_sum_f(float v, float* sh) {
 }
 
 // Sum of column c (stride 4) of nb per-CTA partials, in the same fixed order
-// in every CTA, so that every CTA takes the same scalar.  Up to 32 partials
-// (a single cluster, small grids) one warp adds them.
+// in every CTA, so that every CTA takes the same scalar.  One warp adds them
+// (lane l takes partials l, l + 32, ..., then a shuffle tree) and shares the
+// sum: FP64 arithmetic is narrow on GB300, so the other warps do none of it.
 __device__ __forceinline__ double sum_partials(const double* part, int nb, int c, double* sh) {
-  if (nb <= 32) {
-    __shared__ double s_w;
-    if (threadIdx.x < 32) {
-      double v = (int)threadIdx.x < nb ? __ldcg(part + 4 * threadIdx.x + c) : 0.0;
-      v = warp_sum(v);
-      if (threadIdx.x == 0) s_w = v;
-    }
-    __syncthreads();
-    const double r = s_w;
-    __syncthreads();
-    return r;
+  (void)sh;
+  __shared__ double s_w;
+  if (threadIdx.x < 32) {
+    double v = 0.0;
+    for (int k = threadIdx.x; k < nb; k += 32) v += __ldcg(part + 4 * k + c);
+    v = warp_sum(v);
+    if (threadIdx.x == 0) s_w = v;
   }
-  double acc = 0.0;
-  for (int k = threadIdx.x; k < nb; k += blockDim.x) acc += __ldcg(part + 4 * k + c);
-  const double t = block_sum(acc, sh);
-  __shared__ double s_t;
-  if (threadIdx.x == 0) s_t = t;
   __syncthreads();
-  return s_t;
+  const double r = s_w;
+  __syncthreads();
+  return r;
 }
 
 inline int reduce_grid(int64_t count) {
