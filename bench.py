@@ -44,7 +44,7 @@ NCU_TRAFFIC = {"kernel": "stage_kernel_mixed_tma<ModelTTP06<float>, false>", "wo
                "bytes_per_launch": 55196672 + 2728192,
                "sources": ("paper_2401_01745_gb300/csrc/kernels.cuh", "paper_2401_01745_gb300/csrc/models.cuh",
                            "paper_2401_01745_gb300/csrc/kernels_mixed.cu"),
-               "sha256": "05fb6b39caf3eb059d3e4cef07d7db0d58a9720e3bb459896630ee5309d92ad5"}
+               "sha256": "7b835c38f2679ecfed7de52da95acfcc18eee136ec9a1f253d49d19701f43266"}
 
 
 def _sources_sha256(paths):

@@ -336,19 +336,21 @@ __global__ void __launch_bounds__(128) stage_kernel_mixed(const StageArgs a, con
 }
 
 // ---------------------------------------------------------------------------
-// Persistent, bulk-copy pipelined variant of the mixed stage kernel.
+// Persistent, bulk-copy variant of the mixed stage kernel.
 //
 // A CTA of 128 threads owns tiles of 128 consecutive nodes (tile, tile + G,
-// tile + 2G, ...).  One elected thread streams the next tiles' inputs (the
-// NZ rows of z, V hi and the stimulus mask: contiguous 512-byte / 128-byte
-// segments of the SoA arrays) into a double-buffered shared-memory stage
-// with cp.async.bulk completing on an mbarrier, while all threads compute
-// the current tile from shared memory.  Memory-level parallelism then no
-// longer depends on how many warps the register budget of the ionic model
-// leaves resident.  The sparse row and the neighbour gathers use ordinary
-// read-only loads.  Waits are bounded: after kTmaSpinLimit polls a CTA
-// records bit 1 in flags, waits (bounded) for its copies in flight and
-// returns.
+// tile + 2G, ...).  One elected thread copies a tile's inputs (the NZ rows of
+// z, V hi and the stimulus mask: contiguous 512-byte / 128-byte segments of
+// the SoA arrays, and the tile's four sliced-ELL slices when rows have at
+// most kTmaStageEllWidth entries) into a shared-memory stage buffer with
+// cp.async.bulk completing on an mbarrier; the slices' offsets and widths go
+// to shared memory with them.  One buffer per CTA by default (more CTAs per
+// SM), two on request (the next tile's copy overlaps the current tile).
+// The first tile's ELL slices are requested before griddepcontrol.wait, L
+// being constant.  Each node issues its neighbour gathers (ordinary
+// read-only loads) before its ionic model.  Waits are bounded: after
+// kTmaSpinLimit polls a CTA records bit 1 in flags, waits (bounded) for its
+// copies in flight and returns.
 constexpr int kTmaTile = 128;
 constexpr int kTmaStageEllWidth = 8;  // rows of at most this many entries are staged too
 constexpr long long kTmaSpinLimit = 1ll << 26;
