@@ -44,7 +44,7 @@ NCU_TRAFFIC = {"kernel": "stage_kernel_mixed_tma<ModelTTP06<float>, false>", "wo
                "bytes_per_launch": 55196672 + 2728192,
                "sources": ("paper_2401_01745_gb300/csrc/kernels.cuh", "paper_2401_01745_gb300/csrc/models.cuh",
                            "paper_2401_01745_gb300/csrc/kernels_mixed.cu"),
-               "sha256": "7b835c38f2679ecfed7de52da95acfcc18eee136ec9a1f253d49d19701f43266"}
+               "sha256": "495c811ad7114dec47e47a89215d5ac27960068f4b38d6c6420266d119c0aa2e"}
 
 
 def _sources_sha256(paths):

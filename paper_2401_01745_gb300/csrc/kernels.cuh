@@ -986,13 +986,6 @@ __global__ void convert_kernel(int64_t count, const void* src, double* dst, int 
 // Host-side launch helpers shared by the per-precision translation units.
 inline unsigned blocks_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
 
-// Algorithm 5 for rho_F and rho_S in one cooperative launch: the iteration
-// loops run on the device (every CTA takes the same scalars from the same
-// partial sums, so all take the same branches) and the host reads the two
-// estimates once.  FP64 path: the differences f(y + q v) - f(y) of Algorithm
-// 5; mixed path: q J v (q L v for f_F, dual numbers for f_S).  Iterates
-// ping-pong between two buffers per estimate; out[4], out[5] say which holds
-// the last one.
 // Barrier between the phases of power_fused_kernel.  CLUSTER: the grid is
 // one thread-block cluster, and the hardware cluster barrier (release /
 // acquire at cluster scope, which covers the partial sums in global memory)
@@ -1009,12 +1002,20 @@ __device__ __forceinline__ bool power_barrier(const PowerFusedArgs& a) {
   }
 }
 
+// Algorithm 5 for rho_F and rho_S in one persistent launch (a cooperative
+// grid, or one thread-block cluster for small problems): the iteration
+// loops run on the device (every CTA takes the same scalars from the same
+// partial sums, so all take the same branches) and the host reads the two
+// estimates once.  FP64 path: the differences f(y + q v) - f(y) of Algorithm
+// 5; mixed path: q J v (q L v for f_F, dual numbers for f_S).  Iterates
+// ping-pong between two buffers per estimate; out[4], out[5] say which holds
+// the last one.
 template <class MD, class MDu, typename Z, bool MIXED, bool CLUSTER = false>
 __global__ void __launch_bounds__(kReduceBlock) power_fused_kernel(const PowerFusedArgs a, const Ell A) {
   constexpr int NE = MD::NE, NS = MD::NS, N = 1 + NE + NS;
-  // Mixed path: iterates and per-thread sums in FP32 (GB300's FP64 pipe is a
-  // small fraction of its FP32 rate), block and grid sums and the scalars
-  // of Algorithm 5 in FP64.  FP64 path: everything in FP64.
+  // Mixed path: iterates, per-thread and per-CTA sums in FP32 (GB300's FP64
+  // pipe is a small fraction of its FP32 rate); the grid sums and the
+  // scalars of Algorithm 5 in FP64.  FP64 path: everything in FP64.
   using VT = typename std::conditional<MIXED, float, double>::type;
   __shared__ double sh[32];
   __shared__ float shf[32];
