@@ -83,6 +83,37 @@ def test_rush_larsen_exact_for_frozen_V(model_id, V):
     np.testing.assert_array_equal(YE[1 + prob.nE:], Y[1 + prob.nE:])
 
 
+def test_hh_single_cell_action_potential():
+    """Textbook features of the 1952 Hodgkin-Huxley membrane action potential
+    (6.3 C, rest at V_rest): an overshooting spike of about 100 mV amplitude,
+    about 1-2 ms wide at half amplitude, followed by an after-hyperpolarisation
+    that approaches but never crosses the potassium reversal potential
+    E_K = V_rest - 12 mV, then recovery toward rest."""
+    hh = HHModel()
+    w = make_workload("line2_hh", length=0.001)
+    w.stim_mask[:] = 1
+    w.stim_amp = 20.0
+    w.t_on, w.t_off = 0.0, 0.5
+    prob = Monodomain.from_workload(w)
+    r = OracleRun(prob, rho_every=1)
+    dt = 0.01
+    V = []
+    for _ in range(2000):
+        r.step(dt)
+        V.append(r.Y[0, 0])
+    V = np.array(V)
+    t = dt * np.arange(1, V.size + 1)
+    rest, E_K = hh.V_rest, hh.V_rest - 12.0
+    amp = V.max() - rest
+    assert 90.0 < amp < 115.0
+    assert V.max() > 0.0  # overshoot
+    above = t[V > rest + 0.5 * amp]
+    assert 0.8 < above.max() - above.min() < 2.5
+    undershoot = V[t > t[V.argmax()]].min()
+    assert E_K < undershoot < rest - 5.0
+    assert abs(V[-1] - rest) < 2.0
+
+
 def test_table2_hh_stiffness():
     """rho_S of HH over an action potential peaks near Table 2's rho_max = 40."""
     rows = {r[0]: (int(r[1]), float(r[2])) for r in _read("table2_stiffness.txt")}
