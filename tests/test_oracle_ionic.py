@@ -163,8 +163,9 @@ def test_ttp_rest_state_nearly_stationary():
 @pytest.mark.slow
 def test_ttp_single_cell_action_potential():
     """Published TTP06 epicardial characteristics: rest near -85 mV, upstroke
-    velocity of a few hundred mV/ms, APD90 near 300 ms (parity of the model
-    beyond these features is unpinned)."""
+    velocity of a few hundred mV/ms, APD90 near 300 ms, the epicardial
+    spike-and-dome shape and a calcium transient peaking near 1 uM (parity of
+    the model beyond these features is unpinned)."""
     w = make_workload("line2_ttp", length=0.001)
     w.stim_mask[:] = 1
     w.stim_amp = 52.0
@@ -172,11 +173,12 @@ def test_ttp_single_cell_action_potential():
     prob = Monodomain.from_workload(w)
     r = OracleRun(prob, rho_every=1)
     dt = 0.1
-    V = []
+    V, Cai = [], []
     for _ in range(4000):
         r.step(dt)
         V.append(r.Y[0, 0])
-    V = np.array(V)
+        Cai.append(r.Y[1 + 12 + 3, 0])  # z_S = (Rbar, Ki, Nai, Cai, CaSR, CaSS)
+    V, Cai = np.array(V), np.array(Cai)
     t = dt * np.arange(1, V.size + 1)
     assert -87.0 < V[-1] < -83.0
     assert 10.0 < V.max() < 80.0
@@ -186,6 +188,20 @@ def test_ttp_single_cell_action_potential():
     after = (t > t[V.argmax()]) & (V < -85.23 + 0.1 * amp)
     apd90 = t[np.nonzero(after)[0][0]]
     assert 240.0 < apd90 < 360.0
+    # epicardial spike-and-dome (transient outward current I_to): a notch
+    # within 30 ms of the peak, then a dome several mV above it
+    ip = int(V.argmax())
+    early = V[ip:ip + int(30 / dt)]
+    notch = int(early.argmin())
+    dome = V[ip + notch:ip + int(150 / dt)].max()
+    assert early.min() < V.max() - 10.0
+    assert dome > early.min() + 3.0
+    # calcium transient: from ~0.1 uM at rest to a peak near 1 uM tens of ms
+    # after the upstroke, back toward rest by the end of the beat
+    assert 0.05e-3 < Cai[0] < 0.3e-3
+    assert 0.4e-3 < Cai.max() < 2.0e-3
+    assert 5.0 < t[Cai.argmax()] - t[ip] < 80.0
+    assert Cai[-1] < 0.3e-3
 
 
 def test_passive_model_linear():
