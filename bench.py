@@ -38,13 +38,13 @@ import numpy as np  # noqa: E402
 
 # DRAM traffic of the dominant kernel from one ncu capture of the headline
 # workload (dram__bytes_read.sum + dram__bytes_write.sum of one launch; the
-# command is in profiles/stage_kernel_mixed_tma_slab_ttp.md).  Reported only
+# command is in profiles/stage_kernel_mixed_tma_pf_slab_ttp.md).  Reported only
 # while the kernel sources hash to the captured state.
-NCU_TRAFFIC = {"kernel": "stage_kernel_mixed_tma<ModelTTP06<float>, false>", "workload": "slab_ttp",
-               "bytes_per_launch": 55196672 + 2728192,
+NCU_TRAFFIC = {"kernel": "stage_kernel_mixed_tma_pf<ModelTTP06<float>, false>", "workload": "slab_ttp",
+               "bytes_per_launch": 55202816 + 1882880,
                "sources": ("paper_2401_01745_gb300/csrc/kernels.cuh", "paper_2401_01745_gb300/csrc/models.cuh",
                            "paper_2401_01745_gb300/csrc/kernels_mixed.cu"),
-               "sha256": "495c811ad7114dec47e47a89215d5ac27960068f4b38d6c6420266d119c0aa2e"}
+               "sha256": "309de6ecbdf410129a4e51c0110d328bc797c33c48170875b76e4a91e16794e7"}
 
 
 def _sources_sha256(paths):

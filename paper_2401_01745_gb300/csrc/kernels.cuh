@@ -405,29 +405,22 @@ __host__ __device__ constexpr int tma_stage_bytes(int nz, int wmax) {
 __host__ __device__ constexpr int tma_smem_bytes(int nz, int wmax, int ell) {
   return ell ? tma_stage_bytes(nz, wmax) : tma_fixed_bytes(nz);
 }
+// prefetching variant: one state region and two ELL buffers
+__host__ __device__ constexpr int tma_pf_smem_bytes(int nz, int wmax) {
+  return tma_fixed_bytes(nz) + 2 * (2 * 4 * wmax * 32 * 4);
+}
 
-// One node of an outer stage (mixed path) from a shared-memory stage buffer
-// holding the tile's z rows, V hi and stimulus mask (kTmaTile entries each):
-// the body of the bulk-copy stage kernels.  scol/sval/base locate the row in
-// a staged sliced-ELL tile, or scol = nullptr to read the row from global.
+// The outputs of one node of a mixed outer stage from its inputs in
+// registers: z, V hi, the stimulus bit, and the neighbour values xv of a
+// staged row (w entries at base + 32 k of the staged values sval), or
+// sval = nullptr to take the row from global memory.
 template <class Model, bool HAS_M2>
-__device__ __forceinline__ void stage_node_staged(const StageArgs& a, const Ell& A, const int64_t i, const int tid,
-                                                  const float* sz, const int32_t* scol, const float* sval,
-                                                  const int base, const int w) {
+__device__ __forceinline__ void stage_node_core(const StageArgs& a, const Ell& A, const int64_t i,
+                                                const float (&z)[(Model::NE + Model::NS) > 0 ? Model::NE + Model::NS : 1],
+                                                const float V, const unsigned char mk,
+                                                const float (&xv)[kTmaStageEllWidth], const int w, const float* sval,
+                                                const int base) {
   constexpr int NE = Model::NE, NS = Model::NS, NZ = NE + NS;
-  float z[NZ > 0 ? NZ : 1];
-#pragma unroll
-  for (int k = 0; k < NZ; ++k) z[k] = sz[k * kTmaTile + tid];
-  const float V = sz[NZ * kTmaTile + tid];
-  const unsigned char mk = reinterpret_cast<const unsigned char*>(sz + (NZ + 1) * kTmaTile)[tid];
-  // neighbour values of the staged row first: the gathers are in flight
-  // while the ionic model runs
-  float xv[kTmaStageEllWidth];
-  if (scol != nullptr) {
-#pragma unroll
-    for (int k = 0; k < kTmaStageEllWidth; ++k)
-      if (k < w) xv[k] = __ldg(a.V32m1 + scol[base + 32 * k]);
-  }
   float dz[NE > 0 ? NE : 1];
   float Iion;
   float gS[NS > 0 ? NS : 1];
@@ -451,7 +444,7 @@ __device__ __forceinline__ void stage_node_staged(const StageArgs& a, const Ell&
   }
   // sparse row: slot k of row i at base + 32 k in the staged tile
   float LV = 0.0f;
-  if (scol == nullptr) {
+  if (sval == nullptr) {
     LV = ell_diff32<false>(A, i, a.V32m1);
   } else {
 #pragma unroll
@@ -473,6 +466,31 @@ __device__ __forceinline__ void stage_node_staged(const StageArgs& a, const Ell&
     a.D1[i] = a.f_mu1eta * (LV + F);
     if (a.LV != nullptr) a.LV[i] = LV + F;  // kept for inner stages k >= 4 only
   }
+}
+
+// One node of an outer stage (mixed path) from a shared-memory stage buffer
+// holding the tile's z rows, V hi and stimulus mask (kTmaTile entries each):
+// the body of the bulk-copy stage kernel.  scol/sval/base/w locate the row in
+// a staged sliced-ELL tile, or scol = nullptr to read the row from global.
+template <class Model, bool HAS_M2>
+__device__ __forceinline__ void stage_node_staged(const StageArgs& a, const Ell& A, const int64_t i, const int tid,
+                                                  const float* sz, const int32_t* scol, const float* sval,
+                                                  const int base, const int w) {
+  constexpr int NZ = Model::NE + Model::NS;
+  float z[NZ > 0 ? NZ : 1];
+#pragma unroll
+  for (int k = 0; k < NZ; ++k) z[k] = sz[k * kTmaTile + tid];
+  const float V = sz[NZ * kTmaTile + tid];
+  const unsigned char mk = reinterpret_cast<const unsigned char*>(sz + (NZ + 1) * kTmaTile)[tid];
+  // neighbour values of the staged row first: the gathers are in flight
+  // while the ionic model runs
+  float xv[kTmaStageEllWidth];
+  if (scol != nullptr) {
+#pragma unroll
+    for (int k = 0; k < kTmaStageEllWidth; ++k)
+      if (k < w) xv[k] = __ldg(a.V32m1 + scol[base + 32 * k]);
+  }
+  stage_node_core<Model, HAS_M2>(a, A, i, z, V, mk, xv, w, scol != nullptr ? sval : nullptr, base);
 }
 
 template <class Model, bool HAS_M2>
@@ -596,6 +614,132 @@ __global__ void __launch_bounds__(kTmaTile) stage_kernel_mixed_tma(const StageAr
   // buffer whose wait gave up, and the other one if its tile was issued)
   if (s_abort && tid == 0) {
     for (int b = 0; b < nb; ++b) {
+      long long spins = 0;
+      while (!mbar_try_wait(b ? bar1 : bar0, phase[b]) && ++spins < kTmaSpinLimit) {
+      }
+    }
+  }
+}
+
+// Bulk-copy stage kernel with the next tile prefetched during compute (rows
+// of at most kTmaStageEllWidth entries only).  Shared memory: one state
+// region (z rows, V hi, mask) and two ELL buffers.  Each thread first moves
+// its node's state from shared memory into registers and issues its
+// neighbour gathers; after a CTA barrier the state region is free, and the
+// elected thread requests the next tile's state and ELL slices (into the
+// other ELL buffer) while all threads compute the current tile.  So one
+// tile is always in flight per CTA at the shared-memory cost of one state
+// buffer.  Waits are bounded as in stage_kernel_mixed_tma.
+template <class Model, bool HAS_M2>
+__global__ void __launch_bounds__(kTmaTile) stage_kernel_mixed_tma_pf(const StageArgs a, const Ell A) {
+  constexpr int NE = Model::NE, NS = Model::NS, NZ = NE + NS;
+  constexpr int FB = tma_fixed_bytes(NZ);
+  const int EB = 2 * 4 * a.ell_wmax * 32 * 4;  // one ELL buffer: columns, then values
+  const int64_t nslices = A.n_slices;
+  extern __shared__ __align__(128) unsigned char tma_smem[];
+  __shared__ __align__(8) unsigned long long bars[2];
+  __shared__ int s_abort;
+  __shared__ int s_roff[2][kTmaTile / 32];
+  __shared__ int s_rw[2][kTmaTile / 32];
+  const int tid = threadIdx.x;
+  const int64_t ntiles = (a.n + kTmaTile - 1) / kTmaTile;
+  const int64_t G = gridDim.x;
+  const unsigned bar0 = smem_u32(&bars[0]), bar1 = smem_u32(&bars[1]);
+  const unsigned base_s = smem_u32(tma_smem);
+
+  auto issue_ell = [&](int64_t tile, int e) {
+    const unsigned bar = e ? bar1 : bar0;
+    const unsigned dst = base_s + FB + e * EB;
+    const int64_t s0 = tile * (kTmaTile / 32);
+    const int64_t s1 = (s0 + kTmaTile / 32 < nslices) ? s0 + kTmaTile / 32 : nslices;
+    const int64_t e0 = __ldg(A.slice_ptr + s0), e1 = __ldg(A.slice_ptr + s1);
+#pragma unroll
+    for (int q = 0; q < kTmaTile / 32; ++q) {
+      const bool in = s0 + q < s1;
+      s_roff[e][q] = in ? (int)(__ldg(A.slice_ptr + s0 + q) - e0) : 0;
+      s_rw[e][q] = in ? __ldg(A.width + s0 + q) : 0;
+    }
+    const unsigned ell_bytes = (unsigned)((e1 - e0) * 4);
+    if (ell_bytes == 0) return;
+    mbar_expect_tx_only(bar, 2u * ell_bytes);
+    bulk_g2s(dst, A.col + e0, ell_bytes, bar);
+    bulk_g2s(dst + (unsigned)(EB / 2), A.val32 + e0, ell_bytes, bar);
+  };
+  auto issue_state = [&](int64_t tile, int e) {
+    const unsigned bar = e ? bar1 : bar0;
+    const int64_t off = tile * kTmaTile;
+    mbar_expect_tx(bar, (unsigned)FB);
+    const float* Zm1 = static_cast<const float*>(a.Zm1);
+#pragma unroll 1
+    for (int k = 0; k < NZ; ++k) bulk_g2s(base_s + k * kTmaTile * 4, Zm1 + k * a.ld + off, kTmaTile * 4, bar);
+    bulk_g2s(base_s + NZ * kTmaTile * 4, a.V32m1 + off, kTmaTile * 4, bar);
+    bulk_g2s(base_s + (NZ + 1) * kTmaTile * 4, a.mask + off, kTmaTile, bar);
+  };
+
+  if (tid == 0) {
+    mbar_init(bar0, 1);
+    mbar_init(bar1, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+  }
+  __syncthreads();
+  pdl_trigger();
+  const bool run = a.mask != nullptr;  // the mask is copied with the state
+  const int64_t first = blockIdx.x;
+  if (tid == 0 && run && first < ntiles) issue_ell(first, 0);
+  pdl_wait();
+  if (!run) return;
+  if (tid == 0 && first < ntiles) issue_state(first, 0);
+  unsigned phase[2] = {0u, 0u};
+  const float* sz = reinterpret_cast<const float*>(tma_smem);
+  int it = 0;
+  for (int64_t tile = first; tile < ntiles; tile += G, ++it) {
+    const int e = it & 1;
+    const unsigned bar = e ? bar1 : bar0;
+    long long spins = 0;
+    bool ok = true;
+    while (!mbar_try_wait(bar, phase[e])) {
+      if (++spins > kTmaSpinLimit) {
+        atomicOr(a.flags, 2);
+        s_abort = 1;
+        ok = false;
+        break;
+      }
+    }
+    if (ok) phase[e] ^= 1u;
+    __syncthreads();
+    if (s_abort) break;
+    // inputs of this thread's node into registers; gathers issued
+    const int64_t i = tile * kTmaTile + tid;
+    const bool live = i < a.n;
+    float z[NZ > 0 ? NZ : 1];
+    float V = 0.0f;
+    unsigned char mk = 0;
+    float xv[kTmaStageEllWidth];
+    const int base = s_roff[e][tid >> 5] + (tid & 31);
+    const int w = s_rw[e][tid >> 5];
+    const int32_t* scol = reinterpret_cast<const int32_t*>(tma_smem + FB + e * EB);
+    const float* sval = reinterpret_cast<const float*>(tma_smem + FB + e * EB + EB / 2);
+    if (live) {
+#pragma unroll
+      for (int k = 0; k < NZ; ++k) z[k] = sz[k * kTmaTile + tid];
+      V = sz[NZ * kTmaTile + tid];
+      mk = reinterpret_cast<const unsigned char*>(sz + (NZ + 1) * kTmaTile)[tid];
+#pragma unroll
+      for (int k = 0; k < kTmaStageEllWidth; ++k)
+        if (k < w) xv[k] = __ldg(a.V32m1 + scol[base + 32 * k]);
+    }
+    __syncthreads();  // the state region and the other ELL buffer are free
+    if (tid == 0 && tile + G < ntiles) {
+      fence_proxy_async();
+      issue_ell(tile + G, e ^ 1);
+      issue_state(tile + G, e ^ 1);
+    }
+    if (live) stage_node_core<Model, HAS_M2>(a, A, i, z, V, mk, xv, w, sval, base);
+  }
+  // on abort: give copies already in flight a bounded chance to land
+  if (s_abort && tid == 0) {
+    for (int b = 0; b < 2; ++b) {
       long long spins = 0;
       while (!mbar_try_wait(b ? bar1 : bar0, phase[b]) && ++spins < kTmaSpinLimit) {
       }
@@ -1258,8 +1402,14 @@ struct Kernels {
     const unsigned g = blocks_for(a.n, 128);
     if constexpr (MIXED) {
       const bool pdl = a.pdl != 0;
-      if (a.mask != nullptr && a.tma_grid > 0) {
-        const int smem = a.tma_nbuf * tma_smem_bytes(MR::NE + MR::NS, a.ell_wmax, a.tma_ell);
+      if (a.mask != nullptr && a.tma_grid > 0 && a.tma_nbuf == 3 && a.tma_ell && a.ell_wmax <= kTmaStageEllWidth) {
+        const int smem = tma_pf_smem_bytes(MR::NE + MR::NS, a.ell_wmax);
+        const int64_t ntiles = (a.n + kTmaTile - 1) / kTmaTile;
+        const unsigned g2 = (unsigned)std::min<int64_t>(a.tma_grid, ntiles);
+        if (has_m2) launch_k(pdl, stage_kernel_mixed_tma_pf<MR, true>, g2, kTmaTile, smem, st, a, A);
+        else launch_k(pdl, stage_kernel_mixed_tma_pf<MR, false>, g2, kTmaTile, smem, st, a, A);
+      } else if (a.mask != nullptr && a.tma_grid > 0) {
+        const int smem = (a.tma_nbuf == 3 ? 1 : a.tma_nbuf) * tma_smem_bytes(MR::NE + MR::NS, a.ell_wmax, a.tma_ell);
         // no more CTAs than tiles (small problems)
         const int64_t ntiles = (a.n + kTmaTile - 1) / kTmaTile;
         const unsigned g2 = (unsigned)std::min<int64_t>(a.tma_grid, ntiles);
@@ -1371,8 +1521,16 @@ struct Kernels {
     if constexpr (!MIXED) {
       return 0;
     } else {
-      const int smem = nbuf * tma_smem_bytes(MR::NE + MR::NS, wmax, ell);
       int per_sm = 0, sms = 0;
+      if (nbuf == 3 && ell && wmax <= kTmaStageEllWidth) {
+        const int smem = tma_pf_smem_bytes(MR::NE + MR::NS, wmax);
+        cudaFuncSetAttribute(stage_kernel_mixed_tma_pf<MR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(stage_kernel_mixed_tma_pf<MR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel_mixed_tma_pf<MR, false>, kTmaTile, smem);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+        return per_sm * sms;
+      }
+      const int smem = (nbuf == 3 ? 1 : nbuf) * tma_smem_bytes(MR::NE + MR::NS, wmax, ell);
       cudaFuncSetAttribute(stage_kernel_mixed_tma<MR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
       cudaFuncSetAttribute(stage_kernel_mixed_tma<MR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel_mixed_tma<MR, false>, kTmaTile, smem);

@@ -79,7 +79,8 @@ struct StageArgs {
   float* Vn32_copy = nullptr;   // store hi of V_n (first stage when s >= 2)
   float f_th = -20;
   int tma_grid = 0;             // > 0: persistent bulk-copy variant with this grid
-  int tma_nbuf = 1;             // stage buffers per CTA of the bulk-copy variant (1 or 2)
+  int tma_nbuf = 3;             // bulk-copy variant: 1 or 2 whole-tile stage buffers per CTA, or 3 = one
+                                // state region + two ELL buffers with the next tile prefetched
   int tma_ell = 1;              // bulk-copy variant stages the tile's ELL slices (1) or reads them (0)
   int pdl = 0;                  // 1: programmatic dependent launch
   int ell_wmax = 1 << 30;       // widest sliced-ELL slice (selects unrolled row variants)

@@ -953,7 +953,9 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
     if (!(no_tma && no_tma[0] == '1')) {
       const char* nbuf = std::getenv("EMRKC_TMA_NBUF");
       const char* ell = std::getenv("EMRKC_TMA_ELL");
-      if (nbuf && nbuf[0] == '2') s->tma_nbuf = 2;
+      // default 3: one state region and two ELL buffers, the next tile
+      // prefetched during compute; 1 or 2: whole-tile stage buffers
+      if (nbuf && (nbuf[0] == '1' || nbuf[0] == '2')) s->tma_nbuf = nbuf[0] - '0';
       if (ell && ell[0] == '0') s->tma_ell = 0;
       s->tma_grid = s->ks.tma_grid(s->device, s->ell_wmax, s->tma_nbuf, s->tma_ell);
     }

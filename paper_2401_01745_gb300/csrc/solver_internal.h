@@ -164,7 +164,7 @@ struct emrkc_solver {
   int64_t total_it = 0, launches = 0;
   int64_t mat_entries = 0, mat_slots = 0;
   int tma_grid = 0;  // persistent bulk-copy stage kernel grid (mixed path), 0 = off
-  int tma_nbuf = 1;  // its stage buffers per CTA
+  int tma_nbuf = 3;  // its stage buffers per CTA (3: state region + two ELL buffers, prefetching)
   int tma_ell = 1;   // it stages the ELL slices of a tile
   int pdl = 0;             // mixed path: programmatic dependent launch of the step kernels
   // Algorithm 5 in one cooperative launch (emRKC)

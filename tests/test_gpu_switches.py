@@ -1,8 +1,9 @@
 """The launch-shape switches of the mixed path give the same results.
 
 `EMRKC_NO_TMA=1` selects the register-loaded stage kernel instead of the
-persistent bulk-copy one; `EMRKC_TMA_NBUF=2` gives the bulk-copy kernel two
-stage buffers per CTA instead of one, `EMRKC_TMA_ELL=0` has it read the ELL
+persistent bulk-copy one; by default the bulk-copy kernel prefetches the next
+tile into one state region and a second ELL buffer, `EMRKC_TMA_NBUF=1` or `2`
+give it one or two whole-tile stage buffers instead, `EMRKC_TMA_ELL=0` has it read the ELL
 rows from global memory instead of staging them; `EMRKC_NO_PDL=1` drops
 programmatic dependent launch.  All are read at solver creation.  The
 per-node arithmetic of the stage (Rush-Larsen step, ionic currents, first
@@ -51,7 +52,7 @@ def case():
 
 @pytest.mark.parametrize("env", [{}, {"EMRKC_NO_TMA": "1"}, {"EMRKC_NO_PDL": "1"},
                                  {"EMRKC_NO_TMA": "1", "EMRKC_NO_PDL": "1"},
-                                 {"EMRKC_TMA_NBUF": "2"}, {"EMRKC_TMA_ELL": "0"},
+                                 {"EMRKC_TMA_NBUF": "1"}, {"EMRKC_TMA_NBUF": "2"}, {"EMRKC_TMA_ELL": "0"},
                                  {"EMRKC_TMA_NBUF": "2", "EMRKC_TMA_ELL": "0"}])
 def test_switches_same_result(case, monkeypatch, env):
     w, steps, Vo = case
