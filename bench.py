@@ -44,7 +44,7 @@ NCU_TRAFFIC = {"kernel": "stage_kernel_mixed_tma_pf<ModelTTP06<float>, false>", 
                "bytes_per_launch": 55202816 + 1882880,
                "sources": ("paper_2401_01745_gb300/csrc/kernels.cuh", "paper_2401_01745_gb300/csrc/models.cuh",
                            "paper_2401_01745_gb300/csrc/kernels_mixed.cu"),
-               "sha256": "309de6ecbdf410129a4e51c0110d328bc797c33c48170875b76e4a91e16794e7"}
+               "sha256": "52b2461eb9a44a3caa96bff03d75accf7bb19913baa9acd2eef2860e25e723f2"}
 
 
 def _sources_sha256(paths):

@@ -499,7 +499,9 @@ __global__ void __launch_bounds__(kTmaTile) stage_kernel_mixed_tma(const StageAr
   constexpr int FB = tma_fixed_bytes(NZ);
   const bool stage_ell = a.tma_ell && a.ell_wmax <= kTmaStageEllWidth;
   const int SB = stage_ell ? tma_stage_bytes(NZ, a.ell_wmax) : FB;
-  const int nb = a.tma_nbuf;  // stage buffers per CTA: 1 or 2
+  // stage buffers per CTA: 1 or 2 (mode 3 belongs to the prefetching kernel;
+  // rows it cannot stage come here with one buffer)
+  const int nb = (a.tma_nbuf == 2) ? 2 : 1;
   const int64_t nslices = A.n_slices;
   extern __shared__ __align__(128) unsigned char tma_smem[];
   __shared__ __align__(8) unsigned long long bars[2];

@@ -90,3 +90,34 @@ def test_power_iteration_cluster_matches_grid(monkeypatch, prec):
     assert a[0] == pytest.approx(b[0], rel=tol)
     assert a[1] == pytest.approx(b[1], rel=tol)
     assert np.linalg.norm(a[4] - b[4]) <= 1e-12 * np.linalg.norm(b[4])
+
+
+def test_wide_rows_fall_back_to_unstaged_stage_kernel(monkeypatch):
+    """Rows wider than the staging width (the jittered shell has up to ~27
+    entries per row) cannot use the prefetching kernel; the bulk-copy kernel
+    then runs with one stage buffer and the rows read from global memory.
+    Every launch shape must agree with the others and with the FP64 path."""
+    from paper_2401_01745_gb300 import assemble_p1
+    w = make_workload("shell_ttp", nr=6, nuv=24)
+    w.stim_amp = 100.0
+    rp, col, K, M = assemble_p1(w.coords, w.cells, w.D)
+    assert np.max(np.diff(rp)) > 9  # diagonal + more than 8 off-diagonal entries
+    steps = 40
+    out = {}
+    for name, env in (("default", {}), ("one_buffer", {"EMRKC_TMA_NBUF": "1"}), ("no_tma", {"EMRKC_NO_TMA": "1"})):
+        for k in ("EMRKC_TMA_NBUF", "EMRKC_NO_TMA"):
+            monkeypatch.delenv(k, raising=False)
+        for k, v in env.items():
+            monkeypatch.setenv(k, v)
+        out[name] = _run(w, steps)[0]
+    monkeypatch.delenv("EMRKC_TMA_NBUF", raising=False)
+    monkeypatch.delenv("EMRKC_NO_TMA", raising=False)
+    sol = pkg.Solver.from_workload(w, precision=pkg.PREC_FP64, rho_every=0)
+    for _ in range(steps):
+        sol.step(w.dt)
+    sol.sync()
+    V64 = sol.get_state(var=0)
+    sol.close()
+    for name in ("one_buffer", "no_tma"):
+        assert np.linalg.norm(out[name] - out["default"]) <= 1e-6 * np.linalg.norm(out["default"])
+    assert np.linalg.norm(out["default"] - V64) <= 1e-3 * np.linalg.norm(V64)
