@@ -44,7 +44,7 @@ NCU_TRAFFIC = {"kernel": "stage_kernel_mixed_tma_pf<ModelTTP06<float>, false>", 
                "bytes_per_launch": 55202816 + 1882880,
                "sources": ("paper_2401_01745_gb300/csrc/kernels.cuh", "paper_2401_01745_gb300/csrc/models.cuh",
                            "paper_2401_01745_gb300/csrc/kernels_mixed.cu"),
-               "sha256": "52b2461eb9a44a3caa96bff03d75accf7bb19913baa9acd2eef2860e25e723f2"}
+               "sha256": "285376c43bd783704d2d98124bd2f8a99c46226ae7667b8f479d918256ee1d31"}
 
 
 def _sources_sha256(paths):

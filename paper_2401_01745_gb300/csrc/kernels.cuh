@@ -57,10 +57,10 @@ __device__ __forceinline__ float ell_diff32(const Ell& A, int64_t i, const float
   return acc;
 }
 
-// Split form of ell_diff32 for rows of at most W stored entries: ell_gather
-// issues every column, value and neighbour load of the row up front (into
-// registers), ell_reduce sums them later, so the loads can be in flight
-// while the caller does other work (the ionic model).  Same sum, same order.
+// Split form of ell_diff32 for rows of at most W stored entries: ell_row
+// loads the row's columns and values, ell_gather_x issues every neighbour
+// load up front (into registers), ell_reduce sums them later, so the loads
+// can be in flight while the caller does other work.  Same sum, same order.
 template <int W>
 __device__ __forceinline__ int ell_row(const Ell& A, int64_t i, int32_t (&c)[W], float (&lv)[W]) {
   const int64_t b = i >> 5;
@@ -84,37 +84,12 @@ __device__ __forceinline__ void ell_gather_x(const int32_t (&c)[W], int w, const
     if (k < w) xv[k] = ldm<CG>(x + c[k]);
 }
 
-template <int W, bool CG = false>
-__device__ __forceinline__ int ell_gather(const Ell& A, int64_t i, const float* __restrict__ x, float (&xv)[W],
-                                          float (&lv)[W]) {
-  int32_t c[W];
-  const int w = ell_row<W>(A, i, c, lv);
-  ell_gather_x<W, CG>(c, w, x, xv);
-  return w;
-}
-
 template <int W>
 __device__ __forceinline__ float ell_reduce(const float (&xv)[W], const float (&lv)[W], int w, float xi) {
   float acc = 0.0f;
 #pragma unroll
   for (int k = 0; k < W; ++k)
     if (k < w) acc += lv[k] * (xv[k] - xi);
-  return acc;
-}
-
-// FP64 evaluation with the off-diagonal FP32 matrix (power iteration in mixed mode).
-__device__ __forceinline__ double ell_diff64(const Ell& A, int64_t i, const double* __restrict__ x,
-                                             const double* __restrict__ v, double q) {
-  const int64_t b = i >> 5;
-  const int w = __ldg(A.width + b);
-  int64_t p = __ldg(A.slice_ptr + b) + (i & 31);
-  const double xi = v ? x[i] + q * v[i] : x[i];
-  double acc = 0.0;
-  for (int k = 0; k < w; ++k, p += 32) {
-    const int32_t c = __ldg(A.col + p);
-    const double xc = v ? x[c] + q * v[c] : x[c];
-    acc += (double)__ldg(A.val32 + p) * (xc - xi);
-  }
   return acc;
 }
 
