@@ -19,7 +19,9 @@ pytestmark = pytest.mark.gpu
 
 def test_served_results_equal_solo_runs():
     pkg.build()
-    reqs = served_requests(count=8, rate=400.0, seed=11, n_min=2e3, n_max=3e4, horizon=(1.0, 4.0),
+    # arrivals 0.25 ms apart on average: the second request arrives while the
+    # first (at least 20 steps) is still on the device, whatever the GPU's speed
+    reqs = served_requests(count=8, rate=4000.0, seed=11, n_min=2e3, n_max=3e4, horizon=(1.0, 4.0),
                            size_classes=3)
     cache = MeshCache(request_workload)
     cache.prepare(reqs)
