@@ -123,7 +123,9 @@ typedef struct {
 /* Nodal stimulus (Eq. sd_sys, linear interpolation of I_stim):
  * I_stim(t, x_i) = amplitude if node_mask[i] != 0 and t_on <= t <= t_off. */
 typedef struct {
-  const uint8_t* node_mask; /* n host entries, or NULL for no stimulus */
+  const uint8_t* node_mask; /* n host entries, or NULL for no stimulus (amplitude and
+                             * window then apply to a mask set later, e.g. by
+                             * emrkc_batch_set_stimulus_async) */
   double amplitude;         /* uA/cm^2 */
   double t_on, t_off;       /* ms, inclusive */
 } emrkc_stimulus;
@@ -249,24 +251,28 @@ int emrkc_get_activation_times(emrkc_solver* s, double* host_out, int64_t n);
  * raw estimates (without the safety factor) and iteration counts. */
 int emrkc_estimate_rho(emrkc_solver* s, double* rho_F, double* rho_S, int* it_F, int* it_S);
 
-/* Allocation-free variant of the f_F half of emrkc_estimate_rho (the paper
- * has no counterpart: it exists for callers that must not allocate device
- * memory while they run, e.g. a host whose allocator owns the whole GPU or a
- * time-critical loop that cannot afford cudaMalloc's synchronisation).
- * Runs Algorithm 5 on f_F for the solver's current V with caller-owned
- * device vectors: d_v (n doubles; in: start or warm-start direction, out:
- * final iterate) and d_w (n doubles of work space); rho_warm is the warm
- * start (0 for none).  Writes the raw estimate (no safety factor) and the
- * iteration count.  The reduction scratch (8 KiB of partial sums, 8 result
- * slots and a ticket counter, 8.5 KiB in all) is a static device array that
- * every GPU loading the library holds until exit; the first call on a device
- * looks its address up (cudaGetSymbolAddress) and zeroes the ticket, so make
- * that first call before any stream capture.  Every call shares the array:
- * calls that overlap on the GPU (other streams, other threads) race.  The
- * grid is capped at 1024 blocks, the capacity of the scratch; a problem that
- * would need more is rejected.  Errors: EMRKC_ERR_ARG for a null pointer or
- * n != number of nodes, EMRKC_ERR_CUDA if the set-up fails.  Calls no
- * cudaMalloc / cudaFree and synchronises the solver's stream. */
+/* Allocation-free variant of the f_F half of emrkc_estimate_rho.  The paper
+ * has no counterpart: this entry point exists for callers that must not
+ * allocate device memory while they run, e.g. a host whose own allocator
+ * owns the whole GPU, or a time-critical loop that cannot afford
+ * cudaMalloc's implicit synchronisation.  It runs the same nonlinear power
+ * iteration on the diffusion term f_F at the solver's current V, with
+ * caller-owned device vectors: d_v (n doubles; in: start or warm-start
+ * direction, out: final iterate) and d_w (n doubles of work space);
+ * rho_warm is the warm start (0 for none).  Writes the raw estimate (no
+ * safety factor) and the iteration count.  emRKC solvers only (for mRKC the
+ * solver's own estimate runs on (V, z_k), not on V).
+ * The reduction scratch (1024 partial sums, 8 result slots and a ticket
+ * counter: 8.5 KiB) is a static device array that every GPU loading the
+ * library holds until exit.  The reduction grid is capped at 1024 blocks,
+ * one partial sum each; grid-stride loops cover any n.  The first call on a
+ * device looks the array's address up (cudaGetSymbolAddress) and zeroes the
+ * ticket, so make that first call before any stream capture; the address is
+ * kept for the life of the device's primary context.  Every call shares the
+ * array: calls that overlap on the GPU (other streams, other threads) race.
+ * Errors: EMRKC_ERR_ARG for a null pointer, n != number of nodes or a
+ * method other than emRKC; EMRKC_ERR_CUDA if the set-up or a launch fails.
+ * Calls no cudaMalloc / cudaFree and synchronises the solver's stream. */
 int emrkc_estimate_rho_F_noalloc(emrkc_solver* s, double* d_v, double* d_w, int64_t n, double rho_warm,
                                  double* rho_out, int* it_out);
 
@@ -382,6 +388,36 @@ int emrkc_batch_autotune(emrkc_batch* b, double dt, int reps, int* tile_out, int
  * up, records EMRKC_ERR_TIMEOUT (reported by emrkc_batch_sync) and returns;
  * default 2^24 (about 2 s with 100 ns back-off).  limit >= 0. */
 int emrkc_batch_set_spin_limit(emrkc_batch* b, int64_t limit);
+/* Pipelined host I/O of a whole batch (as emrkc_set_stimulus_async /
+ * emrkc_get_state_async for one solver, with the state held on the device
+ * as a model's weights are).  The host arrays hold every instance's nodes
+ * concatenated in the order returned by emrkc_batch_ids (the order in which
+ * the instances were added); len must equal the batch's total node count.
+ * emrkc_batch_set_stimulus_async: node masks (one byte per node, nonzero =
+ * stimulated), copied from host_masks into one of two device staging
+ * buffers on a host-to-device copy stream, then scattered into the
+ * instances' mask buffers on the batch's stream; steps enqueued after the
+ * call use the new masks (amplitude and time window stay per instance).
+ * emrkc_batch_get_V_async: V of every instance after the steps enqueued so
+ * far, joined from the float-float pair into one of two device staging
+ * buffers on the batch's stream and copied to host_out on a device-to-host
+ * copy stream, overlapping the following steps.  Host buffers (pinned
+ * memory for overlap) must stay valid, and host_out is complete, once
+ * emrkc_batch_sync returns; emrkc_batch_sync waits for both copy streams.
+ * Errors: EMRKC_ERR_ARG (null buffer), EMRKC_ERR_STATE (len; get_V_async
+ * before the first step after instances joined or left), EMRKC_ERR_OOM,
+ * EMRKC_ERR_CUDA. */
+int emrkc_batch_set_stimulus_async(emrkc_batch* b, const uint8_t* host_masks, int64_t len);
+int emrkc_batch_get_V_async(emrkc_batch* b, double* host_out, int64_t len);
+/* Instance ids in batch order into ids_out (up to cap entries); returns the
+ * number of instances (-1 if b is NULL). */
+int emrkc_batch_ids(const emrkc_batch* b, int* ids_out, int cap);
+/* Kernel timing: with on != 0 every persistent launch is bracketed by CUDA
+ * events on the batch's stream (steps are then launched directly, not as a
+ * graph); emrkc_batch_get_kernel_time returns the summed milliseconds and
+ * the number of timed launches so far (read at emrkc_batch_sync). */
+int emrkc_batch_set_profile(emrkc_batch* b, int on);
+int emrkc_batch_get_kernel_time(emrkc_batch* b, double* ms_out, int64_t* launches_out);
 /* Device bytes an instance of n nodes with nnz_per_row stored entries per
  * row would hold (for admission control against an HBM budget). */
 int64_t emrkc_instance_bytes(int64_t n, double nnz_per_row, int ionic_model);

@@ -374,7 +374,37 @@ class Batch:
         return t.value, b.value, ms.value
 
     def ids(self):
-        return list(self._n)
+        """Instance ids in batch order (the order of the concatenated I/O arrays)."""
+        cnt = self._lib.emrkc_batch_ids(self._h, None, 0)
+        buf = (C.c_int * max(cnt, 1))()
+        self._lib.emrkc_batch_ids(self._h, buf, cnt)
+        return list(buf[:cnt])
+
+    def total_nodes(self):
+        return int(sum(self._n.values()))
+
+    def set_stimulus_async(self, masks):
+        """Node masks of every instance, concatenated in batch order (uint8)."""
+        if masks.dtype != np.uint8 or not masks.flags.c_contiguous:
+            raise ValueError("masks must be a C-contiguous uint8 array")
+        self._check(self._lib.emrkc_batch_set_stimulus_async(
+            self._h, masks.ctypes.data_as(C.POINTER(C.c_uint8)), masks.size))
+
+    def get_V_async(self, out):
+        """V of every instance, concatenated in batch order, into ``out``
+        (float64, complete after sync)."""
+        if out.dtype != np.float64 or not out.flags.c_contiguous:
+            raise ValueError("out must be a C-contiguous float64 array")
+        self._check(self._lib.emrkc_batch_get_V_async(self._h, _dp(out), out.size))
+
+    def set_profile(self, on=True):
+        self._check(self._lib.emrkc_batch_set_profile(self._h, int(on)))
+
+    def kernel_time(self):
+        """(summed ms, launches) of the persistent kernel while profiling."""
+        ms, n = C.c_double(), C.c_int64()
+        self._check(self._lib.emrkc_batch_get_kernel_time(self._h, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
 
     def close(self):
         if self._h:

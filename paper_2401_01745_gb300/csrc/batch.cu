@@ -232,6 +232,43 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) batch_step_kernel(const B
   }
 }
 
+// ---- Pipelined host I/O of a whole batch ---------------------------------
+// Instance k (blockIdx.y) owns entries [off[k], off[k + 1]) of the batch's
+// concatenated host arrays.  The join reads V = hi + lo of the instance's
+// current state buffer from the device table, which the persistent kernel of
+// the preceding step has advanced (same stream).
+__global__ void __launch_bounds__(256) batch_join_V_kernel(const BatchInst* __restrict__ inst,
+                                                          const int64_t* __restrict__ off, double* __restrict__ out) {
+  const BatchInst* I = inst + blockIdx.y;
+  const int cur = I->cur;
+  const float* __restrict__ hi = I->Vhi[cur];
+  const float* __restrict__ lo = I->Vlo[cur];
+  const int64_t n = I->n;
+  double* __restrict__ o = out + off[blockIdx.y];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    o[i] = (double)hi[i] + (double)lo[i];
+}
+
+__global__ void __launch_bounds__(256) batch_scatter_mask_kernel(uint8_t* const* __restrict__ masks,
+                                                                const int64_t* __restrict__ off,
+                                                                const uint8_t* __restrict__ src) {
+  uint8_t* __restrict__ dst = masks[blockIdx.y];
+  const int64_t o = off[blockIdx.y], n = off[blockIdx.y + 1] - o;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[o + i];
+}
+
+void launch_batch_join_V(const BatchInst* inst, const int64_t* off, int ni, double* out, cudaStream_t st) {
+  if (ni <= 0) return;
+  batch_join_V_kernel<<<dim3(64, (unsigned)ni), 256, 0, st>>>(inst, off, out);
+}
+
+void launch_batch_scatter_mask(uint8_t* const* masks, const int64_t* off, int ni, const uint8_t* src,
+                               cudaStream_t st) {
+  if (ni <= 0) return;
+  batch_scatter_mask_kernel<<<dim3(64, (unsigned)ni), 256, 0, st>>>(masks, off, src);
+}
+
 void launch_batch_step(const BatchCtl& c, int grid, int block, cudaStream_t st) {
   if (block == 256) batch_step_kernel<256><<<grid, 256, 0, st>>>(c);
   else batch_step_kernel<128><<<grid, 128, 0, st>>>(c);

@@ -59,6 +59,31 @@ struct emrkc_batch {
   cudaGraphExec_t exec = nullptr;
   int64_t launches = 0;
   std::string err;
+  // membership version (bumped by add / remove); the I/O tables follow it
+  int64_t version = 0;
+  // pipelined whole-batch host I/O: one copy stream per direction, two
+  // staging buffers per direction, per-instance offsets into the
+  // concatenated host arrays (member order) and mask pointers
+  cudaStream_t h2d_stream = nullptr, d2h_stream = nullptr;
+  int64_t io_version = -1, io_total = 0;
+  int64_t* d_off = nullptr;
+  size_t off_cap = 0;
+  uint8_t** d_masks = nullptr;
+  size_t masks_cap = 0;
+  uint8_t* d_mstage[2] = {nullptr, nullptr};
+  size_t mstage_cap[2] = {0, 0};
+  double* d_vstage[2] = {nullptr, nullptr};
+  size_t vstage_cap[2] = {0, 0};
+  cudaEvent_t ev_mready[2] = {nullptr, nullptr}, ev_mfree[2] = {nullptr, nullptr};
+  cudaEvent_t ev_vready[2] = {nullptr, nullptr}, ev_vfree[2] = {nullptr, nullptr};
+  bool mfree_rec[2] = {false, false}, vfree_rec[2] = {false, false};
+  int mk = 0, vk = 0;
+  // kernel timing (emrkc_batch_set_profile): CUDA events around each
+  // persistent launch on the batch's stream, read at emrkc_batch_sync
+  bool profile = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pending, prof_pool;
+  double kernel_ms = 0.0;
+  int64_t kernel_launches = 0;
 
   int fail(int code, const std::string& m) {
     err = m;
@@ -78,6 +103,17 @@ struct emrkc_batch {
     if (graph) cudaGraphDestroy(graph);
     exec = nullptr;
     graph = nullptr;
+  }
+  void harvest() {
+    for (auto& pr : prof_pending) {
+      float ms = 0.f;
+      cudaEventSynchronize(pr.second);
+      cudaEventElapsedTime(&ms, pr.first, pr.second);
+      kernel_ms += ms;
+      ++kernel_launches;
+      prof_pool.push_back(pr);
+    }
+    prof_pending.clear();
   }
 };
 
@@ -250,7 +286,7 @@ int enqueue_step(emrkc_batch* b, int dry) {
   const size_t ni = b->members.size();
   if (ni == 0 || b->n_items == 0) return EMRKC_OK;
   cudaError_t e;
-  if (!dry && b->opt.use_graphs) {
+  if (!dry && b->opt.use_graphs && !b->profile) {
     if (!b->exec) {
       e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) return b->cuda_fail(e, "graph capture");
@@ -267,9 +303,23 @@ int enqueue_step(emrkc_batch* b, int dry) {
   } else {
     cudaMemsetAsync(b->d_done, 0, ni * kBatchMaxPhases * sizeof(unsigned int), b->stream);
     cudaMemsetAsync(b->d_ticket, 0, sizeof(unsigned int), b->stream);
+    std::pair<cudaEvent_t, cudaEvent_t> pr{nullptr, nullptr};
+    if (b->profile && !dry) {
+      if (!b->prof_pool.empty()) {
+        pr = b->prof_pool.back();
+        b->prof_pool.pop_back();
+      } else if ((e = cudaEventCreate(&pr.first)) != cudaSuccess || (e = cudaEventCreate(&pr.second)) != cudaSuccess) {
+        return b->cuda_fail(e, "event creation");
+      }
+      cudaEventRecord(pr.first, b->stream);
+    }
     launch_batch_step(make_ctl(b, dry), b->grid, b->block, b->stream);
     e = cudaGetLastError();
     if (e != cudaSuccess) return b->cuda_fail(e, "batch launch");
+    if (pr.second) {
+      cudaEventRecord(pr.second, b->stream);
+      b->prof_pending.push_back(pr);
+    }
   }
   ++b->launches;
   return EMRKC_OK;
@@ -373,6 +423,7 @@ int emrkc_batch_add(emrkc_batch* b, const emrkc_matrix* mat, const emrkc_tissue*
   mb.s = s;
   b->members.push_back(mb);
   b->dirty = true;
+  ++b->version;
   if (id_out) *id_out = mb.id;
   return EMRKC_OK;
 }
@@ -386,6 +437,7 @@ int emrkc_batch_remove(emrkc_batch* b, int id) {
       emrkc_destroy(b->members[i].s);
       b->members.erase(b->members.begin() + (long)i);
       b->dirty = true;
+      ++b->version;
       return EMRKC_OK;
     }
   }
@@ -427,6 +479,10 @@ int emrkc_batch_sync(emrkc_batch* b) {
   e = cudaMemcpy(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return b->cuda_fail(e, "error flag");
   if (err) return b->fail(EMRKC_ERR_TIMEOUT, "a dependency wait of the persistent kernel gave up");
+  for (cudaStream_t cs : {b->h2d_stream, b->d2h_stream}) {
+    if (cs && (e = cudaStreamSynchronize(cs)) != cudaSuccess) return b->cuda_fail(e, "copy stream synchronisation");
+  }
+  b->harvest();
   for (auto& mb : b->members) {
     int rc = emrkc_sync(mb.s);
     if (rc == EMRKC_ERR_NONFINITE) return b->fail(rc, "instance " + std::to_string(mb.id) + ": non-finite V");
@@ -571,6 +627,146 @@ int emrkc_batch_set_spin_limit(emrkc_batch* b, int64_t limit) {
   return EMRKC_OK;
 }
 
+namespace {
+// Copy streams, events and the per-instance tables of the whole-batch host
+// I/O, (re)built when instances joined or left since the last call.
+int io_prepare(emrkc_batch* b) {
+  cudaError_t e;
+  if (!b->h2d_stream) {
+    if ((e = cudaStreamCreateWithFlags(&b->h2d_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+      b->h2d_stream = nullptr;
+      return b->cuda_fail(e, "copy stream creation");
+    }
+    if ((e = cudaStreamCreateWithFlags(&b->d2h_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+      b->d2h_stream = nullptr;
+      return b->cuda_fail(e, "copy stream creation");
+    }
+    cudaEvent_t* evs[] = {&b->ev_mready[0], &b->ev_mready[1], &b->ev_mfree[0], &b->ev_mfree[1],
+                          &b->ev_vready[0], &b->ev_vready[1], &b->ev_vfree[0], &b->ev_vfree[1]};
+    for (cudaEvent_t* ev : evs)
+      if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess)
+        return b->cuda_fail(e, "event creation");
+  }
+  if (b->io_version == b->version) return EMRKC_OK;
+  const size_t ni = b->members.size();
+  std::vector<int64_t> off(ni + 1, 0);
+  std::vector<uint8_t*> masks(ni, nullptr);
+  for (size_t i = 0; i < ni; ++i) {
+    emrkc_solver* s = b->members[i].s;
+    off[i + 1] = off[i] + s->n;
+    if (!s->d_mask) {
+      // an instance created without a stimulus gets a zeroed mask buffer
+      // (ld bytes: the padding of its last tile is read)
+      if ((e = cudaMalloc((void**)&s->d_mask, (size_t)s->ld)) != cudaSuccess) {
+        s->d_mask = nullptr;
+        return b->fail(EMRKC_ERR_OOM, "device allocation failed");
+      }
+      if ((e = cudaMemsetAsync(s->d_mask, 0, (size_t)s->ld, b->stream)) != cudaSuccess)
+        return b->cuda_fail(e, "mask clear");
+      b->dirty = true;  // the plan picks up the new mask pointer
+    }
+    masks[i] = s->d_mask;
+  }
+  // the tables are rewritten only after every enqueued use of them
+  if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return b->cuda_fail(e, "stream synchronisation");
+  if ((e = grow(&b->d_off, &b->off_cap, ni + 1)) != cudaSuccess) return b->fail(EMRKC_ERR_OOM, "batch I/O table");
+  if ((e = grow(&b->d_masks, &b->masks_cap, std::max<size_t>(ni, 1))) != cudaSuccess)
+    return b->fail(EMRKC_ERR_OOM, "batch I/O table");
+  if ((e = cudaMemcpy(b->d_off, off.data(), (ni + 1) * sizeof(int64_t), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return b->cuda_fail(e, "batch I/O table upload");
+  if (ni && (e = cudaMemcpy(b->d_masks, masks.data(), ni * sizeof(uint8_t*), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return b->cuda_fail(e, "batch I/O table upload");
+  b->io_total = off[ni];
+  b->io_version = b->version;
+  return EMRKC_OK;
+}
+}  // namespace
+
+int emrkc_batch_set_stimulus_async(emrkc_batch* b, const uint8_t* host_masks, int64_t len) {
+  if (!b) return EMRKC_ERR_ARG;
+  if (!host_masks) return b->fail(EMRKC_ERR_ARG, "null buffer");
+  cudaSetDevice(b->device);
+  int rc = io_prepare(b);
+  if (rc) return rc;
+  if (len != b->io_total) return b->fail(EMRKC_ERR_STATE, "buffer length must equal the batch's total node count");
+  if (b->members.empty()) return EMRKC_OK;
+  cudaError_t e;
+  const int k = b->mk;
+  if ((e = grow(&b->d_mstage[k], &b->mstage_cap[k], (size_t)len)) != cudaSuccess)
+    return b->fail(EMRKC_ERR_OOM, "device allocation failed");
+  // the staging buffer is overwritten only after the scatter that read it
+  if (b->mfree_rec[k] && (e = cudaStreamWaitEvent(b->h2d_stream, b->ev_mfree[k], 0)) != cudaSuccess)
+    return b->cuda_fail(e, "mask copy ordering");
+  if ((e = cudaMemcpyAsync(b->d_mstage[k], host_masks, (size_t)len, cudaMemcpyHostToDevice, b->h2d_stream)) !=
+      cudaSuccess)
+    return b->cuda_fail(e, "mask copy");
+  if ((e = cudaEventRecord(b->ev_mready[k], b->h2d_stream)) != cudaSuccess) return b->cuda_fail(e, "mask copy");
+  // steps enqueued after this call read the new masks: the scatter runs on
+  // the batch's stream after the copy and after every step enqueued so far
+  if ((e = cudaStreamWaitEvent(b->stream, b->ev_mready[k], 0)) != cudaSuccess)
+    return b->cuda_fail(e, "mask copy ordering");
+  launch_batch_scatter_mask(b->d_masks, b->d_off, (int)b->members.size(), b->d_mstage[k], b->stream);
+  if ((e = cudaGetLastError()) != cudaSuccess) return b->cuda_fail(e, "mask scatter");
+  if ((e = cudaEventRecord(b->ev_mfree[k], b->stream)) != cudaSuccess) return b->cuda_fail(e, "mask scatter");
+  b->mfree_rec[k] = true;
+  b->mk = k ^ 1;
+  return EMRKC_OK;
+}
+
+int emrkc_batch_get_V_async(emrkc_batch* b, double* host_out, int64_t len) {
+  if (!b) return EMRKC_ERR_ARG;
+  if (!host_out) return b->fail(EMRKC_ERR_ARG, "null buffer");
+  cudaSetDevice(b->device);
+  if (b->dirty || b->n_items == 0)
+    return b->fail(EMRKC_ERR_STATE, "step the batch once after instances joined or left");
+  int rc = io_prepare(b);
+  if (rc) return rc;
+  if (len != b->io_total) return b->fail(EMRKC_ERR_STATE, "buffer length must equal the batch's total node count");
+  cudaError_t e;
+  const int k = b->vk;
+  if ((e = grow(&b->d_vstage[k], &b->vstage_cap[k], (size_t)len)) != cudaSuccess)
+    return b->fail(EMRKC_ERR_OOM, "device allocation failed");
+  // the staging buffer is refilled only after its previous copy-out
+  if (b->vfree_rec[k] && (e = cudaStreamWaitEvent(b->stream, b->ev_vfree[k], 0)) != cudaSuccess)
+    return b->cuda_fail(e, "state copy ordering");
+  launch_batch_join_V(b->d_inst, b->d_off, (int)b->members.size(), b->d_vstage[k], b->stream);
+  if ((e = cudaGetLastError()) != cudaSuccess) return b->cuda_fail(e, "state staging");
+  if ((e = cudaEventRecord(b->ev_vready[k], b->stream)) != cudaSuccess) return b->cuda_fail(e, "state staging");
+  if ((e = cudaStreamWaitEvent(b->d2h_stream, b->ev_vready[k], 0)) != cudaSuccess)
+    return b->cuda_fail(e, "state copy ordering");
+  if ((e = cudaMemcpyAsync(host_out, b->d_vstage[k], (size_t)len * sizeof(double), cudaMemcpyDeviceToHost,
+                           b->d2h_stream)) != cudaSuccess)
+    return b->cuda_fail(e, "state copy");
+  if ((e = cudaEventRecord(b->ev_vfree[k], b->d2h_stream)) != cudaSuccess) return b->cuda_fail(e, "state copy");
+  b->vfree_rec[k] = true;
+  b->vk = k ^ 1;
+  return EMRKC_OK;
+}
+
+int emrkc_batch_ids(const emrkc_batch* b, int* ids_out, int cap) {
+  if (!b) return -1;
+  const int ni = (int)b->members.size();
+  if (ids_out)
+    for (int i = 0; i < ni && i < cap; ++i) ids_out[i] = b->members[i].id;
+  return ni;
+}
+
+int emrkc_batch_set_profile(emrkc_batch* b, int on) {
+  if (!b) return EMRKC_ERR_ARG;
+  b->profile = on != 0;
+  b->drop_graph();
+  return EMRKC_OK;
+}
+
+int emrkc_batch_get_kernel_time(emrkc_batch* b, double* ms_out, int64_t* launches_out) {
+  if (!b) return EMRKC_ERR_ARG;
+  cudaSetDevice(b->device);
+  b->harvest();
+  if (ms_out) *ms_out = b->kernel_ms;
+  if (launches_out) *launches_out = b->kernel_launches;
+  return EMRKC_OK;
+}
+
 const char* emrkc_batch_last_error(const emrkc_batch* b) {
   if (!b) return g_batch_create_error.c_str();
   return b->err.c_str();
@@ -583,9 +779,24 @@ void emrkc_batch_destroy(emrkc_batch* b) {
   for (auto& mb : b->members) emrkc_destroy(mb.s);
   b->members.clear();
   b->drop_graph();
-  void* ptrs[] = {b->d_inst, b->d_items, b->d_ticket, b->d_done, b->d_err};
+  for (cudaStream_t cs : {b->h2d_stream, b->d2h_stream})
+    if (cs) cudaStreamSynchronize(cs);
+  b->harvest();
+  for (auto& pr : b->prof_pool) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  void* ptrs[] = {b->d_inst,       b->d_items,      b->d_ticket,     b->d_done,       b->d_err,
+                  b->d_off,        b->d_masks,      b->d_mstage[0],  b->d_mstage[1],  b->d_vstage[0],
+                  b->d_vstage[1]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  cudaEvent_t evs[] = {b->ev_mready[0], b->ev_mready[1], b->ev_mfree[0], b->ev_mfree[1],
+                       b->ev_vready[0], b->ev_vready[1], b->ev_vfree[0], b->ev_vfree[1]};
+  for (cudaEvent_t ev : evs)
+    if (ev) cudaEventDestroy(ev);
+  for (cudaStream_t cs : {b->h2d_stream, b->d2h_stream})
+    if (cs) cudaStreamDestroy(cs);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }

@@ -366,10 +366,15 @@ inline uint64_t batch_item(int inst, int phase, int tile) {
 }
 void launch_batch_step(const BatchCtl& c, int grid, int block, cudaStream_t st);
 int batch_blocks_per_sm(int block);
+// Whole-batch host I/O: V of every instance (current state buffer, joined to
+// double) into out[off[k] ...]; node masks from src[off[k] ...] into each
+// instance's mask buffer.  ni instances, off has ni + 1 entries.
+void launch_batch_join_V(const BatchInst* inst, const int64_t* off, int ni, double* out, cudaStream_t st);
+void launch_batch_scatter_mask(uint8_t* const* masks, const int64_t* off, int ni, const uint8_t* src,
+                               cudaStream_t st);
 
 // Allocation-free power iteration on f_F (noalloc.cu): static device scratch.
 int noalloc_scratch(int device, cudaStream_t st, ReduceScratch* out, const char** why);
-int noalloc_max_blocks();
 void noalloc_sumsq(int64_t count, const double* x, const ReduceScratch& rs, int slot, cudaStream_t st);
 void noalloc_power_F(const PowerFArgs& a, const Ell& A, bool mixed, const ReduceScratch& rs, cudaStream_t st);
 

@@ -46,7 +46,12 @@ static __global__ void __launch_bounds__(kReduceBlock) noalloc_sumsq_kernel(int6
 
 // Device address of the static scratch on the current device (which must be
 // `device`).  The first call per device looks the symbol up with
-// cudaGetSymbolAddress and zeroes the ticket counter; later calls reuse it.
+// cudaGetSymbolAddress and zeroes the ticket counter; later calls reuse the
+// address, which stays valid while the device's primary context lives (a
+// cudaDeviceReset while the library is in use would leave it stale).
+// The reductions launch at most kReduceMaxBlocks blocks (grid-stride loops
+// cover any n), one partial sum each, which is what the array holds.
+static_assert(kNoAllocPartialBytes >= (size_t)kReduceMaxBlocks * sizeof(double), "one partial per block");
 int noalloc_scratch(int device, cudaStream_t st, ReduceScratch* out, const char** why) {
   if (device < 0 || device >= kMaxDevices) {
     *why = "device ordinal beyond the allocation-free scratch table";
@@ -78,8 +83,6 @@ int noalloc_scratch(int device, cudaStream_t st, ReduceScratch* out, const char*
   *out = d.rs;
   return 0;
 }
-
-int noalloc_max_blocks() { return kReduceMaxBlocks; }
 
 void noalloc_sumsq(int64_t count, const double* x, const ReduceScratch& rs, int slot, cudaStream_t st) {
   noalloc_sumsq_kernel<<<reduce_grid(count), kReduceBlock, 0, st>>>(count, x, rs, slot);

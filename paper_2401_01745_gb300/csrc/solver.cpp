@@ -1028,13 +1028,17 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
   }
   if ((e = cudaMallocHost(&s->h_pin, 32 * sizeof(double))) != cudaSuccess) return bail(EMRKC_ERR_OOM, "pinned allocation failed");
   std::memset(s->h_pin, 0, 32 * sizeof(double));
+  if (stim) {
+    // amplitude and window are kept without a mask too: they apply to a mask
+    // given later (emrkc_batch_set_stimulus_async)
+    s->amp = stim->amplitude;
+    s->t_on = stim->t_on;
+    s->t_off = stim->t_off;
+  }
   if (stim && stim->node_mask) {
     if ((e = dalloc(&s->d_mask, ld)) != cudaSuccess) return bail(EMRKC_ERR_OOM, "device allocation failed");
     cudaMemsetAsync(s->d_mask, 0, ld, s->stream);
     cudaMemcpyAsync(s->d_mask, stim->node_mask, s->n, cudaMemcpyHostToDevice, s->stream);
-    s->amp = stim->amplitude;
-    s->t_on = stim->t_on;
-    s->t_off = stim->t_off;
   }
   cudaMemsetAsync(s->d_flags, 0, 4 * sizeof(int), s->stream);
   cudaMemsetAsync(s->rs.ticket, 0, 4 * sizeof(unsigned int), s->stream);
@@ -1339,10 +1343,8 @@ int emrkc_estimate_rho_F_noalloc(emrkc_solver* s, double* d_v, double* d_w, int6
   if (!s) return EMRKC_ERR_ARG;
   if (!d_v || !d_w || !rho_out) return s->fail(EMRKC_ERR_ARG, "null pointer");
   if (n != s->n) return s->fail(EMRKC_ERR_ARG, "vector length must equal the number of nodes");
-  // the reduction launches min(ceil(n/256), kReduceMaxBlocks) blocks, one partial sum each
-  const int64_t blocks = std::min<int64_t>((n + kReduceBlock - 1) / kReduceBlock, kReduceMaxBlocks);
-  if (blocks > noalloc_max_blocks())
-    return s->fail(EMRKC_ERR_ARG, "problem needs more reduction blocks than the static scratch holds");
+  if (s->method != EMRKC_METHOD_EMRKC)
+    return s->fail(EMRKC_ERR_ARG, "the allocation-free estimate is for emRKC solvers (f_F on V) only");
   if (!(rho_warm >= 0.0) || !std::isfinite(rho_warm)) return s->fail(EMRKC_ERR_ARG, "rho_warm must be >= 0");
   cudaSetDevice(s->device);
   ReduceScratch rs;
@@ -1360,6 +1362,7 @@ int emrkc_estimate_rho_F_noalloc(emrkc_solver* s, double* d_v, double* d_w, int6
   };
   noalloc_sumsq(n, V, rs, 0, s->stream);
   noalloc_sumsq(n, d_v, rs, 1, s->stream);
+  if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) return s->cuda_fail(e, "allocation-free power iteration");
   int rc = read(0, 2);
   if (rc) return rc;
   const double ny = std::sqrt(res[0]);
@@ -1385,6 +1388,7 @@ int emrkc_estimate_rho_F_noalloc(emrkc_solver* s, double* d_v, double* d_w, int6
     a.q = q;
     a.slot = 2;
     noalloc_power_F(a, s->ell, mixed, rs, s->stream);
+    if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) return s->cuda_fail(e, "allocation-free power iteration");
     if ((rc = read(2, 1))) return rc;
     std::swap(cur, nxt);
     ++it;

@@ -156,3 +156,56 @@ def test_dependency_wait_timeout_is_reported():
             break
     assert code == 5
     b.close()
+
+
+def test_batch_pipelined_io_matches_waiting_calls():
+    """emrkc_batch_set_stimulus_async / emrkc_batch_get_V_async (every
+    instance's mask in, every instance's V out, two host buffers in rotation)
+    give exactly the V that emrkc_batch_get_state returns, after each step,
+    and a mask set this way acts like the mask given at creation."""
+    dt, steps = 0.05, 12
+    ws = [make_workload(n, h=h) for n, h in WORKLOADS[:3]]
+    a, b = pkg.Batch(), pkg.Batch()
+    ia = [a.add_workload(w) for w in ws]
+    for w in ws:  # b: created without a stimulus; masks only through the async call
+        rp, col, K, M = pkg.assemble_p1(w.coords, w.cells, w.D)
+        b.add(rp, col, K, M, chi=w.chi, Cm=w.Cm, model=w.model, mask=None, amplitude=w.stim_amp,
+              t_on=w.t_on, t_off=w.t_off)
+    assert b.ids() == sorted(b.ids()) and a.ids() == ia
+    masks = np.concatenate([np.ascontiguousarray(w.stim_mask, dtype=np.uint8) for w in ws])
+    total = sum(w.n for w in ws)
+    assert a.total_nodes() == total
+    ring = [np.empty(total), np.empty(total)]
+    got = []
+    for k in range(steps):
+        a.step(dt)
+        b.set_stimulus_async(masks)
+        b.step(dt)
+        b.get_V_async(ring[k % 2])
+        if k % 2 == 1:
+            b.sync()
+            a.sync()
+            ref = np.concatenate([a.get_state(i, var=0) for i in ia])
+            got.append(np.array_equal(ring[k % 2], ref))
+    assert all(got)
+    with pytest.raises(pkg.EmrkcError):
+        b.get_V_async(np.empty(total - 1))
+    a.close()
+    b.close()
+
+
+def test_batch_kernel_timing():
+    b = pkg.Batch()
+    b.add_workload(make_workload("slab23x9x5_ttp", h=0.01))
+    b.step(0.05)
+    b.set_profile(True)
+    for _ in range(4):
+        b.step(0.05)
+    b.sync()
+    ms, n = b.kernel_time()
+    assert n == 4 and ms > 0
+    b.set_profile(False)
+    b.step(0.05)
+    b.sync()
+    assert b.kernel_time()[1] == 4
+    b.close()

@@ -337,6 +337,45 @@ def test_full_size_shell_one_step_from_gpu_state():
         assert np.max(np.abs(Y21[k] - ref.Y[k])) / scale <= 1e-9, f"variable {k}"
 
 
+def test_full_size_shell_mixed_vs_fp64_activation():
+    """The ventricle-like shell at full size (4,193,408 nodes) over T = 100
+    ms, mixed against FP64 (rho once at t = 0): V within 1e-3 relative L2 and
+    activation times within 0.05 ms.  A node whose crossing falls within a
+    rounding-level distance of T can be activated by T in one run and not
+    the other; every such node must have crossed within one step of T in the
+    run that activated it, and one more step must activate it in both runs,
+    with activation times within 0.05 ms."""
+    w = make_workload("shell_ttp")
+    H = int(round(w.T / w.dt))
+    sols = {p: pkg.Solver.from_workload(w, precision=p, rho_every=0) for p in (pkg.PREC_FP64, pkg.PREC_MIXED)}
+    for p, sol in sols.items():
+        for _ in range(H):
+            sol.step(w.dt)
+        sol.sync()
+    V64, V32 = sols[pkg.PREC_FP64].get_state(var=0), sols[pkg.PREC_MIXED].get_state(var=0)
+    a64, a32 = sols[pkg.PREC_FP64].activation_times(), sols[pkg.PREC_MIXED].activation_times()
+    M = pkg.assemble_p1(w.coords, w.cells, w.D)[3]
+    err = np.sqrt(M @ (V32 - V64) ** 2) / np.sqrt(M @ (V64 * V64))
+    assert err <= 1e-3, f"mixed vs FP64 rel L2 error in V {err:.3e}"
+    both = np.isfinite(a64) & np.isfinite(a32)
+    assert both.sum() > 1e6  # the wave has crossed most of the shell
+    assert np.max(np.abs(a64[both] - a32[both])) <= 0.05
+    one = np.isfinite(a64) != np.isfinite(a32)
+    n_one = int(one.sum())
+    print(f"shell: rel L2 {err:.2e}, activated in both {int(both.sum())}, in one run only {n_one}")
+    if n_one:
+        t_one = np.where(np.isfinite(a64), a64, a32)[one]
+        assert np.all(w.T - t_one <= w.dt)
+        for sol in sols.values():
+            sol.step(w.dt)
+            sol.sync()
+        b64, b32 = sols[pkg.PREC_FP64].activation_times(), sols[pkg.PREC_MIXED].activation_times()
+        assert np.all(np.isfinite(b64[one]) & np.isfinite(b32[one]))
+        assert np.max(np.abs(b64[one] - b32[one])) <= 0.05
+    for sol in sols.values():
+        sol.close()
+
+
 @pytest.mark.parametrize("name,dt,steps,h,amp_scale", [
     ("slab41x15x7_ttp", 0.05, 300, 0.01, 1.0),
     ("square33x33_hh", 0.02, 300, 1.0 / 64, 1.0),

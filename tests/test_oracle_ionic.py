@@ -160,6 +160,71 @@ def test_ttp_rest_state_nearly_stationary():
     assert np.all(np.abs(lam[:, 0] * (zE[:, 0] - zinf[:, 0])) < 0.01)
 
 
+def _ttp_random_states(rng, k):
+    """Random TTP06 states within physiological ranges."""
+    V = rng.uniform(-95.0, 50.0, k)
+    zE = rng.uniform(0.0, 1.0, (12, k))
+    zS = np.stack([rng.uniform(0.3, 1.0, k),        # Rbar
+                   rng.uniform(125.0, 145.0, k),    # Ki (mM)
+                   rng.uniform(6.0, 14.0, k),       # Nai
+                   rng.uniform(5e-5, 2e-3, k),      # Cai
+                   rng.uniform(0.5, 4.5, k),        # CaSR
+                   rng.uniform(5e-5, 2e-2, k)])     # CaSS
+    return V, zE, zS
+
+
+def test_ttp_charge_balance():
+    """Every ionic current of TTP06 moves charge between the membrane and the
+    tracked ion pools, so (without stimulus) the membrane's dV/dt = -I_ion
+    equals the rate of change of the cell's total ion charge per unit
+    capacitance: (V_c F / C) [dNa_i + dK_i + 2 (dCa_c + (V_sr/V_c) dCa_sr +
+    (V_ss/V_c) dCa_ss)], where the calcium terms count free plus buffered
+    calcium (d(total)/dt = d(free)/dt / beta).  The fluxes between the
+    compartments (release, uptake, leak, transfer) cancel.  Checked pointwise
+    at random states; it fails if any current is missing from, or enters with
+    a wrong sign or stoichiometry into, either I_ion or the concentration
+    equations."""
+    m = TTP06Model()
+    rng = np.random.default_rng(6)
+    V, zE, zS = _ttp_random_states(rng, 500)
+    Rbar, Ki, Nai, Cai, CaSR, CaSS = zS
+    dV = -m.I_ion(V, zE, zS)
+    g = m.g_S(V, zE, zS)
+    dKi, dNai, dCai, dCaSR, dCaSS = g[1], g[2], g[3], g[4], g[5]
+
+    def total_rate(dc, c, buf, kbuf):  # free -> free + buffered
+        return dc * (1.0 + buf * kbuf / (c + kbuf) ** 2)
+
+    dCa_tot = (total_rate(dCai, Cai, m.Bufc, m.Kbufc)
+               + m.Vsr / m.Vc * total_rate(dCaSR, CaSR, m.Bufsr, m.Kbufsr)
+               + m.Vss / m.Vc * total_rate(dCaSS, CaSS, m.Bufss, m.Kbufss))
+    charge_rate = m.Vc * m.F / m.Cap * (dNai + dKi + 2.0 * dCa_tot)
+    scale = np.abs(np.stack(list(m.currents(V, zE, zS).values()))).sum(axis=0)
+    assert np.all(np.abs(charge_rate - dV) <= 1e-9 * scale + 1e-12)
+    # the check is sensitive: a Na/Ca exchanger with 2 instead of 3 Na per
+    # cycle in dNa_i shifts the charge rate by I_NaCa
+    c = m.currents(V, zE, zS)
+    slip = charge_rate - c["I_NaCa"]
+    assert np.max(np.abs(slip - dV)) > 1e-3 * np.max(np.abs(c["I_NaCa"]))
+
+
+def test_ttp_gates_bounded_and_monotone_rates():
+    """TTP06 gating: z_inf in [0, 1] and time constants positive over the
+    whole voltage range (the Rush-Larsen step then keeps every gate in
+    [0, 1]); the activation gates' z_inf (m, xr1, xs, r, d) rise and the
+    inactivation gates' (h, j, xr2, s, f, f2) fall with V."""
+    m = TTP06Model()
+    V = np.linspace(-120.0, 80.0, 2001)
+    zE = np.full((12, V.size), 0.5)
+    zS = np.tile(m.y0()[13:, None], (1, V.size))
+    lam, zinf = m.gating(V, zE, zS)
+    assert np.all((zinf >= 0.0) & (zinf <= 1.0)) and np.all(lam < 0.0)
+    for k in (0, 3, 5, 6, 8):  # m, xr1, xs, r, d
+        assert np.all(np.diff(zinf[k]) >= -1e-15), k
+    for k in (1, 2, 4, 7, 9, 10):  # h, j, xr2, s, f, f2
+        assert np.all(np.diff(zinf[k]) <= 1e-15), k
+
+
 @pytest.mark.slow
 def test_ttp_single_cell_action_potential():
     """Published TTP06 epicardial characteristics: rest near -85 mV, upstroke

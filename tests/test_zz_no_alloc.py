@@ -4,9 +4,10 @@ Some callers cannot allocate device memory while they run (a host whose own
 allocator owns the GPU, or a time-critical loop that must not call
 cudaMalloc).  For them the library keeps the reduction scratch of the f_F
 power iteration in a static device array; this test checks, through the C
-ABI, that the variant gives the same rho_F and iteration count as
-emrkc_estimate_rho on two calls in a row (cold start, then warm start), and
-that it rejects a vector length that does not match the solver.
+ABI, that the variant gives the rho_F and iteration count of
+emrkc_estimate_rho on two calls in a row (cold start, then warm start), in
+FP64 and in the mixed precision, and that it rejects a vector length that
+does not match the solver and every method other than emRKC.
 
 It sits in a file of its own that pytest collects last, and it passes both
 alone in a fresh process and after the other GPU tests (the first call on a
@@ -22,30 +23,39 @@ from workloads import make_workload, splitmix64, u01
 pytestmark = pytest.mark.gpu
 
 
-def test_noalloc_rho_F_matches_estimate_rho():
+@pytest.mark.parametrize("precision", [pkg.PREC_FP64, pkg.PREC_MIXED])
+def test_noalloc_rho_F_matches_estimate_rho(precision):
+    """Two calls in a row (cold start, then warm start from the first call's
+    iterate and estimate) against emrkc_estimate_rho of an identical solver.
+    FP64: the same differences of f_F in the same order, so the same estimate
+    to rounding and the same iteration count.  Mixed: emrkc_estimate_rho
+    iterates in FP32 (q L v), this variant forms L v in FP32 on FP64 iterates,
+    so the estimates agree to the mixed path's 1e-4 and the iteration counts
+    to one."""
     import torch
 
     pkg.build()
     w = make_workload("slab23x9x5_ttp", h=0.01)
     seed = 77
-    ref = pkg.Solver.from_workload(w, seed=seed)
-    sol = pkg.Solver.from_workload(w, seed=seed)
+    ref = pkg.Solver.from_workload(w, seed=seed, precision=precision)
+    sol = pkg.Solver.from_workload(w, seed=seed, precision=precision)
     # the same start vector as the solver's own: u01(splitmix64(seed ^ i)) - 0.5
     v0 = u01(splitmix64(np.uint64(seed), np.arange(w.n, dtype=np.uint64))) - 0.5
     d_v = torch.tensor(v0, dtype=torch.float64, device="cuda")
     d_w = torch.empty_like(d_v)
     torch.cuda.synchronize()
+    rel, dit = (1e-12, 0) if precision == pkg.PREC_FP64 else (1e-4, 1)
 
     rF1, _, itF1, _ = ref.estimate_rho()
     r1, it1 = sol.estimate_rho_F_noalloc(d_v.data_ptr(), d_w.data_ptr(), w.n, 0.0)
-    assert it1 == itF1
-    assert r1 == pytest.approx(rF1, rel=1e-12)
+    assert abs(it1 - itF1) <= dit
+    assert r1 == pytest.approx(rF1, rel=rel)
 
     # second call, warm started from the first call's iterate and estimate
     rF2, _, itF2, _ = ref.estimate_rho()
     r2, it2 = sol.estimate_rho_F_noalloc(d_v.data_ptr(), d_w.data_ptr(), w.n, r1)
-    assert it2 == itF2
-    assert r2 == pytest.approx(rF2, rel=1e-12)
+    assert abs(it2 - itF2) <= dit
+    assert r2 == pytest.approx(rF2, rel=rel)
     assert it2 <= 3
 
     with pytest.raises(pkg.EmrkcError) as ei:
@@ -53,3 +63,20 @@ def test_noalloc_rho_F_matches_estimate_rho():
     assert ei.value.code == 1
     ref.close()
     sol.close()
+
+
+def test_noalloc_rejects_other_methods():
+    """For mRKC the solver's own estimate runs on (V, z_k); the variant, which
+    works on V only, refuses every method other than emRKC."""
+    import torch
+
+    pkg.build()
+    w = make_workload("slab23x9x5_ttp", h=0.01)
+    d_v = torch.zeros(w.n, dtype=torch.float64, device="cuda")
+    d_w = torch.empty_like(d_v)
+    for method in (pkg.METHOD_MRKC, pkg.METHOD_EXEX_RL):
+        sol = pkg.Solver.from_workload(w, method=method)
+        with pytest.raises(pkg.EmrkcError) as ei:
+            sol.estimate_rho_F_noalloc(d_v.data_ptr(), d_w.data_ptr(), w.n, 0.0)
+        assert ei.value.code == 1
+        sol.close()
