@@ -254,10 +254,12 @@ def _cpu_info():
 def _oracle_worker(job):
     """One process: build instance ``index`` of the batched workload, run the
     FP64 oracle from rest (rho once at t = 0, as the GPU arm) after every
-    process of the pool is ready, and time its steps.  ``steps`` fixes the
-    step count; otherwise steps are taken until ``budget_s`` has passed (at
-    least one)."""
-    index, count, steps, warmup, budget_s, barrier = job
+    process of the pool is ready, and time its steps.  With ``rounds`` set,
+    the process takes that many rounds of k steps, k chosen from its warm-up
+    step time so that a round lasts about ``round_s`` (at least one step), so
+    that every core stays busy whatever its instance's size; otherwise steps
+    are taken until ``budget_s`` has passed (at least one)."""
+    index, count, rounds, warmup, budget_s, round_s, barrier = job
     from oracle.emrkc import Monodomain, OracleRun
     from workloads.configs import batched_specs, batched_workload
 
@@ -266,17 +268,26 @@ def _oracle_worker(job):
     prob = Monodomain.from_workload(w)
     rho_min = HH_RHO_S_MAX if w.model == 2 else 0.0
     warm = OracleRun(prob, rho_every=0, rho_S_min=rho_min)
-    for _ in range(warmup):
+    tw = time.perf_counter()
+    for _ in range(max(warmup, 2)):
         warm.step(w.dt)
+    t_step = (time.perf_counter() - tw) / max(warmup, 2)
+    per_round = max(1, int(round(round_s / max(t_step, 1e-9))))
     r = OracleRun(prob, rho_every=0, rho_S_min=rho_min)
     if barrier is not None:
         barrier.wait()
     t0 = time.perf_counter()
     k = 0
-    while (steps is not None and k < steps) or (steps is None and (k == 0 or time.perf_counter() - t0 < budget_s)):
-        r.step(w.dt)
-        k += 1
-    return {"index": index, "n": w.n, "model": int(w.model), "steps": k, "seconds": time.perf_counter() - t0}
+    if rounds is not None:
+        for _ in range(rounds * per_round):
+            r.step(w.dt)
+            k += 1
+    else:
+        while k == 0 or time.perf_counter() - t0 < budget_s:
+            r.step(w.dt)
+            k += 1
+    return {"index": index, "n": w.n, "model": int(w.model), "steps": k, "seconds": time.perf_counter() - t0,
+            "steps_per_round": per_round}
 
 
 def _sample_instances(count, k):
@@ -293,7 +304,7 @@ def _sample_instances(count, k):
     return sorted(set(picks))
 
 
-def _oracle_pool(count, steps=None, warmup=0, budget_s=10.0, procs=None):
+def _oracle_pool(count, rounds=None, warmup=0, budget_s=10.0, procs=None, round_s=1.0):
     """The oracle on ``procs`` instances of the batched workload at once, one
     process per host core (instances from _sample_instances).  Returns (node-steps/s of the whole pool, cores,
     per-process records)."""
@@ -310,7 +321,7 @@ def _oracle_pool(count, steps=None, warmup=0, budget_s=10.0, procs=None):
         with ctx.Manager() as mgr:
             barrier = mgr.Barrier(len(idx))
             with ctx.Pool(len(idx)) as pool:
-                recs = pool.map(_oracle_worker, [(i, count, steps, warmup, budget_s, barrier) for i in idx])
+                recs = pool.map(_oracle_worker, [(i, count, rounds, warmup, budget_s, round_s, barrier) for i in idx])
     finally:
         for k, v in env_keep.items():
             if v is None:
@@ -322,14 +333,18 @@ def _oracle_pool(count, steps=None, warmup=0, budget_s=10.0, procs=None):
     return units / wall, len(idx), recs
 
 
-def _pool_sample_text(recs, count):
+def _pool_sample_text(recs, count, rounds=None, round_s=1.0):
     n = sum(r["n"] for r in recs)
-    return (f"FP64 oracle (numpy, one process per core, one thread each) on {len(recs)} of the {count} "
+    text = (f"FP64 oracle (numpy, one process per core, one thread each) on {len(recs)} of the {count} "
             f"batched instances (half HH, half TTP06, each spread over that model's sizes; {n} nodes in all, "
             f"{sum(1 for r in recs if r['model'] == 2)} HH / {sum(1 for r in recs if r['model'] == 3)} TTP06), "
             f"from rest, rho once at t = 0; {min(r['steps'] for r in recs)}-{max(r['steps'] for r in recs)} "
-            "steps per process, all processes started together; value = node-steps of all processes / the "
-            "slowest process's time")
+            "steps per process, all processes started together")
+    if rounds:
+        text += (f"; one bench step = one round in which each process takes the steps that last about "
+                 f"{round_s} s on its instance ({min(r['steps_per_round'] for r in recs)}-"
+                 f"{max(r['steps_per_round'] for r in recs)})")
+    return text + "; value = node-steps of all processes / the slowest process's time"
 
 
 def run_reference(args):
@@ -339,16 +354,17 @@ def run_reference(args):
     if rank != 0:
         return 0
     cores, cpu = _cpu_info()
-    value, used, recs = _oracle_pool(args.instances, steps=args.steps, warmup=args.warmup)
+    value, used, recs = _oracle_pool(args.instances, rounds=args.steps, warmup=args.warmup)
     ms = 1e3 * max(r["seconds"] for r in recs) / args.steps
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": batched_workload_text(args.instances),
-                   "sample": _pool_sample_text(recs, args.instances), "cpu": cpu, "host_cores": cores},
+                   "sample": _pool_sample_text(recs, args.instances, rounds=args.steps), "cpu": cpu,
+                   "host_cores": cores},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
-                         "sample": _pool_sample_text(recs, args.instances)},
+                         "sample": _pool_sample_text(recs, args.instances, rounds=args.steps)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
