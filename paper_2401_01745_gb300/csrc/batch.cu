@@ -21,54 +21,6 @@
 
 namespace emrkc {
 
-// Prefetches of the thread's next node (i + B) while the current one
-// computes: its streamed rows and its row of L into L1 (L2 when the launch
-// rewrites buffers), so that its loads find them there.  The slice offset
-// and width of the node after that are prefetched one step earlier, so
-// reading them here rarely waits.  A prefetch holds no register and never
-// faults; every address is inside its array.
-template <bool CG>
-__device__ __forceinline__ void pf(const void* p) {
-  if constexpr (CG) asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-  else asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-}
-
-template <bool CG>
-__device__ __forceinline__ void pf_row_of(const Ell& A, int64_t nx, int64_t nn, int64_t r1) {
-  const int64_t b = nx >> 5;
-  const int w = __ldg(A.width + b);
-  const int64_t p = __ldg(A.slice_ptr + b) + (nx & 31);
-  for (int k = 0; k < w; ++k) {
-    pf<CG>(A.col + p + 32 * k);
-    pf<CG>(A.val32 + p + 32 * k);
-  }
-  if (nn < r1) {
-    pf<CG>(A.width + (nn >> 5));
-    pf<CG>(A.slice_ptr + (nn >> 5));
-  }
-}
-
-// The streamed inputs of stage node nx (see stage_node_mixed_with).
-template <class Model, bool HAS_M2, bool CG>
-__device__ __forceinline__ void pf_stage_node(const StageArgs& a, int64_t nx) {
-  constexpr int NZ = Model::NE + Model::NS;
-  const float* Zm1 = static_cast<const float*>(a.Zm1);
-  const float* Zm2 = static_cast<const float*>(a.Zm2);
-  pf<CG>(a.V32m1 + nx);
-#pragma unroll
-  for (int k = 0; k < NZ; ++k) pf<CG>(Zm1 + k * a.ld + nx);
-  if (a.mask != nullptr) pf<CG>(a.mask + nx);
-  if (a.m == 1) pf<CG>(a.Vlo_m1 + nx);
-  if constexpr (HAS_M2) {
-#pragma unroll
-    for (int k = 0; k < NZ; ++k) pf<CG>(Zm2 + k * a.ld + nx);
-    if (a.m == 1) {
-      pf<CG>(a.Vhi_m2 + nx);
-      pf<CG>(a.Vlo_m2 + nx);
-    }
-  }
-}
-
 // Which loads may use the non-coherent (L1) path.  L1 holds no line of a
 // buffer from an earlier launch, so a load can go through L1 unless this
 // launch rewrites a buffer after reading it: the three state buffers rotate
@@ -98,57 +50,8 @@ __device__ __forceinline__ void light_rows(const StageArgs& a, const Ell& A, int
       Vn = ldm<CG>(a.V32m1 + i + B);
 #pragma unroll
       for (int k = 0; k < NZ; ++k) zn[k] = ldm<CG>(Zm1 + k * ld + i + B);
-      if (a.mask != nullptr) pf<CG>(a.mask + i + B);
-      if (a.m == 1) pf<CG>(a.Vlo_m1 + i + B);
-      if constexpr (HAS_M2) {
-#pragma unroll
-        for (int k = 0; k < NZ; ++k) pf<CG>(static_cast<const float*>(a.Zm2) + k * ld + i + B);
-        if (a.m == 1) {
-          pf<CG>(a.Vhi_m2 + i + B);
-          pf<CG>(a.Vlo_m2 + i + B);
-        }
-      }
-      pf_row_of<CG>(A, i + B, i + 2 * B, r1);
     }
     stage_node_mixed_with<Model, HAS_M2, CG>(a, A, i, V, z);
-  }
-}
-
-// Heavy models: the next node's inputs are prefetched (no registers) while
-// the current node's ionic model runs.
-template <class Model, bool HAS_M2, bool CG>
-__device__ __forceinline__ void heavy_rows(const StageArgs& a, const Ell& A, int64_t r0, int64_t r1) {
-  const int64_t B = blockDim.x;
-  for (int64_t i = r0 + threadIdx.x; i < r1; i += B) {
-    if (i + B < r1) {
-      pf_stage_node<Model, HAS_M2, CG>(a, i + B);
-      pf_row_of<CG>(A, i + B, i + 2 * B, r1);
-    }
-    stage_node_mixed<Model, HAS_M2, CG>(a, A, i);
-  }
-}
-
-// Inner items: the next node's increments, V and row of L are prefetched.
-template <bool CG>
-__device__ __forceinline__ void batch_inner_rows(const InnerArgs& b, const Ell& A, int64_t r0, int64_t r1) {
-  const int64_t B = blockDim.x;
-  for (int64_t i = r0 + threadIdx.x; i < r1; i += B) {
-    const int64_t nx = i + B;
-    if (nx < r1) {
-      pf<CG>(b.d1 + nx);
-      if (b.d2 != nullptr) pf<CG>(b.d2 + nx);
-      if (b.lf_src == 0) pf<CG>(b.LV + nx);
-      if (b.last) {
-        pf<CG>(b.Vhi1 + nx);
-        pf<CG>(b.Vlo1 + nx);
-        if (b.Vhi2 != nullptr) {
-          pf<CG>(b.Vhi2 + nx);
-          pf<CG>(b.Vlo2 + nx);
-        }
-      }
-      pf_row_of<CG>(A, nx, nx + B, r1);
-    }
-    inner_node_mixed<CG>(b, A, i);
   }
 }
 
@@ -165,10 +68,13 @@ __device__ __forceinline__ void batch_stage_rows(const StageArgs& a, const Ell& 
     return;
   }
   if (has_m2) {
-    if (cg) heavy_rows<Model, true, true>(a, A, r0, r1);
-    else heavy_rows<Model, true, false>(a, A, r0, r1);
+    if (cg) {
+      for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) stage_node_mixed<Model, true, true>(a, A, i);
+    } else {
+      for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) stage_node_mixed<Model, true, false>(a, A, i);
+    }
   } else {
-    heavy_rows<Model, false, false>(a, A, r0, r1);
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) stage_node_mixed<Model, false, false>(a, A, i);
   }
 }
 
@@ -305,8 +211,11 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) batch_step_kernel(const B
       b.f_inv_eta = I->f_inv_eta;
       b.f_okappa = I->o_kappa[j];
       b.f_omu_dt = I->o_mudt[j];
-      if (s >= 3 || m >= 4) batch_inner_rows<true>(b, I->ell, r0, r1);
-      else batch_inner_rows<false>(b, I->ell, r0, r1);
+      if (s >= 3 || m >= 4) {
+        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) inner_node_mixed<true>(b, I->ell, i);
+      } else {
+        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) inner_node_mixed<false>(b, I->ell, i);
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
