@@ -409,6 +409,9 @@ int emrkc_batch_set_spin_limit(emrkc_batch* b, int64_t limit);
  * EMRKC_ERR_CUDA. */
 int emrkc_batch_set_stimulus_async(emrkc_batch* b, const uint8_t* host_masks, int64_t len);
 int emrkc_batch_get_V_async(emrkc_batch* b, double* host_out, int64_t len);
+/* As emrkc_batch_get_V_async with V rounded to FP32 (the hi part of the
+ * float-float V, its nearest float): half the bytes over the host link. */
+int emrkc_batch_get_V32_async(emrkc_batch* b, float* host_out, int64_t len);
 /* Instance ids in batch order into ids_out (up to cap entries); returns the
  * number of instances (-1 if b is NULL). */
 int emrkc_batch_ids(const emrkc_batch* b, int* ids_out, int cap);

@@ -397,6 +397,14 @@ class Batch:
             raise ValueError("out must be a C-contiguous float64 array")
         self._check(self._lib.emrkc_batch_get_V_async(self._h, _dp(out), out.size))
 
+    def get_V32_async(self, out):
+        """V of every instance rounded to FP32, concatenated in batch order,
+        into ``out`` (float32, complete after sync)."""
+        if out.dtype != np.float32 or not out.flags.c_contiguous:
+            raise ValueError("out must be a C-contiguous float32 array")
+        self._check(self._lib.emrkc_batch_get_V32_async(self._h, out.ctypes.data_as(C.POINTER(C.c_float)),
+                                                        out.size))
+
     def set_profile(self, on=True):
         self._check(self._lib.emrkc_batch_set_profile(self._h, int(on)))
 

@@ -116,6 +116,7 @@ SIGNATURES = {
                                        C.POINTER(C.c_double)]),
     "emrkc_batch_set_stimulus_async": (C.c_int, [_P, C.POINTER(C.c_uint8), C.c_int64]),
     "emrkc_batch_get_V_async": (C.c_int, [_P, _PD, C.c_int64]),
+    "emrkc_batch_get_V32_async": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int64]),
     "emrkc_batch_ids": (C.c_int, [_P, C.POINTER(C.c_int), C.c_int]),
     "emrkc_batch_set_profile": (C.c_int, [_P, C.c_int]),
     "emrkc_batch_get_kernel_time": (C.c_int, [_P, _PD, C.POINTER(C.c_int64)]),

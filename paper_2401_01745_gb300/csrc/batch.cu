@@ -249,6 +249,18 @@ __global__ void __launch_bounds__(256) batch_join_V_kernel(const BatchInst* __re
     o[i] = (double)hi[i] + (double)lo[i];
 }
 
+// The same with V rounded to FP32: the hi part (|lo| is at most half an ulp
+// of hi, so hi is V's nearest float).
+__global__ void __launch_bounds__(256) batch_join_V32_kernel(const BatchInst* __restrict__ inst,
+                                                            const int64_t* __restrict__ off, float* __restrict__ out) {
+  const BatchInst* I = inst + blockIdx.y;
+  const float* __restrict__ hi = I->Vhi[I->cur];
+  const int64_t n = I->n;
+  float* __restrict__ o = out + off[blockIdx.y];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    o[i] = hi[i];
+}
+
 __global__ void __launch_bounds__(256) batch_scatter_mask_kernel(uint8_t* const* __restrict__ masks,
                                                                 const int64_t* __restrict__ off,
                                                                 const uint8_t* __restrict__ src) {
@@ -260,7 +272,12 @@ __global__ void __launch_bounds__(256) batch_scatter_mask_kernel(uint8_t* const*
 
 void launch_batch_join_V(const BatchInst* inst, const int64_t* off, int ni, double* out, cudaStream_t st) {
   if (ni <= 0) return;
-  batch_join_V_kernel<<<dim3(64, (unsigned)ni), 256, 0, st>>>(inst, off, out);
+  batch_join_V_kernel<<<dim3(128, (unsigned)ni), 256, 0, st>>>(inst, off, out);
+}
+
+void launch_batch_join_V32(const BatchInst* inst, const int64_t* off, int ni, float* out, cudaStream_t st) {
+  if (ni <= 0) return;
+  batch_join_V32_kernel<<<dim3(128, (unsigned)ni), 256, 0, st>>>(inst, off, out);
 }
 
 void launch_batch_scatter_mask(uint8_t* const* masks, const int64_t* off, int ni, const uint8_t* src,

@@ -713,7 +713,11 @@ int emrkc_batch_set_stimulus_async(emrkc_batch* b, const uint8_t* host_masks, in
   return EMRKC_OK;
 }
 
-int emrkc_batch_get_V_async(emrkc_batch* b, double* host_out, int64_t len) {
+namespace {
+// V of every instance into host_out (doubles, or floats when f32) through a
+// staging buffer: the join on the batch's stream, the copy on the
+// device-to-host stream (the two staging buffers rotate).
+int get_V_async(emrkc_batch* b, void* host_out, int64_t len, bool f32) {
   if (!b) return EMRKC_ERR_ARG;
   if (!host_out) return b->fail(EMRKC_ERR_ARG, "null buffer");
   cudaSetDevice(b->device);
@@ -729,18 +733,29 @@ int emrkc_batch_get_V_async(emrkc_batch* b, double* host_out, int64_t len) {
   // the staging buffer is refilled only after its previous copy-out
   if (b->vfree_rec[k] && (e = cudaStreamWaitEvent(b->stream, b->ev_vfree[k], 0)) != cudaSuccess)
     return b->cuda_fail(e, "state copy ordering");
-  launch_batch_join_V(b->d_inst, b->d_off, (int)b->members.size(), b->d_vstage[k], b->stream);
+  const int ni = (int)b->members.size();
+  if (f32) launch_batch_join_V32(b->d_inst, b->d_off, ni, reinterpret_cast<float*>(b->d_vstage[k]), b->stream);
+  else launch_batch_join_V(b->d_inst, b->d_off, ni, b->d_vstage[k], b->stream);
   if ((e = cudaGetLastError()) != cudaSuccess) return b->cuda_fail(e, "state staging");
   if ((e = cudaEventRecord(b->ev_vready[k], b->stream)) != cudaSuccess) return b->cuda_fail(e, "state staging");
   if ((e = cudaStreamWaitEvent(b->d2h_stream, b->ev_vready[k], 0)) != cudaSuccess)
     return b->cuda_fail(e, "state copy ordering");
-  if ((e = cudaMemcpyAsync(host_out, b->d_vstage[k], (size_t)len * sizeof(double), cudaMemcpyDeviceToHost,
-                           b->d2h_stream)) != cudaSuccess)
+  const size_t bytes = (size_t)len * (f32 ? sizeof(float) : sizeof(double));
+  if ((e = cudaMemcpyAsync(host_out, b->d_vstage[k], bytes, cudaMemcpyDeviceToHost, b->d2h_stream)) != cudaSuccess)
     return b->cuda_fail(e, "state copy");
   if ((e = cudaEventRecord(b->ev_vfree[k], b->d2h_stream)) != cudaSuccess) return b->cuda_fail(e, "state copy");
   b->vfree_rec[k] = true;
   b->vk = k ^ 1;
   return EMRKC_OK;
+}
+}  // namespace
+
+int emrkc_batch_get_V_async(emrkc_batch* b, double* host_out, int64_t len) {
+  return get_V_async(b, host_out, len, false);
+}
+
+int emrkc_batch_get_V32_async(emrkc_batch* b, float* host_out, int64_t len) {
+  return get_V_async(b, host_out, len, true);
 }
 
 int emrkc_batch_ids(const emrkc_batch* b, int* ids_out, int cap) {

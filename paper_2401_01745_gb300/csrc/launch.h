@@ -370,6 +370,7 @@ int batch_blocks_per_sm(int block);
 // double) into out[off[k] ...]; node masks from src[off[k] ...] into each
 // instance's mask buffer.  ni instances, off has ni + 1 entries.
 void launch_batch_join_V(const BatchInst* inst, const int64_t* off, int ni, double* out, cudaStream_t st);
+void launch_batch_join_V32(const BatchInst* inst, const int64_t* off, int ni, float* out, cudaStream_t st);
 void launch_batch_scatter_mask(uint8_t* const* masks, const int64_t* off, int ni, const uint8_t* src,
                                cudaStream_t st);
 

@@ -188,6 +188,12 @@ def test_batch_pipelined_io_matches_waiting_calls():
             ref = np.concatenate([a.get_state(i, var=0) for i in ia])
             got.append(np.array_equal(ring[k % 2], ref))
     assert all(got)
+    # V rounded to FP32: the nearest float of the V that get_state returns
+    v32 = np.empty(total, dtype=np.float32)
+    b.get_V32_async(v32)
+    b.sync()
+    ref = np.concatenate([b.get_state(i, var=0) for i in b.ids()])
+    assert np.all(np.abs(v32.astype(np.float64) - ref) <= np.spacing(np.abs(v32)) * 0.5000001)
     with pytest.raises(pkg.EmrkcError):
         b.get_V_async(np.empty(total - 1))
     a.close()

@@ -143,3 +143,50 @@ def test_served_results_match_oracle():
                             rho_S_min=42.0 if req["model"] == pkg.MODEL_HH else 0.0)
         assert res.steps == req["steps"]
         _check(prob, ref, res.V, None)
+
+
+def test_full_batch_sampled_instances_match_oracle():
+    """The batched workload at full size (256 instances, 31.2M nodes) in the
+    launch configuration the benchmark times (autotuned tile and block, graph
+    replay), 40 steps from rest: the smallest 2-D and 3-D instances of each
+    ionic model (TTP06 with s = 1 and m = 1 or 2, HH with s = 2, m = 1)
+    against the oracle element by element; every instance finite, within the
+    physiological range of its model, and with the same step count and time."""
+    from workloads.configs import batched_specs, batched_workload
+
+    dt, steps = 0.05, 40
+    specs = batched_specs(256)
+    b = pkg.Batch(rho_every=pkg.RHO_ONCE)
+    for sp in specs:
+        b.add_workload(batched_workload(sp), rho_S_min=42.0 if sp["model"] == pkg.MODEL_HH else 0.0)
+    for _ in range(3):
+        b.step(dt)
+    b.sync()
+    b.autotune(dt, reps=2)
+    for _ in range(steps - 3):
+        b.step(dt)
+    b.sync()
+    ids = b.ids()
+    assert len(ids) == 256 and b.stats()["total_nodes"] == 31163705
+    for iid in ids:
+        info = b.info(iid)
+        assert info["steps"] == steps and abs(info["t"] - steps * dt) < 1e-9
+        V = b.get_state(iid, var=0)
+        assert np.all(np.isfinite(V)) and V.min() > -100.0 and V.max() < 80.0
+    # the sample: smallest 2-D and 3-D instances of each model
+    sample = {}
+    for sp in specs:
+        key = (sp["model"], len(sp["dims"]))
+        n = int(np.prod(sp["dims"]))
+        if key not in sample or n < sample[key][0]:
+            sample[key] = (n, sp)
+    assert len(sample) == 4
+    for (model, dim), (n, sp) in sorted(sample.items()):
+        w = batched_workload(sp)
+        iid = ids[sp["index"]]
+        rmin = 42.0 if model == pkg.MODEL_HH else 0.0
+        prob, ref = _oracle(w, steps, dt, rho_every=0, rho_S_min=rmin)
+        info = b.info(iid)
+        assert (info["s"], info["m"]) == (ref.log[-1][0], ref.log[-1][1])
+        _check(prob, ref, b.get_state(iid, var=0), b.activation_times(iid))
+    b.close()
