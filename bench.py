@@ -500,7 +500,8 @@ def batched_line(args, world, rank, local, dev):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "precision": MIXED_PRECISION_TEXT,
                    "persistent_launches_per_step": launches / args.steps,
-                   "tile": tile, "block": block, "grid": st["grid"], "items_per_step": st["items"],
+                   "tile": tile, "block": block, "schedule": st["schedule"], "grid": st["grid"],
+                   "items_per_step": st["items"],
                    "stage_counts": _stage_count_summary(b, specs),
                    "setup_s": setup_s, "device_gb": st["device_bytes"] / 1e9,
                    "l2": "not flushed: the working set (state and matrices, GBs) is far larger than L2 (129 MB)"},

@@ -351,6 +351,9 @@ typedef struct {
   int tile, block, grid;/* launch configuration in use            */
   int64_t launches;     /* persistent launches so far             */
   int64_t device_bytes; /* all instances plus the batch tables    */
+  int schedule;         /* order of the work list: 0 whole phases,
+                           1 / 2 at most 16 / 4 tiles per instance
+                           in turn (chosen by the autotuner)       */
 } emrkc_batch_stats;
 
 /* Options: device, cuda_stream, seed, act_threshold, rho_every (ONCE or
@@ -378,7 +381,7 @@ int emrkc_batch_get_info(emrkc_batch* b, int id, emrkc_batch_info* out);
 int emrkc_batch_get_stats(emrkc_batch* b, emrkc_batch_stats* out);
 /* Launch configuration: tile in {256, 512, ..., 8192} nodes, block 128 or 256. */
 int emrkc_batch_set_config(emrkc_batch* b, int tile, int block);
-/* Time each (tile, block) candidate over `reps` steps of size dt without
+/* Time each (tile, block, work-list order) candidate over `reps` steps of size dt without
  * advancing any instance (the candidates run with bookkeeping and
  * activation writes disabled) and keep the fastest.  Returns EMRKC_ERR_STATE
  * (configuration unchanged) if an instance has s >= 3, whose dry steps would

@@ -64,7 +64,7 @@ class BatchInfo(C.Structure):
 class BatchStats(C.Structure):
     _fields_ = [("instances", C.c_int), ("total_nodes", C.c_int64), ("items", C.c_int64),
                 ("tile", C.c_int), ("block", C.c_int), ("grid", C.c_int), ("launches", C.c_int64),
-                ("device_bytes", C.c_int64)]
+                ("device_bytes", C.c_int64), ("schedule", C.c_int)]
 
 
 _P = C.c_void_p

@@ -54,6 +54,7 @@ struct emrkc_batch {
   size_t done_cap = 0;
   int* d_err = nullptr;
   int tile = 1024, block = 128, grid = 0;
+  int sched = 0;  // order of the work list (rebuild)
   long long spin_limit = 1 << 24;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -240,28 +241,53 @@ int rebuild(emrkc_batch* b, double dt) {
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
   b->grid = std::max(1, sms * std::max(1, batch_blocks_per_sm(b->block)));
+  // Schedule 0 emits an instance's whole phase at once (the first ready
+  // instance in index order); schedules 1 and 2 emit at most 16 or 4 tiles of
+  // an instance before moving on to the next ready instance (cyclically), so
+  // that tiles of different instances, models and phases interleave finely.
   std::vector<uint64_t> items;
   {
     const int64_t lag = 2 * (int64_t)std::max(b->grid, 1);
-    std::vector<int> next(ni, 0);
+    const int chunk = b->sched == 1 ? 16 : b->sched == 2 ? 4 : (1 << 30);
+    std::vector<int> next(ni, 0), tnext(ni, 0);
     std::vector<int64_t> ready(ni, 0);
     size_t left = ni;
     int64_t now = 0;
+    size_t cursor = 0;
     while (left > 0) {
       int best = -1;
-      for (size_t i = 0; i < ni; ++i) {
-        if (next[i] >= b->h_inst[i].P) continue;
-        if (best < 0 || ready[i] < ready[best]) best = (int)i;
-        if (ready[i] <= now) {
-          best = (int)i;
-          break;
+      if (b->sched == 0) {
+        for (size_t i = 0; i < ni; ++i) {
+          if (next[i] >= b->h_inst[i].P) continue;
+          if (best < 0 || ready[i] < ready[best]) best = (int)i;
+          if (ready[i] <= now) {
+            best = (int)i;
+            break;
+          }
         }
+      } else {
+        for (size_t q = 0; q < ni; ++q) {
+          const size_t i = (cursor + q) % ni;
+          if (next[i] >= b->h_inst[i].P) continue;
+          if (best < 0 || ready[i] < ready[best]) best = (int)i;
+          if (ready[i] <= now) {
+            best = (int)i;
+            break;
+          }
+        }
+        cursor = (size_t)best + 1;
       }
       const int p = next[best];
-      for (int t = 0; t < b->h_inst[best].ntiles; ++t) items.push_back(batch_item(best, p, t));
-      now = std::max(now, ready[best]) + b->h_inst[best].ntiles;
-      ready[best] = now + lag;
-      if (++next[best] >= b->h_inst[best].P) --left;
+      const int nt = b->h_inst[best].ntiles;
+      const int t1 = std::min(nt, tnext[best] + chunk);
+      for (int t = tnext[best]; t < t1; ++t) items.push_back(batch_item(best, p, t));
+      now = std::max(now, ready[best]) + (t1 - tnext[best]);
+      tnext[best] = t1;
+      if (t1 == nt) {
+        tnext[best] = 0;
+        ready[best] = now + lag;
+        if (++next[best] >= b->h_inst[best].P) --left;
+      }
     }
   }
   if (items.size() >= 0xffffffffull) return b->fail(EMRKC_ERR_ARG, "too many work items");
@@ -547,6 +573,7 @@ int emrkc_batch_get_stats(emrkc_batch* b, emrkc_batch_stats* out) {
   out->block = b->block;
   out->grid = b->grid;
   out->launches = b->launches;
+  out->schedule = b->sched;
   return EMRKC_OK;
 }
 
@@ -573,30 +600,36 @@ int emrkc_batch_autotune(emrkc_batch* b, double dt, int reps, int* tile_out, int
     if (mb.S >= 3) return b->fail(EMRKC_ERR_STATE, "an instance has s >= 3: dry steps would overwrite its state");
   const int tiles[] = {512, 1024, 2048, 4096, 8192};
   const int blocks[] = {128, 256};
-  const int keep_tile = b->tile, keep_block = b->block;
-  int best_tile = keep_tile, best_block = keep_block;
+  const int scheds[] = {0, 1, 2};
+  const int keep_tile = b->tile, keep_block = b->block, keep_sched = b->sched;
+  int best_tile = keep_tile, best_block = keep_block, best_sched = keep_sched;
   double best = 1e300;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (int tl : tiles) {
-    for (int bl : blocks) {
-      b->tile = tl;
-      b->block = bl;
-      if ((rc = rebuild(b, dt))) break;
-      if ((rc = enqueue_step(b, 1))) break;
-      cudaEventRecord(e0, b->stream);
-      for (int r = 0; r < reps && !rc; ++r) rc = enqueue_step(b, 1);
-      cudaEventRecord(e1, b->stream);
-      cudaEventSynchronize(e1);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      const double per = ms / reps;
-      if (per < best) {
-        best = per;
-        best_tile = tl;
-        best_block = bl;
+  for (int sc : scheds) {
+    for (int tl : tiles) {
+      for (int bl : blocks) {
+        b->tile = tl;
+        b->block = bl;
+        b->sched = sc;
+        if ((rc = rebuild(b, dt))) break;
+        if ((rc = enqueue_step(b, 1))) break;
+        cudaEventRecord(e0, b->stream);
+        for (int r = 0; r < reps && !rc; ++r) rc = enqueue_step(b, 1);
+        cudaEventRecord(e1, b->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = ms / reps;
+        if (per < best) {
+          best = per;
+          best_tile = tl;
+          best_block = bl;
+          best_sched = sc;
+        }
       }
+      if (rc) break;
     }
     if (rc) break;
   }
@@ -604,10 +637,12 @@ int emrkc_batch_autotune(emrkc_batch* b, double dt, int reps, int* tile_out, int
   cudaEventDestroy(e1);
   b->tile = best_tile;
   b->block = best_block;
+  b->sched = best_sched;
   b->dirty = true;
   if (rc) {
     b->tile = keep_tile;
     b->block = keep_block;
+    b->sched = keep_sched;
     return rc;
   }
   int err = 0;
