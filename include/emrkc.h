@@ -381,6 +381,9 @@ int emrkc_batch_get_info(emrkc_batch* b, int id, emrkc_batch_info* out);
 int emrkc_batch_get_stats(emrkc_batch* b, emrkc_batch_stats* out);
 /* Launch configuration: tile in {256, 512, ..., 8192} nodes, block 128 or 256. */
 int emrkc_batch_set_config(emrkc_batch* b, int tile, int block);
+/* Order of the work list: 0 (default) an instance's whole phase at a time,
+ * 1 / 2 at most 16 / 4 tiles of an instance before the next ready one. */
+int emrkc_batch_set_schedule(emrkc_batch* b, int schedule);
 /* Time each (tile, block, work-list order) candidate over `reps` steps of size dt without
  * advancing any instance (the candidates run with bookkeeping and
  * activation writes disabled) and keep the fastest.  Returns EMRKC_ERR_STATE

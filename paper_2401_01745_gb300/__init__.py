@@ -365,6 +365,9 @@ class Batch:
     def set_config(self, tile, block):
         self._check(self._lib.emrkc_batch_set_config(self._h, tile, block))
 
+    def set_schedule(self, schedule):
+        self._check(self._lib.emrkc_batch_set_schedule(self._h, schedule))
+
     def set_spin_limit(self, limit):
         self._check(self._lib.emrkc_batch_set_spin_limit(self._h, limit))
 

@@ -112,6 +112,7 @@ SIGNATURES = {
     "emrkc_batch_get_stats": (C.c_int, [_P, C.POINTER(BatchStats)]),
     "emrkc_batch_set_config": (C.c_int, [_P, C.c_int, C.c_int]),
     "emrkc_batch_set_spin_limit": (C.c_int, [_P, C.c_int64]),
+    "emrkc_batch_set_schedule": (C.c_int, [_P, C.c_int]),
     "emrkc_batch_autotune": (C.c_int, [_P, C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                        C.POINTER(C.c_double)]),
     "emrkc_batch_set_stimulus_async": (C.c_int, [_P, C.POINTER(C.c_uint8), C.c_int64]),

@@ -589,6 +589,16 @@ int emrkc_batch_set_config(emrkc_batch* b, int tile, int block) {
   return EMRKC_OK;
 }
 
+int emrkc_batch_set_schedule(emrkc_batch* b, int schedule) {
+  if (!b) return EMRKC_ERR_ARG;
+  if (schedule < 0 || schedule > 2) return b->fail(EMRKC_ERR_ARG, "schedule must be 0, 1 or 2");
+  if (schedule != b->sched) {
+    b->sched = schedule;
+    b->dirty = true;
+  }
+  return EMRKC_OK;
+}
+
 int emrkc_batch_autotune(emrkc_batch* b, double dt, int reps, int* tile_out, int* block_out, double* ms_out) {
   if (!b) return EMRKC_ERR_ARG;
   if (!(dt > 0) || reps < 1) return b->fail(EMRKC_ERR_ARG, "dt > 0 and reps >= 1 required");
