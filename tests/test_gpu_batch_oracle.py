@@ -190,3 +190,25 @@ def test_full_batch_sampled_instances_match_oracle():
         assert (info["s"], info["m"]) == (ref.log[-1][0], ref.log[-1][1])
         _check(prob, ref, b.get_state(iid, var=0), b.activation_times(iid))
     b.close()
+
+
+def test_batch_tiny_and_empty():
+    """Degenerate batches: no instance at all (steps are no-ops), and
+    instances of 2, 3 and 4 nodes (one ragged sliced-ELL slice, a single
+    tile) beside a larger one, each against the oracle."""
+    b = pkg.Batch()
+    b.step(0.05)
+    b.sync()
+    assert b.stats()["instances"] == 0 and b.stats()["launches"] == 0
+    dt, steps = 0.05, 30
+    names = ["line2_hh", "line3_ttp", "square2x2_hh", "slab23x9x5_ttp"]
+    ws = [make_workload(n) if n != "slab23x9x5_ttp" else make_workload(n, h=0.01) for n in names]
+    rmins = [42.0 if w.model == pkg.MODEL_HH else 0.0 for w in ws]
+    ids = [b.add_workload(w, rho_S_min=r) for w, r in zip(ws, rmins)]
+    for _ in range(steps):
+        b.step(dt)
+    b.sync()
+    for iid, w, r in zip(ids, ws, rmins):
+        prob, ref = _oracle(w, steps, dt, rho_every=0, rho_S_min=r)
+        _check(prob, ref, b.get_state(iid, var=0), b.activation_times(iid))
+    b.close()
