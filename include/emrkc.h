@@ -157,6 +157,15 @@ typedef struct {
   double lin_rtol;    /* IMEX-RL: relative residual of the CG solve, 1e-10  */
   int lin_max_iter;   /* IMEX-RL: CG iteration cap, 1000 (a solve that hits
                          it is not an error; see emrkc_stats.lin_iters)     */
+  double pow_tol_cold;   /* Algorithm 5 with no initial guess (the first
+                            estimate of rho_F or rho_S, from the arbitrary
+                            start vector): relative tolerance 1e-4.  The
+                            warm-started calls that follow use pow_tol.
+                            From a cold start the 1e-2 test of App. A can
+                            stop on an early plateau (0.80-0.97 of rho(L)
+                            measured on 3-D slabs), below what the safety
+                            factor covers                                 */
+  int pow_max_iter_cold; /* iteration cap of a cold start, 1000            */
 } emrkc_options;
 
 /* Kernel classes reported in emrkc_stats.phase_ms / phase_launches. */
@@ -190,7 +199,8 @@ typedef struct {
 
 /* Fill *opt with the defaults listed above (FP64, rho every step, seed 0,
  * threshold -20 mV, NULL stream, device 0, no profiling, graphs on,
- * rho_S_min 0, method EMRKC_METHOD_EMRKC, lin_rtol 1e-10, lin_max_iter 1000). */
+ * rho_S_min 0, method EMRKC_METHOD_EMRKC, lin_rtol 1e-10, lin_max_iter 1000,
+ * pow_tol_cold 1e-4, pow_max_iter_cold 1000). */
 int emrkc_default_options(emrkc_options* opt);
 
 /* Number of state variables N (V included) of an ionic model, or -1. */

@@ -82,7 +82,8 @@ class Solver:
                  amplitude=50.0, t_on=0.0, t_off=1.0, precision=PREC_FP64, rho_every=1,
                  rho_F=0.0, rho_S=0.0, seed=0, act_threshold=-20.0, stream=None, device=0,
                  profile=False, use_graphs=True, pow_tol=1e-2, pow_max_iter=50, safety=1.05,
-                 rho_S_min=0.0, method=0, lin_rtol=1e-10, lin_max_iter=1000):
+                 rho_S_min=0.0, method=0, lin_rtol=1e-10, lin_max_iter=1000, pow_tol_cold=1e-4,
+                 pow_max_iter_cold=1000):
         self._lib = lib()
         self._h = C.c_void_p()
         self.row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
@@ -115,6 +116,8 @@ class Solver:
         o.use_graphs = int(use_graphs)
         o.pow_tol = pow_tol
         o.pow_max_iter = pow_max_iter
+        o.pow_tol_cold = pow_tol_cold
+        o.pow_max_iter_cold = pow_max_iter_cold
         o.safety = safety
         o.rho_S_min = rho_S_min
         o.method = method

@@ -43,7 +43,7 @@ class Options(C.Structure):
                 ("seed", C.c_uint64), ("act_threshold", C.c_double), ("cuda_stream", C.c_void_p),
                 ("device", C.c_int), ("profile", C.c_int), ("use_graphs", C.c_int),
                 ("rho_S_min", C.c_double), ("method", C.c_int), ("lin_rtol", C.c_double),
-                ("lin_max_iter", C.c_int)]
+                ("lin_max_iter", C.c_int), ("pow_tol_cold", C.c_double), ("pow_max_iter_cold", C.c_int)]
 
 
 class Stats(C.Structure):

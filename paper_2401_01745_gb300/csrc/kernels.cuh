@@ -1198,8 +1198,8 @@ __global__ void __launch_bounds__(kReduceBlock) power_fused_kernel(const PowerFu
   // The scalars of Algorithm 5 (norms, q, rho, the stopping test) are
   // computed by thread 0 and shared: they are FP64, and GB300's FP64 pipe is
   // narrow, so the other threads must not repeat them.
-  __shared__ double s_q, s_rho, s_delta;
-  __shared__ int s_go, s_it;
+  __shared__ double s_q, s_rho, s_delta, s_tol;
+  __shared__ int s_go, s_it, s_maxit;
   // squared norms of y_F, v_F, y_S, v_S (the same value in every thread)
   const double nsum[4] = {sum_partials(part(par), G, 0, sh), sum_partials(part(par), G, 1, sh),
                           sum_partials(part(par), G, 2, sh), sum_partials(part(par), G, 3, sh)};
@@ -1208,18 +1208,21 @@ __global__ void __launch_bounds__(kReduceBlock) power_fused_kernel(const PowerFu
   // one power iteration per loop trip: v_new = f(y + q v) - f(y) (FP64 path)
   // or q J v (mixed path), rho = |v_new| / delta, until the relative change
   // of rho is below tol or max_iter iterations
+  // no initial guess (warm value 0): the cold-start tolerance and cap
   auto start = [&](double ny2, double nv2, double warm) {
     if (threadIdx.x == 0) {
       const double ny = sqrt(ny2), nv = sqrt(nv2);
       s_delta = ny > 0.0 ? ny * a.eps : a.eps;
       s_rho = warm;
       s_it = 0;
+      s_tol = warm == 0.0 ? a.tol_cold : a.tol;
+      s_maxit = warm == 0.0 ? a.max_iter_cold : a.max_iter;
       if (nv == 0.0) {
         s_rho = 0.0;
         s_go = 0;
       } else {
         s_q = s_delta / nv;
-        s_go = (fabs(warm) >= a.tol * warm && a.max_iter > 0) ? 1 : 0;
+        s_go = (fabs(warm) >= s_tol * warm && s_maxit > 0) ? 1 : 0;
       }
     }
     __syncthreads();
@@ -1235,7 +1238,7 @@ __global__ void __launch_bounds__(kReduceBlock) power_fused_kernel(const PowerFu
         const double rho_old = s_rho;
         s_q = s_delta / nv;
         s_rho = nv / s_delta;
-        s_go = (fabs(s_rho - rho_old) >= a.tol * s_rho && s_it < a.max_iter) ? 1 : 0;
+        s_go = (fabs(s_rho - rho_old) >= s_tol * s_rho && s_it < s_maxit) ? 1 : 0;
       }
     }
     __syncthreads();

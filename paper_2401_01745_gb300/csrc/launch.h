@@ -166,6 +166,8 @@ struct PowerFusedArgs {
   double stim = 0, Cm = 1;
   double eps = 1e-8, tol = 1e-2;
   int max_iter = 50;
+  double tol_cold = 1e-4;        // a start with warm value 0 (no initial guess)
+  int max_iter_cold = 1000;
   double rhoF_warm = 0, rhoS_warm = 0;
   double* part = nullptr;              // 2 x 4 x grid partial sums
   unsigned int* bar = nullptr;         // grid barrier
@@ -373,6 +375,8 @@ void launch_batch_join_V(const BatchInst* inst, const int64_t* off, int ni, doub
 void launch_batch_join_V32(const BatchInst* inst, const int64_t* off, int ni, float* out, cudaStream_t st);
 void launch_batch_scatter_mask(uint8_t* const* masks, const int64_t* off, int ni, const uint8_t* src,
                                cudaStream_t st);
+// out[k] = the flag word of instance k (bit 0: non-finite V), ni instances.
+void launch_batch_gather_flags(const BatchInst* inst, int ni, int* out, cudaStream_t st);
 
 // Allocation-free power iteration on f_F (noalloc.cu): static device scratch.
 int noalloc_scratch(int device, cudaStream_t st, ReduceScratch* out, const char** why);

@@ -103,6 +103,16 @@ void materialise_V(emrkc_solver* s) {
   if (s->d_V32[s->cur]) launch_ff_join(s->d_V32[s->cur], s->d_Vlo[s->cur], s->d_V[s->cur], s->n, s->stream);
 }
 
+// Stopping test of Algorithm 5: a call with no initial guess (rho still 0)
+// is a cold start from the arbitrary start vector and takes the tighter
+// tolerance; warm-started calls take the App. A tolerance.
+double pow_tol_for(const emrkc_solver* s, double rho_warm) {
+  return rho_warm == 0.0 ? s->opt.pow_tol_cold : s->opt.pow_tol;
+}
+int pow_max_iter_for(const emrkc_solver* s, double rho_warm) {
+  return rho_warm == 0.0 ? s->opt.pow_max_iter_cold : s->opt.pow_max_iter;
+}
+
 double stim_at(const emrkc_solver* s, double t) {
   return (s->d_mask != nullptr && s->t_on <= t && t <= s->t_off) ? s->amp : 0.0;
 }
@@ -132,8 +142,10 @@ int power_F(emrkc_solver* s) {
     s->itF = 0;
     return EMRKC_OK;
   }
+  const double tol = pow_tol_for(s, rho);
+  const int max_iter = pow_max_iter_for(s, rho);
   double q = delta / nv, rho_old = 0.0;
-  while (std::fabs(rho - rho_old) >= s->opt.pow_tol * rho && it < s->opt.pow_max_iter) {
+  while (std::fabs(rho - rho_old) >= tol * rho && it < max_iter) {
     rho_old = rho;
     if (mrkc) {
       MrkcPowerArgs a;
@@ -209,8 +221,10 @@ int power_S(emrkc_solver* s) {
     s->itS = 0;
     return EMRKC_OK;
   }
+  const double tol = pow_tol_for(s, rho);
+  const int max_iter = pow_max_iter_for(s, rho);
   double q = delta / nv, rho_old = 0.0;
-  while (std::fabs(rho - rho_old) >= s->opt.pow_tol * rho && it < s->opt.pow_max_iter) {
+  while (std::fabs(rho - rho_old) >= tol * rho && it < max_iter) {
     rho_old = rho;
     a.v_old = s->d_vS;
     a.v_new = s->d_vS2;
@@ -326,6 +340,8 @@ int power_fused(emrkc_solver* s) {
   a.eps = s->opt.pow_eps;
   a.tol = s->opt.pow_tol;
   a.max_iter = s->opt.pow_max_iter;
+  a.tol_cold = s->opt.pow_tol_cold;
+  a.max_iter_cold = s->opt.pow_max_iter_cold;
   a.rhoF_warm = s->rhoF_raw;
   a.rhoS_warm = s->rhoS_raw;
   a.part = s->d_ppart;
@@ -826,6 +842,8 @@ int emrkc_default_options(emrkc_options* o) {
   o->method = EMRKC_METHOD_EMRKC;
   o->lin_rtol = 1e-10;
   o->lin_max_iter = 1000;
+  o->pow_tol_cold = 1e-4;
+  o->pow_max_iter_cold = 1000;
   return EMRKC_OK;
 }
 
@@ -873,7 +891,7 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
     return EMRKC_ERR_ARG;
   }
   if (o.rho_every < EMRKC_RHO_FIXED || !(o.eps > 0) || !(o.safety > 0) || !(o.pow_tol > 0) || !(o.pow_eps > 0) ||
-      o.pow_max_iter < 1) {
+      o.pow_max_iter < 1 || !(o.pow_tol_cold > 0) || o.pow_max_iter_cold < 1) {
     g_create_error = "options: invalid rho policy or power-iteration parameters";
     return EMRKC_ERR_ARG;
   }
@@ -1377,8 +1395,10 @@ int emrkc_estimate_rho_F_noalloc(emrkc_solver* s, double* d_v, double* d_w, int6
   }
   double* cur = d_v;
   double* nxt = d_w;
+  const double tol = pow_tol_for(s, rho);
+  const int max_iter = pow_max_iter_for(s, rho);
   double q = delta / nv, rho_old = 0.0;
-  while (std::fabs(rho - rho_old) >= s->opt.pow_tol * rho && it < s->opt.pow_max_iter) {
+  while (std::fabs(rho - rho_old) >= tol * rho && it < max_iter) {
     rho_old = rho;
     PowerFArgs a;
     a.n = n;
