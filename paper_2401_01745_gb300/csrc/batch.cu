@@ -270,6 +270,17 @@ __global__ void __launch_bounds__(256) batch_scatter_mask_kernel(uint8_t* const*
     dst[i] = src[o + i];
 }
 
+__global__ void __launch_bounds__(256) batch_gather_flags_kernel(const BatchInst* __restrict__ inst, int ni,
+                                                                int* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < ni) out[k] = *inst[k].flags;
+}
+
+void launch_batch_gather_flags(const BatchInst* inst, int ni, int* out, cudaStream_t st) {
+  if (ni <= 0) return;
+  batch_gather_flags_kernel<<<(unsigned)((ni + 255) / 256), 256, 0, st>>>(inst, ni, out);
+}
+
 void launch_batch_join_V(const BatchInst* inst, const int64_t* off, int ni, double* out, cudaStream_t st) {
   if (ni <= 0) return;
   batch_join_V_kernel<<<dim3(128, (unsigned)ni), 256, 0, st>>>(inst, off, out);

@@ -85,6 +85,11 @@ struct emrkc_batch {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pending, prof_pool;
   double kernel_ms = 0.0;
   int64_t kernel_launches = 0;
+  // every instance's flag word gathered into one device array and read with
+  // one copy at emrkc_batch_sync
+  int* d_flagv = nullptr;
+  int* h_flagv = nullptr;
+  size_t flagv_cap = 0;
 
   int fail(int code, const std::string& m) {
     err = m;
@@ -509,6 +514,37 @@ int emrkc_batch_sync(emrkc_batch* b) {
     if (cs && (e = cudaStreamSynchronize(cs)) != cudaSuccess) return b->cuda_fail(e, "copy stream synchronisation");
   }
   b->harvest();
+  const size_t ni = b->members.size();
+  if (ni > 0 && !b->dirty && b->h_inst.size() == ni) {
+    // the device table lists every member: one gather of the flag words and
+    // one copy instead of a copy and a synchronisation per instance
+    if (b->flagv_cap < ni) {
+      if (b->d_flagv) cudaFree(b->d_flagv);
+      if (b->h_flagv) cudaFreeHost(b->h_flagv);
+      b->d_flagv = nullptr;
+      b->h_flagv = nullptr;
+      b->flagv_cap = 0;
+      if (cudaMalloc(&b->d_flagv, ni * sizeof(int)) != cudaSuccess ||
+          cudaMallocHost(&b->h_flagv, ni * sizeof(int)) != cudaSuccess)
+        return b->fail(EMRKC_ERR_OOM, "flag array allocation failed");
+      b->flagv_cap = ni;
+    }
+    launch_batch_gather_flags(b->d_inst, (int)ni, b->d_flagv, b->stream);
+    if ((e = cudaGetLastError()) != cudaSuccess) return b->cuda_fail(e, "flag gather");
+    if ((e = cudaMemcpyAsync(b->h_flagv, b->d_flagv, ni * sizeof(int), cudaMemcpyDeviceToHost, b->stream)) !=
+        cudaSuccess)
+      return b->cuda_fail(e, "copy of flags");
+    if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return b->cuda_fail(e, "stream synchronisation");
+    for (size_t i = 0; i < ni; ++i) {
+      if (b->h_flagv[i] == 0) continue;
+      // the instance's own check reads, reports and clears its flag word
+      Member& mb = b->members[i];
+      int rc = emrkc_sync(mb.s);
+      if (rc == EMRKC_ERR_NONFINITE) return b->fail(rc, "instance " + std::to_string(mb.id) + ": non-finite V");
+      if (rc) return b->fail(rc, mb.s->err);
+    }
+    return EMRKC_OK;
+  }
   for (auto& mb : b->members) {
     int rc = emrkc_sync(mb.s);
     if (rc == EMRKC_ERR_NONFINITE) return b->fail(rc, "instance " + std::to_string(mb.id) + ": non-finite V");
@@ -848,9 +884,10 @@ void emrkc_batch_destroy(emrkc_batch* b) {
   }
   void* ptrs[] = {b->d_inst,       b->d_items,      b->d_ticket,     b->d_done,       b->d_err,
                   b->d_off,        b->d_masks,      b->d_mstage[0],  b->d_mstage[1],  b->d_vstage[0],
-                  b->d_vstage[1]};
+                  b->d_vstage[1],  b->d_flagv};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (b->h_flagv) cudaFreeHost(b->h_flagv);
   cudaEvent_t evs[] = {b->ev_mready[0], b->ev_mready[1], b->ev_mfree[0], b->ev_mfree[1],
                        b->ev_vready[0], b->ev_vready[1], b->ev_vfree[0], b->ev_vfree[1]};
   for (cudaEvent_t ev : evs)

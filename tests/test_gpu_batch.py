@@ -158,6 +158,32 @@ def test_dependency_wait_timeout_is_reported():
     b.close()
 
 
+def test_non_finite_instance_is_reported_by_id():
+    """An instance whose fixed rho_F is far below rho(f_F) (m = 1 with
+    dt rho(f_F) ~ 6, so the highest diffusion modes grow every step) overflows.
+    emrkc_batch_sync, which reads every instance's flag word with one copy,
+    names that instance by its id; once it leaves, the batch steps on cleanly
+    and the other instance equals its solo run."""
+    good = make_workload("slab23x9x5_ttp", h=0.01)
+    bad = make_workload("slab19x11x9_hh", h=0.01)
+    b = pkg.Batch()
+    ig = b.add_workload(good)
+    ib = b.add_workload(bad, rho_every=pkg.RHO_FIXED, rho_F=1.0, rho_S=1.0)
+    for _ in range(40):
+        b.step(0.05)
+    with pytest.raises(pkg.EmrkcError) as ei:
+        b.sync()
+    assert ei.value.code == 4 and f"instance {ib}:" in str(ei.value)
+    b.remove(ib)
+    for _ in range(10):
+        b.step(0.05)
+    b.sync()
+    Y = b.get_state(ig)
+    b.close()
+    Yref, _, _ = _solo(good, 50, 0.05)
+    _close(Y, Yref)
+
+
 def test_batch_pipelined_io_matches_waiting_calls():
     """emrkc_batch_set_stimulus_async / emrkc_batch_get_V_async (every
     instance's mask in, every instance's V out, two host buffers in rotation)
