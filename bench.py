@@ -1043,27 +1043,45 @@ def latency_result(args, local, dev):
                                   "stimulus 1 ms, dt 0.05 ms, T 20 ms, rho every step (timed), rho_S >= "
                                   f"{HH_RHO_S_MAX}", "nodes": w.n, "rho_S_min": HH_RHO_S_MAX}}
     finals = {}
+
+    def timed(prec):
+        res = []
+        for rep in range(args.warmup // 3 + 2):
+            sol = pkg.Solver(rp, col, K, M, chi=w.chi, Cm=w.Cm, model=w.model, mask=w.stim_mask,
+                             amplitude=w.stim_amp, t_on=w.t_on, t_off=w.t_off, precision=prec, rho_every=1,
+                             rho_S_min=HH_RHO_S_MAX, stream=stream.cuda_stream, device=local)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0 = sol.stats()["launches"]
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                for _ in range(H):
+                    sol.step(w.dt)
+                e1.record(stream)
+            sol.sync()
+            st = sol.stats()
+            res.append((e0.elapsed_time(e1) * 1e3 / H, st["total_pow_iters"] / H, st["s"], st["m"],
+                        (st["launches"] - l0) / H))
+            final = (sol.get_state(var=0), sol.activation_times())
+            sol.close()
+        return res[-1], final  # the first runs are warm-up
+
     with ClockSampler(local) as clk:
         for name, prec in (("fp64", pkg.PREC_FP64), ("mixed", pkg.PREC_MIXED)):
-            res = []
-            for rep in range(args.warmup // 3 + 2):
-                sol = pkg.Solver(rp, col, K, M, chi=w.chi, Cm=w.Cm, model=w.model, mask=w.stim_mask,
-                                 amplitude=w.stim_amp, t_on=w.t_on, t_off=w.t_off, precision=prec, rho_every=1,
-                                 rho_S_min=HH_RHO_S_MAX, stream=stream.cuda_stream, device=local)
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                with torch.cuda.stream(stream):
-                    e0.record(stream)
-                    for _ in range(H):
-                        sol.step(w.dt)
-                    e1.record(stream)
-                sol.sync()
-                st = sol.stats()
-                res.append((e0.elapsed_time(e1) * 1e3 / H, st["total_pow_iters"] / H, st["s"], st["m"]))
-                finals[name] = (sol.get_state(var=0), sol.activation_times())
-                sol.close()
-            us, its, s_, m_ = res[-1]  # the first runs are warm-up
+            (us, its, s_, m_, lps), finals[name] = timed(prec)
             out[name] = {"us_per_step": us, "power_iterations_per_step": its, "s": s_, "m": m_,
-                         "node_timesteps_per_s": w.n / (us * 1e-6)}
+                         "launches_per_step": lps, "node_timesteps_per_s": w.n / (us * 1e-6)}
+        # the other step form of each precision: mixed runs the
+        # device-resident step by default (one launch), FP64 the host-driven
+        # one (a launch per phase, the stage counts read back after each
+        # power iteration)
+        for name, prec, alt, val in (("fp64", pkg.PREC_FP64, "device_resident_step", "1"),
+                                     ("mixed", pkg.PREC_MIXED, "host_driven_step", "0")):
+            os.environ["EMRKC_FUSED_STEP"] = val
+            try:
+                (us, _, _, _, lps), _ = timed(prec)
+            finally:
+                os.environ.pop("EMRKC_FUSED_STEP", None)
+            out[name][alt] = {"us_per_step": us, "launches_per_step": lps}
     (Va, ta), (Vb, tb) = finals["fp64"], finals["mixed"]
     both = np.isfinite(ta) & np.isfinite(tb)
     out["accuracy"] = {"rel_l2_err_V_mixed_vs_fp64": float(np.sqrt(np.sum(M * (Va - Vb) ** 2) / np.sum(M * Va * Va))),

@@ -23,13 +23,17 @@ namespace emrkc {
 
 // Which loads may use the non-coherent (L1) path.  L1 holds no line of a
 // buffer from an earlier launch, so a load can go through L1 unless this
-// launch rewrites a buffer after reading it: the three state buffers rotate
-// with period 3 over the s outer stages and the three increment buffers over
-// the m inner stages, so with s <= 2 and m <= 3 every buffer is written at
-// most once and only read after its write (or only read) within a launch.
-// Otherwise data produced within the launch are loaded through L2 (ld.cg).
+// launch rewrites a buffer after reading it.  The three state buffers rotate
+// with period 3 over the s outer stages: with s <= 2 each is written at most
+// once.  The three increment buffers rotate over the m inner stages and are
+// written again by every outer stage: they are written at most once only
+// when m <= 3 and s = 1 (with m = 1 they are not used).  So L1 serves
+// instances with s <= 2 and m = 1, or s = 1 and m <= 3; the others load data
+// produced within the launch through L2 (ld.cg).
 // Light models (at most 3 z rows): V and z of the thread's next node are
 // loaded before the current node's work, one node ahead.
+__device__ __forceinline__ bool batch_loads_l2(int s, int m) { return s >= 3 || m >= 4 || (s >= 2 && m >= 2); }
+
 template <class Model, bool HAS_M2, bool CG>
 __device__ __forceinline__ void light_rows(const StageArgs& a, const Ell& A, int64_t r0, int64_t r1) {
   constexpr int NZ = Model::NE + Model::NS;
@@ -174,7 +178,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) batch_step_kernel(const B
       a.f_eta = I->f_eta;
       a.ell_wmax = I->wmax;
       const bool has_m2 = j >= 2;
-      const bool cg = (s >= 3 || m >= 4);
+      const bool cg = batch_loads_l2(s, m);
       switch (I->model) {
         case 0: batch_stage_rows<ModelNone<float>>(a, I->ell, r0, r1, has_m2, cg); break;
         case 1: batch_stage_rows<ModelPassive<float>>(a, I->ell, r0, r1, has_m2, cg); break;
@@ -211,7 +215,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) batch_step_kernel(const B
       b.f_inv_eta = I->f_inv_eta;
       b.f_okappa = I->o_kappa[j];
       b.f_omu_dt = I->o_mudt[j];
-      if (s >= 3 || m >= 4) {
+      if (batch_loads_l2(s, m)) {
         for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) inner_node_mixed<true>(b, I->ell, i);
       } else {
         for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) inner_node_mixed<false>(b, I->ell, i);

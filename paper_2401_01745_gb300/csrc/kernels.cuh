@@ -18,6 +18,7 @@
 
 #include "launch.h"
 #include "models.cuh"
+#include "rkc_coeffs.h"
 #include "dual.cuh"
 
 namespace emrkc {
@@ -25,23 +26,30 @@ namespace emrkc {
 // ---------------------------------------------------------------------------
 // Sparse rows.
 
+// Loads of data that may have been written earlier in the same launch by
+// another SM (the persistent batched and fused-step kernels) go through L2
+// only (ld.cg): L1 is not coherent across SMs.  Single-step kernels use
+// read-only loads (ldm) or plain loads (ldp).
+template <bool CG, typename T>
+__device__ __forceinline__ T ldm(const T* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return __ldg(p);
+}
+template <bool CG, typename T>
+__device__ __forceinline__ T ldp(const T* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
 // FP64: sum_k L_ik x_k over the stored row (diagonal included).
+template <bool CG = false>
 __device__ __forceinline__ double ell_dot64(const Ell& A, int64_t i, const double* __restrict__ x) {
   const int64_t b = i >> 5;
   const int w = __ldg(A.width + b);
   int64_t p = __ldg(A.slice_ptr + b) + (i & 31);
   double acc = 0.0;
-  for (int k = 0; k < w; ++k, p += 32) acc += __ldg(A.val + p) * __ldg(x + __ldg(A.col + p));
+  for (int k = 0; k < w; ++k, p += 32) acc += __ldg(A.val + p) * ldm<CG>(x + __ldg(A.col + p));
   return acc;
-}
-
-// Loads of data that may have been written earlier in the same launch by
-// another SM (the batched persistent kernel) go through L2 only (ld.cg): L1
-// is not coherent across SMs.  Single-step kernels use read-only loads.
-template <bool CG, typename T>
-__device__ __forceinline__ T ldm(const T* p) {
-  if constexpr (CG) return __ldcg(p);
-  else return __ldg(p);
 }
 
 // Mixed: sum_{k != i} L_ik (x_k - x_i) in FP32 (row sums of L vanish, so
@@ -162,21 +170,21 @@ __device__ __forceinline__ void ionic_mixed(float eta, float V, const float* z, 
 // Exponential_Euler), frozen forcing f_S(t_j, y_E), first inner RKC stage and
 // the z-part of g_j = nu g_{j-1} + kappa g_{j-2} + mu dt f_bar, where
 // f_bar = ((y_E - y)/eta on the gates, c_m g_S on z_S, (u_m - V)/eta on V).
-template <class Model, bool HAS_M2>
-__global__ void __launch_bounds__(128) stage_kernel_fp64(const StageArgs a, const Ell A) {
+// CG: loads through L2 only (the fused step kernel, which rewrites the
+// buffers within its launch).
+template <class Model, bool HAS_M2, bool CG>
+__device__ __forceinline__ void stage_node_fp64(const StageArgs& a, const Ell& A, const int64_t i) {
   constexpr int NE = Model::NE, NS = Model::NS, NZ = NE + NS;
   using M = Math<double>;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
   const int64_t ld = a.ld;
   const double* __restrict__ Zm1 = static_cast<const double*>(a.Zm1);
   const double* __restrict__ Zm2 = static_cast<const double*>(a.Zm2);
   double* __restrict__ Zout = static_cast<double*>(a.Zout);
 
-  const double V = a.Vm1[i];
+  const double V = ldp<CG>(a.Vm1 + i);
   double z[NZ > 0 ? NZ : 1];
 #pragma unroll
-  for (int k = 0; k < NZ; ++k) z[k] = Zm1[k * ld + i];
+  for (int k = 0; k < NZ; ++k) z[k] = ldp<CG>(Zm1 + k * ld + i);
 
   double zE1[NE > 0 ? NE : 1];
   if constexpr (NE > 0) {
@@ -196,24 +204,31 @@ __global__ void __launch_bounds__(128) stage_kernel_fp64(const StageArgs a, cons
     for (int k = 0; k < NZ; ++k) {
       const double fbar = (k < NE) ? (zE1[k < NE ? k : 0] - z[k]) * a.inv_eta : a.cm_inner * gS[k >= NE ? k - NE : 0];
       double out;
-      if constexpr (HAS_M2) out = a.nu * z[k] + a.kappa * Zm2[k * ld + i] + a.mu_dt * fbar;
+      if constexpr (HAS_M2) out = a.nu * z[k] + a.kappa * ldp<CG>(Zm2 + k * ld + i) + a.mu_dt * fbar;
       else out = z[k] + a.mu_dt * fbar;
       Zout[k * ld + i] = out;
     }
   }
-  const double LV = ell_dot64(A, i, a.Vm1);
+  const double LV = ell_dot64<CG>(A, i, a.Vm1);
   if (a.Vn_copy != nullptr) a.Vn_copy[i] = V;
   if (a.m == 1) {
     const double fbarV = a.mu1 * (LV + F);  // (u_1 - V)/eta with u_1 = V + mu'_1 eta (L V + F)
     double Vnew;
-    if constexpr (HAS_M2) Vnew = a.nu * V + a.kappa * a.Vm2[i] + a.mu_dt * fbarV;
+    if constexpr (HAS_M2) Vnew = a.nu * V + a.kappa * ldp<CG>(a.Vm2 + i) + a.mu_dt * fbarV;
     else Vnew = V + a.mu_dt * fbarV;
     a.Vout[i] = Vnew;
-    if (a.final_stage) step_epilogue(i, a.Vn[i], Vnew, a.act, a.t_n, a.dt, a.threshold, a.flags);
+    if (a.final_stage) step_epilogue(i, ldp<CG>(a.Vn + i), Vnew, a.act, a.t_n, a.dt, a.threshold, a.flags);
   } else {
     a.U1[i] = V + a.mu1_eta * (LV + F);
     static_cast<double*>(a.F)[i] = F;
   }
+}
+
+template <class Model, bool HAS_M2>
+__global__ void __launch_bounds__(128) stage_kernel_fp64(const StageArgs a, const Ell A) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  stage_node_fp64<Model, HAS_M2, false>(a, A, i);
 }
 
 // Outer stage j (mixed path): as above with z, the ionic model, the gating
@@ -223,10 +238,12 @@ __global__ void __launch_bounds__(128) stage_kernel_fp64(const StageArgs a, cons
 // The node's work after its V and z have been loaded (by the caller, possibly
 // one node ahead).
 // SPLIT: rows of at most 8 entries (checked at run time) have their
-// neighbour gathers issued before the ionic model.
-template <class Model, bool HAS_M2, bool CG, bool SPLIT = false>
+// neighbour gathers issued before the ionic model.  ROW: the caller holds
+// the row (rc, rv: rw <= 8 entries, as ell_row returns them).
+template <class Model, bool HAS_M2, bool CG, bool SPLIT = false, bool ROW = false>
 __device__ __forceinline__ void stage_node_mixed_with(const StageArgs& a, const Ell& A, const int64_t i, const float V,
-                                                      const float* z) {
+                                                      const float* z, const int32_t* rc = nullptr,
+                                                      const float* rv = nullptr, const int rw = 0) {
   constexpr int NE = Model::NE, NS = Model::NS, NZ = NE + NS;
   const int64_t ld = a.ld;
   const float* __restrict__ Zm2 = static_cast<const float*>(a.Zm2);
@@ -237,7 +254,12 @@ __device__ __forceinline__ void stage_node_mixed_with(const StageArgs& a, const 
   float xv[8];
   int w = 0;
   int64_t p = 0;
-  if (split) {
+  if constexpr (ROW) {
+    w = rw;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (k < w) xv[k] = ldm<CG>(a.V32m1 + rc[k]);
+  } else if (split) {
     const int64_t b = i >> 5;
     w = __ldg(A.width + b);
     p = __ldg(A.slice_ptr + b) + (i & 31);
@@ -265,7 +287,11 @@ __device__ __forceinline__ void stage_node_mixed_with(const StageArgs& a, const 
     }
   }
   float LV = 0.0f;
-  if (split) {
+  if constexpr (ROW) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (k < w) LV += rv[k] * (xv[k] - V);
+  } else if (split) {
 #pragma unroll
     for (int k = 0; k < 8; ++k)
       if (k < w) LV += __ldg(A.val32 + p + 32 * k) * (xv[k] - V);
@@ -725,23 +751,28 @@ __global__ void __launch_bounds__(kTmaTile) stage_kernel_mixed_tma_pf(const Stag
 }
 
 // Inner RKC stage k >= 2 (FP64 path), Algorithm 1 applied to f_u = f_F + frozen f_S.
-static __global__ void __launch_bounds__(256) inner_kernel_fp64(const InnerArgs a, const Ell A) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
-  const double Lu = ell_dot64(A, i, a.u1);
-  const double F = static_cast<const double*>(a.F)[i];
-  const double uk = a.nu * a.u1[i] + a.kappa * a.u2[i] + a.mu_eta * (Lu + F);
+template <bool CG>
+__device__ __forceinline__ void inner_node_fp64(const InnerArgs& a, const Ell& A, const int64_t i) {
+  const double Lu = ell_dot64<CG>(A, i, a.u1);
+  const double F = ldp<CG>(static_cast<const double*>(a.F) + i);
+  const double uk = a.nu * ldp<CG>(a.u1 + i) + a.kappa * ldp<CG>(a.u2 + i) + a.mu_eta * (Lu + F);
   if (!a.last) {
     a.uk[i] = uk;
     return;
   }
-  const double V1 = a.Vm1[i];
+  const double V1 = ldp<CG>(a.Vm1 + i);
   const double fbar = (uk - V1) * a.inv_eta;
   double Vnew;
-  if (a.Vm2 != nullptr) Vnew = a.onu * V1 + a.okappa * a.Vm2[i] + a.omu_dt * fbar;
+  if (a.Vm2 != nullptr) Vnew = a.onu * V1 + a.okappa * ldp<CG>(a.Vm2 + i) + a.omu_dt * fbar;
   else Vnew = V1 + a.omu_dt * fbar;
   a.Vout[i] = Vnew;
-  if (a.final_stage) step_epilogue(i, a.Vn[i], Vnew, a.act, a.t_n, a.dt, a.threshold, a.flags);
+  if (a.final_stage) step_epilogue(i, ldp<CG>(a.Vn + i), Vnew, a.act, a.t_n, a.dt, a.threshold, a.flags);
+}
+
+static __global__ void __launch_bounds__(256) inner_kernel_fp64(const InnerArgs a, const Ell A) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  inner_node_fp64<false>(a, A, i);
 }
 
 // Inner RKC stage k >= 2 (mixed path) on the FP32 increments:
@@ -1131,9 +1162,37 @@ __device__ __forceinline__ bool power_barrier(const PowerFusedArgs& a) {
 // 5; mixed path: q J v (q L v for f_F, dual numbers for f_S).  Iterates
 // ping-pong between two buffers per estimate; out[4], out[5] say which holds
 // the last one.
-template <class MD, class MDu, typename Z, bool MIXED, bool CLUSTER = false>
-__global__ void __launch_bounds__(kReduceBlock) power_fused_kernel(const PowerFusedArgs a, const Ell A) {
+struct PowerResult {
+  double rhoF = 0, rhoS = 0;
+  int itF = 0, itS = 0;
+  int lastF = 0, lastS = 0;  // iterate buffer (0 or 1) holding the last iterate
+  bool ok = false;           // false: a grid barrier gave up (flags bit 1 set)
+};
+
+// Hardware barrier of the whole cluster (release / acquire at cluster scope).
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// A double in the shared memory of CTA `rank` of this cluster, at the
+// address of `local` in this CTA (distributed shared memory).
+__device__ __forceinline__ double ld_cluster_f64(const double* local, unsigned rank) {
+  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(local));
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(r) : "memory");
+  return v;
+}
+
+// The body of the launch: every thread of every CTA returns the same result.
+// CLUSTER: the per-CTA partial sums stay in each CTA's shared memory and are
+// read across the cluster after the barrier; otherwise they go through
+// global memory.  Same values, same order of addition.
+template <class MD, class MDu, typename Z, bool MIXED, bool CLUSTER>
+__device__ __forceinline__ PowerResult power_fused_body(const PowerFusedArgs& a, const Ell& A) {
   constexpr int NE = MD::NE, NS = MD::NS, N = 1 + NE + NS;
+  PowerResult res;
   // Mixed path: iterates, per-thread and per-CTA sums in FP32 (GB300's FP64
   // pipe is a small fraction of its FP32 rate); the grid sums and the
   // scalars of Algorithm 5 in FP64.  FP64 path: everything in FP64.
@@ -1148,6 +1207,26 @@ __global__ void __launch_bounds__(kReduceBlock) power_fused_kernel(const PowerFu
   VT* const vS[2] = {reinterpret_cast<VT*>(a.vS[0]), reinterpret_cast<VT*>(a.vS[1])};
   int par = 0;
   auto part = [&](int p) { return a.part + (size_t)p * 4 * G; };
+  __shared__ double s_cpart[2][4];  // CLUSTER: this CTA's partials (two parities)
+  __shared__ double s_csum[4];
+  // grid sums of the first cnt columns of the partials of parity par, the
+  // same in every CTA (lane k adds CTA k's partial; G <= 32 here)
+  auto gather = [&](int cnt, double* out) {
+    if constexpr (CLUSTER) {
+      if (threadIdx.x < 32) {
+        for (int c = 0; c < cnt; ++c) {
+          double v = (threadIdx.x < (unsigned)G) ? ld_cluster_f64(&s_cpart[par][c], threadIdx.x) : 0.0;
+          v = warp_sum(v);
+          if (threadIdx.x == 0) s_csum[c] = v;
+        }
+      }
+      __syncthreads();
+      for (int c = 0; c < cnt; ++c) out[c] = s_csum[c];
+      __syncthreads();
+    } else {
+      for (int c = 0; c < cnt; ++c) out[c] = sum_partials(part(par), G, c, sh);
+    }
+  };
   // block sums of the first cnt values into this CTA's partials (FP32 sums
   // of FP32 per-thread sums on the mixed path)
   auto bsum = [&](VT v) -> double {
@@ -1160,11 +1239,18 @@ __global__ void __launch_bounds__(kReduceBlock) power_fused_kernel(const PowerFu
     const double t2 = cnt > 2 ? bsum(v2) : 0.0;
     const double t3 = cnt > 3 ? bsum(v3) : 0.0;
     if (threadIdx.x == 0) {
-      double* p = part(par) + 4 * blockIdx.x;
-      p[0] = t0;
-      p[1] = t1;
-      p[2] = t2;
-      p[3] = t3;
+      if constexpr (CLUSTER) {
+        s_cpart[par][0] = t0;
+        s_cpart[par][1] = t1;
+        s_cpart[par][2] = t2;
+        s_cpart[par][3] = t3;
+      } else {
+        double* p = part(par) + 4 * blockIdx.x;
+        p[0] = t0;
+        p[1] = t1;
+        p[2] = t2;
+        p[3] = t3;
+      }
     }
   };
   // norms of y and of the start iterates; f_S(y) for the FP64 differences
@@ -1194,15 +1280,15 @@ __global__ void __launch_bounds__(kReduceBlock) power_fused_kernel(const PowerFu
     }
     publish(4, s0, s1, s2, s3);
   }
-  if (!power_barrier<CLUSTER>(a)) return;
+  if (!power_barrier<CLUSTER>(a)) return res;
   // The scalars of Algorithm 5 (norms, q, rho, the stopping test) are
   // computed by thread 0 and shared: they are FP64, and GB300's FP64 pipe is
   // narrow, so the other threads must not repeat them.
   __shared__ double s_q, s_rho, s_delta, s_tol;
   __shared__ int s_go, s_it, s_maxit;
   // squared norms of y_F, v_F, y_S, v_S (the same value in every thread)
-  const double nsum[4] = {sum_partials(part(par), G, 0, sh), sum_partials(part(par), G, 1, sh),
-                          sum_partials(part(par), G, 2, sh), sum_partials(part(par), G, 3, sh)};
+  double nsum[4];
+  gather(4, nsum);
   par ^= 1;
 
   // one power iteration per loop trip: v_new = f(y + q v) - f(y) (FP64 path)
@@ -1277,8 +1363,9 @@ __global__ void __launch_bounds__(kReduceBlock) power_fused_kernel(const PowerFu
       acc += wv * wv;
     }
     publish(1, acc, 0, 0, 0);
-    if (!power_barrier<CLUSTER>(a)) return;
-    const double nv2 = sum_partials(part(par), G, 0, sh);
+    if (!power_barrier<CLUSTER>(a)) return res;
+    double nv2;
+    gather(1, &nv2);
     par ^= 1;
     curF ^= 1;
     advance(nv2);
@@ -1296,7 +1383,7 @@ __global__ void __launch_bounds__(kReduceBlock) power_fused_kernel(const PowerFu
     VT* vn = vS[curS ^ 1];
     VT acc = 0;
     const float qf = (float)q;
-    const float inv_Cm = (float)(1.0 / a.Cm);
+    const float inv_Cm = a.f_inv_Cm;
     for (int64_t i = i0; i < a.n; i += stride) {
       if constexpr (MIXED) {
         // q J v by forward-mode dual numbers in FP32
@@ -1336,21 +1423,385 @@ __global__ void __launch_bounds__(kReduceBlock) power_fused_kernel(const PowerFu
       }
     }
     publish(1, acc, 0, 0, 0);
-    if (!power_barrier<CLUSTER>(a)) return;
-    const double nv2 = sum_partials(part(par), G, 0, sh);
+    if (!power_barrier<CLUSTER>(a)) return res;
+    double nv2;
+    gather(1, &nv2);
     par ^= 1;
     curS ^= 1;
     advance(nv2);
   }
-  const double rhoS = s_rho;
-  const int itS = s_it;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    a.out[0] = rhoF;
-    a.out[1] = rhoS;
-    a.out[2] = (double)itF;
-    a.out[3] = (double)itS;
-    a.out[4] = (double)curF;
-    a.out[5] = (double)curS;
+  res.rhoF = rhoF;
+  res.rhoS = s_rho;
+  res.itF = itF;
+  res.itS = s_it;
+  res.lastF = curF;
+  res.lastS = curS;
+  res.ok = true;
+  return res;
+}
+
+template <class MD, class MDu, typename Z, bool MIXED, bool CLUSTER = false>
+__global__ void __launch_bounds__(kReduceBlock) power_fused_kernel(const PowerFusedArgs a, const Ell A) {
+  const PowerResult r = power_fused_body<MD, MDu, Z, MIXED, CLUSTER>(a, A);
+  // no CTA leaves while another may still read its shared memory
+  if constexpr (CLUSTER) cluster_sync_all();
+  if (r.ok && blockIdx.x == 0 && threadIdx.x == 0) {
+    a.out[0] = r.rhoF;
+    a.out[1] = r.rhoS;
+    a.out[2] = (double)r.itF;
+    a.out[3] = (double)r.itS;
+    a.out[4] = (double)r.lastF;
+    a.out[5] = (double)r.lastS;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Device-resident emRKC step for problems that one thread-block cluster
+// holds: Algorithm 5 when due (the body above), Algorithm 1 (rkc_stages,
+// rkc_coeffs) from the resulting radii, then the s outer stages and the
+// m - 1 inner stages of each (Algorithm 3) with the per-node functions of
+// the single-step kernels, phases separated by the hardware cluster
+// barrier (release / acquire at cluster scope).  Buffers rewritten within
+// the launch after being read are loaded through L2, the others may come
+// through L1 (the rule of the batched kernel).  g_j goes to buffer
+// (b0 + r j) mod 3 with r = 2 when s = 2 (mod 3), else r = 1, so that
+// g_s = y_{n+1} lands in buffer (b0 + 1) mod 3 as the host expects; when
+// s = 0 (mod 3) it lands in b0 and is copied over after the last stage.  The
+// host never reads s, m or rho during a step: they are kept in
+// FusedStepState.
+
+// Largest CTA of the fused step: 512 threads for the light models, 256 for
+// TTP06 (its registers); the launch uses the smallest multiple of 32 that
+// gives every node its own thread, up to this bound.
+template <class MR>
+struct FusedBlock {
+  static constexpr int value = (MR::NE + MR::NS > 3) ? 256 : 512;
+};
+
+template <class MD, class MR, class MDu, typename Z, bool MIXED>
+__global__ void __launch_bounds__(FusedBlock<MR>::value, 1) step_fused_kernel(const FusedStepArgs a, const Ell A) {
+  constexpr int NZ = MR::NE + MR::NS;
+  __shared__ double s_co[4][kFusedMaxStages + 1];  // outer mu, nu, kappa, c
+  __shared__ double s_ci[4][kFusedMaxStages + 1];  // inner mu', nu', kappa', c'
+  __shared__ double s_eta;
+  __shared__ int s_S, s_M;
+  // the scalars of the current phase, computed by thread 0 (GB300's FP64
+  // pipe is narrow: the divisions and conversions are done once per CTA,
+  // not once per thread)
+  __shared__ double s_pd[13];
+  __shared__ float s_pf[15];
+  // launched with programmatic dependent launch: the next step's cluster
+  // may be made resident now, and this one waits for the previous step
+  pdl_trigger();
+  pdl_wait();
+  FusedStepState* const st = a.state;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+
+  // ---- spectral radii: given, estimated now (Algorithm 5), or the last
+  // estimates; the safety factor and the rho_S floor as on the host path
+  double rF = 0.0, rS = 0.0;
+  if (!a.fixed) {
+    rF = st->rhoF_raw;
+    rS = st->rhoS_raw;
+    if (a.due) {
+      PowerFusedArgs pa = a.pw;
+      const int cF = st->curF, cS = st->curS;
+      if (cF) {
+        double* t = pa.vF[0];
+        pa.vF[0] = pa.vF[1];
+        pa.vF[1] = t;
+      }
+      if (cS) {
+        double* t = pa.vS[0];
+        pa.vS[0] = pa.vS[1];
+        pa.vS[1] = t;
+      }
+      pa.rhoF_warm = rF;
+      pa.rhoS_warm = rS;
+      pa.stim = (a.mask != nullptr && a.t_on <= a.t_n && a.t_n <= a.t_off) ? a.amp : 0.0;
+      // every CTA has read the state before the body's first barrier, so
+      // the lead thread may rewrite it afterwards
+      const PowerResult r = power_fused_body<MD, MDu, Z, MIXED, true>(pa, A);
+      rF = r.rhoF;
+      rS = r.rhoS;
+      if (lead) {
+        st->rhoF_raw = rF;
+        st->rhoS_raw = rS;
+        st->curF = cF ^ r.lastF;
+        st->curS = cS ^ r.lastS;
+        st->itF = r.itF;
+        st->itS = r.itS;
+        st->total_it += r.itF + r.itS;
+      }
+    } else if (lead) {
+      st->itF = st->itS = 0;
+    }
+  } else if (lead) {
+    st->itF = st->itS = 0;
+  }
+
+  // ---- Algorithm 1: stage counts and coefficients (the same in every CTA)
+  if (threadIdx.x == 0) {
+    const double rhoF = a.fixed ? a.rho_F_fixed : a.safety * rF;
+    const double rhoS = a.fixed ? a.rho_S_fixed : fmax(a.safety * rS, a.rho_S_min);
+    double l_s = 0.0;
+    const int S = rkc_stages(a.dt, rhoS, a.eps, &l_s);
+    const double eta = 2.0 * a.dt / l_s;
+    const int M = rkc_stages(eta, rhoF, a.eps, nullptr);
+    s_S = S;
+    s_M = M;
+    s_eta = eta;
+    if (S <= kFusedMaxStages && M <= kFusedMaxStages) {
+      rkc_coeffs(S, a.eps, s_co[0], s_co[1], s_co[2], s_co[3]);
+      rkc_coeffs(M, a.eps, s_ci[0], s_ci[1], s_ci[2], s_ci[3]);
+    }
+    if (lead) {
+      st->rhoF = rhoF;
+      st->rhoS = rhoS;
+      st->s = S;
+      st->m = M;
+      st->eta = eta;
+    }
+  }
+  __syncthreads();
+  const int S = s_S, M = s_M;
+  if (S > kFusedMaxStages || M > kFusedMaxStages) {
+    if (lead) atomicOr(a.flags, 16);
+    cluster_sync_all();  // the power iteration's shared-memory reads are done
+    return;
+  }
+
+  // ---- the s outer stages, each followed by its m - 1 inner stages
+  // Mixed path with one node per thread and rows of at most 8 entries: the
+  // thread's row of L is loaded once and kept in registers for every stage.
+  const bool row_pre = MIXED && a.n <= stride && a.ell_wmax <= 8;
+  int32_t rc[8];
+  float rv[8];
+  int rw = 0;
+  if (row_pre && i0 < a.n) rw = ell_row<8>(A, i0, rc, rv);
+  const int b0 = a.b0;
+  const int rot = (S % 3 == 2) ? 2 : 1;
+  // L1 may serve the stage loads when no buffer is rewritten after being
+  // read in this launch: with s <= 2 each state buffer is written once, the
+  // increment buffers once only when m <= 3 and s = 1 (the power iteration's
+  // own buffers are always loaded through L2)
+  const bool l2 = S >= 3 || M >= 4 || (S >= 2 && M >= 2);
+  for (int j = 1; j <= S; ++j) {
+    const int bm1 = (b0 + rot * (j - 1)) % 3, bm2 = (b0 + rot * (j + 1)) % 3, bo = (b0 + rot * j) % 3;
+    // the phase's scalars (FP64 arithmetic, divisions, conversions) once
+    // per CTA; every thread then fills its arguments from them
+    if (threadIdx.x == 0) {
+      const double eta = s_eta, mu1 = s_ci[0][1];
+      const double nu = j >= 2 ? s_co[1][j] : 1.0, kappa = j >= 2 ? s_co[2][j] : 0.0, mu_dt = s_co[0][j] * a.dt;
+      const double ts = __dadd_rn(a.t_n, __dmul_rn(s_co[3][j - 1], a.dt));
+      const double stim = (a.mask != nullptr && a.t_on <= ts && ts <= a.t_off) ? a.amp : 0.0;
+      s_pd[0] = nu;
+      s_pd[1] = kappa;
+      s_pd[2] = mu_dt;
+      s_pd[3] = eta;
+      s_pd[4] = s_ci[3][M];
+      s_pd[5] = mu1 * eta;
+      s_pd[6] = stim;
+      s_pd[7] = 1.0 / a.Cm;
+      s_pd[8] = 1.0 / eta;
+      s_pd[9] = mu1;
+      s_pf[0] = (float)nu;
+      s_pf[1] = (float)kappa;
+      s_pf[2] = (float)mu_dt;
+      s_pf[3] = (float)s_pd[8];
+      s_pf[4] = (float)s_pd[4];
+      s_pf[5] = (float)mu1;
+      s_pf[6] = (float)s_pd[5];
+      s_pf[7] = (float)eta;
+      s_pf[8] = (float)stim;
+      s_pf[9] = (float)s_pd[7];
+      s_pf[10] = (float)a.threshold;
+      s_pf[11] = (float)(1.0 / s_pd[5]);
+    }
+    __syncthreads();
+    StageArgs sa;
+    sa.n = a.n;
+    sa.ld = a.ld;
+    sa.Zm1 = a.Z[bm1];
+    sa.Zm2 = j >= 2 ? a.Z[bm2] : nullptr;
+    sa.Zout = a.Z[bo];
+    sa.nu = s_pd[0];
+    sa.kappa = s_pd[1];
+    sa.mu_dt = s_pd[2];
+    sa.eta = s_pd[3];
+    sa.cm_inner = s_pd[4];
+    sa.mu1_eta = s_pd[5];
+    sa.m = M;
+    sa.F = a.F;
+    sa.mask = a.mask;
+    sa.stim = s_pd[6];
+    sa.Cm = a.Cm;
+    sa.inv_Cm = s_pd[7];
+    sa.final_stage = (j == S && M == 1) ? 1 : 0;
+    sa.act = a.act;
+    sa.t_n = a.t_n;
+    sa.dt = a.dt;
+    sa.threshold = a.threshold;
+    sa.flags = a.flags;
+    sa.inv_eta = s_pd[8];
+    sa.mu1 = s_pd[9];
+    if constexpr (MIXED) {
+      sa.V32m1 = a.Vhi[bm1];
+      sa.V32out = a.Vhi[bo];
+      sa.Vlo_m1 = a.Vlo[bm1];
+      sa.Vhi_m2 = j >= 2 ? a.Vhi[bm2] : nullptr;
+      sa.Vlo_m2 = j >= 2 ? a.Vlo[bm2] : nullptr;
+      sa.Vlo_out = a.Vlo[bo];
+      sa.Vn32 = (S <= 2) ? a.Vhi[b0] : a.Vn32;
+      sa.Vn32_copy = (j == 1 && S >= 3) ? a.Vn32 : nullptr;
+      sa.f_th = s_pf[10];
+      sa.D1 = a.D[0];
+      sa.LV = (M >= 4) ? a.LV : nullptr;
+      sa.f_nu = s_pf[0];
+      sa.f_kappa = s_pf[1];
+      sa.f_mudt = s_pf[2];
+      sa.f_inv_eta = s_pf[3];
+      sa.f_cm = s_pf[4];
+      sa.f_mu1 = s_pf[5];
+      sa.f_mu1eta = s_pf[6];
+      sa.f_eta = s_pf[7];
+      sa.f_stim = s_pf[8];
+      sa.f_inv_Cm = s_pf[9];
+      sa.ell_wmax = a.ell_wmax;
+      auto nodes = [&](auto cg_tag) {
+        constexpr bool CG = decltype(cg_tag)::value;
+        if (row_pre) {
+          if (i0 < a.n) {
+            const float* __restrict__ Zm1 = static_cast<const float*>(sa.Zm1);
+            const float V = ldm<CG>(sa.V32m1 + i0);
+            float z[NZ > 0 ? NZ : 1];
+#pragma unroll
+            for (int k = 0; k < NZ; ++k) z[k] = ldm<CG>(Zm1 + k * a.ld + i0);
+            if (j >= 2) stage_node_mixed_with<MR, true, CG, false, true>(sa, A, i0, V, z, rc, rv, rw);
+            else stage_node_mixed_with<MR, false, CG, false, true>(sa, A, i0, V, z, rc, rv, rw);
+          }
+        } else {
+          for (int64_t i = i0; i < a.n; i += stride) {
+            if (j >= 2) stage_node_mixed<MR, true, CG>(sa, A, i);
+            else stage_node_mixed<MR, false, CG>(sa, A, i);
+          }
+        }
+      };
+      if (l2) nodes(std::true_type{});
+      else nodes(std::false_type{});
+    } else {
+      sa.Vm1 = a.V[bm1];
+      sa.Vm2 = j >= 2 ? a.V[bm2] : nullptr;
+      sa.Vout = a.V[bo];
+      sa.U1 = a.U[0];
+      sa.Vn = (S <= 2) ? a.V[b0] : a.Vn;
+      sa.Vn_copy = (j == 1 && S >= 3) ? a.Vn : nullptr;
+      auto nodes = [&](auto cg_tag) {
+        constexpr bool CG = decltype(cg_tag)::value;
+        for (int64_t i = i0; i < a.n; i += stride) {
+          if (j >= 2) stage_node_fp64<MR, true, CG>(sa, A, i);
+          else stage_node_fp64<MR, false, CG>(sa, A, i);
+        }
+      };
+      if (l2) nodes(std::true_type{});
+      else nodes(std::false_type{});
+    }
+    // also the last read of this phase's scalars before thread 0 rewrites them
+    cluster_sync_all();
+    for (int k = 2; k <= M; ++k) {
+      if (threadIdx.x == 0) {
+        const double mu_eta = s_ci[0][k] * s_pd[3];
+        s_pd[10] = s_ci[1][k];
+        s_pd[11] = s_ci[2][k];
+        s_pd[12] = mu_eta;
+        s_pf[12] = (float)s_ci[1][k];
+        s_pf[13] = (float)s_ci[2][k];
+        s_pf[14] = (float)mu_eta;
+      }
+      __syncthreads();
+      InnerArgs ib;
+      ib.n = a.n;
+      ib.F = a.F;
+      ib.nu = s_pd[10];
+      ib.kappa = s_pd[11];
+      ib.mu_eta = s_pd[12];
+      ib.last = (k == M) ? 1 : 0;
+      ib.onu = sa.nu;
+      ib.okappa = sa.kappa;
+      ib.omu_dt = sa.mu_dt;
+      ib.eta = sa.eta;
+      ib.final_stage = (j == S && k == M) ? 1 : 0;
+      ib.act = a.act;
+      ib.t_n = a.t_n;
+      ib.dt = a.dt;
+      ib.threshold = a.threshold;
+      ib.flags = a.flags;
+      ib.inv_eta = sa.inv_eta;
+      if constexpr (MIXED) {
+        ib.d1 = a.D[(k - 2) % 3];
+        ib.d2 = (k == 2) ? nullptr : a.D[(k - 3) % 3];
+        ib.dk = a.D[(k - 1) % 3];
+        ib.LV = a.LV;
+        ib.lf_src = (M >= 4) ? 0 : (k == 2 ? 1 : 2);
+        ib.f_inv_mu1eta = s_pf[11];
+        ib.V32out = a.Vhi[bo];
+        ib.Vhi1 = a.Vhi[bm1];
+        ib.Vlo1 = a.Vlo[bm1];
+        ib.Vhi2 = j >= 2 ? a.Vhi[bm2] : nullptr;
+        ib.Vlo2 = j >= 2 ? a.Vlo[bm2] : nullptr;
+        ib.Vlo_out = a.Vlo[bo];
+        ib.Vn32 = sa.Vn32;
+        ib.f_okappa = sa.f_kappa;
+        ib.f_omu_dt = sa.f_mudt;
+        ib.f_th = sa.f_th;
+        ib.f_nu = s_pf[12];
+        ib.f_kappa = s_pf[13];
+        ib.f_mueta = s_pf[14];
+        ib.f_inv_eta = sa.f_inv_eta;
+        auto nodes = [&](auto cg_tag) {
+          constexpr bool CG = decltype(cg_tag)::value;
+          if (row_pre) {
+            if (i0 < a.n) inner_node_mixed_row<8, CG>(ib, i0, rc, rv, rw);
+          } else {
+            for (int64_t i = i0; i < a.n; i += stride) inner_node_mixed<CG>(ib, A, i);
+          }
+        };
+        if (l2) nodes(std::true_type{});
+        else nodes(std::false_type{});
+      } else {
+        ib.u1 = a.U[(k - 2) % 3];
+        ib.u2 = (k == 2) ? a.V[bm1] : a.U[(k - 3) % 3];
+        ib.uk = a.U[(k - 1) % 3];
+        ib.Vm1 = a.V[bm1];
+        ib.Vm2 = j >= 2 ? a.V[bm2] : nullptr;
+        ib.Vout = a.V[bo];
+        ib.Vn = sa.Vn;
+        if (l2) {
+          for (int64_t i = i0; i < a.n; i += stride) inner_node_fp64<true>(ib, A, i);
+        } else {
+          for (int64_t i = i0; i < a.n; i += stride) inner_node_fp64<false>(ib, A, i);
+        }
+      }
+      cluster_sync_all();
+    }
+  }
+  // s = 0 (mod 3): y_{n+1} is in b0; move it to (b0 + 1) mod 3
+  if (S % 3 == 0) {
+    const int bd = (b0 + 1) % 3;
+    const Z* __restrict__ zs = static_cast<const Z*>(a.Z[b0]);
+    Z* __restrict__ zd = static_cast<Z*>(a.Z[bd]);
+    for (int64_t i = i0; i < a.n; i += stride) {
+      if constexpr (MIXED) {
+        a.Vhi[bd][i] = __ldcg(a.Vhi[b0] + i);
+        a.Vlo[bd][i] = __ldcg(a.Vlo[b0] + i);
+      } else {
+        a.V[bd][i] = __ldcg(a.V[b0] + i);
+      }
+#pragma unroll
+      for (int k = 0; k < NZ; ++k) zd[k * a.ld + i] = __ldcg(zs + k * a.ld + i);
+    }
   }
 }
 
@@ -1475,6 +1926,53 @@ struct Kernels {
     }
     return 0;
   }
+  static cudaError_t step_fused(const FusedStepArgs& a, const Ell& A, int cluster, cudaStream_t st) {
+    FusedStepArgs ac = a;
+    Ell Ac = A;
+    const int64_t per = (a.n + cluster - 1) / cluster;
+    const int block = (int)std::min<int64_t>(FusedBlock<MR>::value, std::max<int64_t>(32, (per + 31) / 32 * 32));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cluster);
+    cfg.blockDim = dim3(block);
+    cfg.stream = st;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelEx(&cfg, step_fused_kernel<MD, MR, MDu, Z, MIXED>, ac, Ac);
+  }
+  // CTAs of the fused step's cluster: 16 where the device allows a
+  // non-portable cluster of that size, else 8, else 0 (no fused step)
+  static int step_fused_cluster_size(int device) {
+    (void)device;
+    auto k = step_fused_kernel<MD, MR, MDu, Z, MIXED>;
+    for (int cl : {16, 8}) {
+      if (cl > 8 && cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(cl);
+      cfg.blockDim = dim3(FusedBlock<MR>::value);
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = cl;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, k, &cfg) == cudaSuccess && nclusters > 0) return cl;
+      cudaGetLastError();
+    }
+    return 0;
+  }
+  static int step_fused_block(void) { return FusedBlock<MR>::value; }
   static int power_fused_grid(int device) {
     int per_sm = 0, sms = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, power_fused_kernel<MD, MDu, Z, MIXED>, kReduceBlock, 0);
@@ -1534,6 +2032,9 @@ struct Kernels {
     ks->power_fused = &power_fused;
     ks->power_fused_grid = &power_fused_grid;
     ks->power_cluster_size = &power_cluster_size;
+    ks->step_fused = &step_fused;
+    ks->step_fused_cluster_size = &step_fused_cluster_size;
+    ks->step_fused_block = &step_fused_block;
   }
 };
 

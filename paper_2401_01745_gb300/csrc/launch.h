@@ -164,6 +164,7 @@ struct PowerFusedArgs {
   double* fy = nullptr;                // FP64 path: f_S(y), N x ld
   const uint8_t* mask = nullptr;
   double stim = 0, Cm = 1;
+  float f_inv_Cm = 1;                  // (float)(1 / Cm)
   double eps = 1e-8, tol = 1e-2;
   int max_iter = 50;
   double tol_cold = 1e-4;        // a start with warm value 0 (no initial guess)
@@ -174,6 +175,48 @@ struct PowerFusedArgs {
   int* flags = nullptr;
   long long spin_limit = 0;
   double* out = nullptr;               // rho_F, rho_S, it_F, it_S, last buffer of v_F, of v_S
+};
+
+// Device-resident emRKC step for problems one thread-block cluster holds:
+// Algorithm 5 (when due), Algorithm 1 and every outer and inner stage of
+// Algorithm 3 in one launch, with no host round trip.  The state below
+// lives in device memory and carries the power iteration from step to step.
+struct FusedStepState {
+  double rhoF_raw = 0, rhoS_raw = 0;  // last estimates (warm start of Algorithm 5)
+  double rhoF = 0, rhoS = 0, eta = 0; // values the last step used (safety factor, floor)
+  int curF = 0, curS = 0;             // iterate buffer holding the last iterate (1: the second)
+  int s = 0, m = 0, itF = 0, itS = 0; // last step's stage counts and power iterations
+  long long total_it = 0;
+};
+constexpr int kFusedMaxStages = 128;  // s and m of one fused step (flags bit 4 beyond)
+
+struct FusedStepArgs {
+  int64_t n = 0, ld = 0;
+  int b0 = 0;                          // state buffer of y_n; y_{n+1} goes to (b0 + 1) mod 3
+  double* V[3] = {nullptr, nullptr, nullptr};  // FP64 path
+  void* Z[3] = {nullptr, nullptr, nullptr};    // z blocks ((N-1) x ld, Z type)
+  float* Vhi[3] = {nullptr, nullptr, nullptr}; // mixed path: V = hi + lo
+  float* Vlo[3] = {nullptr, nullptr, nullptr};
+  double* U[3] = {nullptr, nullptr, nullptr};  // FP64 inner iterates
+  float* D[3] = {nullptr, nullptr, nullptr};   // mixed inner increments
+  void* F = nullptr;                   // frozen forcing (R type)
+  float* LV = nullptr;                 // mixed: L V + F for inner stages k >= 4
+  double* Vn = nullptr;                // FP64: copy of V_n when s >= 3
+  float* Vn32 = nullptr;               // mixed: copy of V_n hi when s >= 3
+  const uint8_t* mask = nullptr;
+  double amp = 0, t_on = 0, t_off = -1;
+  double Cm = 1;
+  double t_n = 0, dt = 0, threshold = -20;
+  double* act = nullptr;
+  int* flags = nullptr;                // bit 0: non-finite V; bit 4: s or m above kFusedMaxStages
+  double eps = 0.05;                   // RKC damping
+  int ell_wmax = 1 << 30;              // widest sliced-ELL slice (rows kept in registers when <= 8)
+  int due = 0;                         // 1: Algorithm 5 before the step
+  int fixed = 0;                       // 1: rho_F_fixed, rho_S_fixed as given (no estimate)
+  double rho_F_fixed = 0, rho_S_fixed = 0;
+  double safety = 1.05, rho_S_min = 0;
+  PowerFusedArgs pw;                   // Algorithm 5: vF, vS in buffer order, scratch, tolerances
+  FusedStepState* state = nullptr;
 };
 
 struct Launchers;  // per precision mode
@@ -194,6 +237,9 @@ struct KernelSet {
   cudaError_t (*power_fused)(const PowerFusedArgs&, const Ell&, int grid, cudaStream_t) = nullptr;
   int (*power_fused_grid)(int device) = nullptr;
   int (*power_cluster_size)(int device) = nullptr;  // CTAs of the single-cluster variant (0: unavailable)
+  cudaError_t (*step_fused)(const FusedStepArgs&, const Ell&, int cluster, cudaStream_t) = nullptr;
+  int (*step_fused_cluster_size)(int device) = nullptr;  // CTAs of the fused step's cluster (0: unavailable)
+  int (*step_fused_block)(void) = nullptr;                // largest CTA of the fused step
 };
 
 // mRKC (mrkc.cu, FP64): one outer stage (stage kernel, inner stage 1) or

@@ -52,7 +52,7 @@ void free_all(emrkc_solver* s) {
                   s->d_D[0], s->d_D[1], s->d_D[2], s->d_LV, s->d_Vlo[0], s->d_Vlo[1], s->d_Vlo[2],
                   s->d_Vn32, s->d_mass, s->d_cg[0], s->d_cg[1], s->d_cg[2], s->d_cg[3], s->d_cg[4],
                   s->d_cg[5], s->d_part, s->d_bar, s->d_iters, s->d_res, s->d_Um[0], s->d_Um[1], s->d_Um[2],
-                  s->d_ppart, s->d_pbar, s->d_mask_alt, s->d_stage[0], s->d_stage[1]};
+                  s->d_ppart, s->d_pbar, s->d_mask_alt, s->d_stage[0], s->d_stage[1], s->d_fstate};
   if (s->copy_stream) cudaStreamSynchronize(s->copy_stream);
   if (s->h2d_stream) cudaStreamSynchronize(s->h2d_stream);
   for (void* p : ptrs)
@@ -95,6 +95,61 @@ int check_flags(emrkc_solver* s) {
     cudaStreamSynchronize(s->stream);
     return s->fail(EMRKC_ERR_TIMEOUT, "a grid barrier of the CG solve gave up");
   }
+  if (flags & 16) {
+    int zero = 0;
+    cudaMemcpyAsync(s->d_flags, &zero, sizeof(int), cudaMemcpyHostToDevice, s->stream);
+    cudaStreamSynchronize(s->stream);
+    return s->fail(EMRKC_ERR_STATE, "a device-resident step needed more than 128 outer or inner stages");
+  }
+  return EMRKC_OK;
+}
+
+// Host copies of the device-resident step's state: rho estimates, iteration
+// counts, the last stage counts, and which power-iteration buffer holds the
+// last iterate (the host's pointers are swapped to match, the device's
+// indices reset).  A no-op unless a device-resident step ran since the
+// last call.
+int fused_pull(emrkc_solver* s) {
+  if (!s->fcluster || !s->fstate_stale) return EMRKC_OK;
+  cudaError_t e = cudaMemcpyAsync(&s->h_fstate, s->d_fstate, sizeof(FusedStepState), cudaMemcpyDeviceToHost,
+                                  s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return s->cuda_fail(e, "device step state");
+  FusedStepState& h = s->h_fstate;
+  s->rhoF_raw = h.rhoF_raw;
+  s->rhoS_raw = h.rhoS_raw;
+  s->itF = h.itF;
+  s->itS = h.itS;
+  s->total_it = h.total_it;
+  s->last_s = h.s;
+  s->last_m = h.m;
+  s->last_eta = h.eta;
+  s->last_rhoF = h.rhoF;
+  s->last_rhoS = h.rhoS;
+  if (h.curF) std::swap(s->d_vF, s->d_vF2);
+  if (h.curS) std::swap(s->d_vS, s->d_vS2);
+  h.curF = h.curS = 0;
+  e = cudaMemcpyAsync(s->d_fstate, &h, sizeof(FusedStepState), cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return s->cuda_fail(e, "device step state");
+  s->fstate_stale = false;
+  return EMRKC_OK;
+}
+
+// The host's rho estimates and counts into the device state (after a
+// power iteration run from the host).
+int fused_push(emrkc_solver* s) {
+  if (!s->fcluster) return EMRKC_OK;
+  FusedStepState& h = s->h_fstate;
+  h.rhoF_raw = s->rhoF_raw;
+  h.rhoS_raw = s->rhoS_raw;
+  h.itF = s->itF;
+  h.itS = s->itS;
+  h.total_it = s->total_it;
+  h.curF = h.curS = 0;
+  cudaError_t e = cudaMemcpyAsync(s->d_fstate, &h, sizeof(FusedStepState), cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return s->cuda_fail(e, "device step state");
   return EMRKC_OK;
 }
 
@@ -337,6 +392,7 @@ int power_fused(emrkc_solver* s) {
   a.mask = s->d_mask;
   a.stim = stim_at(s, s->t);
   a.Cm = s->Cm;
+  a.f_inv_Cm = (float)(1.0 / s->Cm);
   a.eps = s->opt.pow_eps;
   a.tol = s->opt.pow_tol;
   a.max_iter = s->opt.pow_max_iter;
@@ -372,9 +428,15 @@ int power_fused(emrkc_solver* s) {
 // Both spectral radii now: one cooperative launch for emRKC, the host-driven
 // loops for mRKC (whose f~_F and f~_S have their own kernels).
 int update_rho_now(emrkc_solver* s) {
-  if (s->method == EMRKC_METHOD_EMRKC && s->pfused_grid > 0) return power_fused(s);
-  int rc = power_F(s);
-  if (!rc) rc = power_S(s);
+  int rc = fused_pull(s);
+  if (rc) return rc;
+  if (s->method == EMRKC_METHOD_EMRKC && s->pfused_grid > 0) {
+    rc = power_fused(s);
+  } else {
+    rc = power_F(s);
+    if (!rc) rc = power_S(s);
+  }
+  if (!rc) rc = fused_push(s);
   return rc;
 }
 
@@ -476,9 +538,99 @@ int do_step_mrkc(emrkc_solver* s, double dt) {
   return EMRKC_OK;
 }
 
+// One emRKC step as one launch of the device-resident step kernel: the
+// rho policy's decision (due / fixed) is the host's, the estimates, stage
+// counts and coefficients are the kernel's; y_{n+1} lands in (cur + 1) mod 3.
+int do_step_fused(emrkc_solver* s, double dt) {
+  FusedStepArgs a;
+  a.n = s->n;
+  a.ld = s->ld;
+  a.b0 = s->cur;
+  for (int b = 0; b < 3; ++b) {
+    a.V[b] = s->d_V[b];
+    a.Z[b] = s->d_Z[b];
+    a.Vhi[b] = s->d_V32[b];
+    a.Vlo[b] = s->d_Vlo[b];
+    a.U[b] = s->d_U[b];
+    a.D[b] = s->d_D[b];
+  }
+  a.F = s->d_F;
+  a.LV = s->d_LV;
+  a.Vn = s->d_Vn;
+  a.Vn32 = s->d_Vn32;
+  a.mask = s->d_mask;
+  a.amp = s->amp;
+  a.t_on = s->t_on;
+  a.t_off = s->t_off;
+  a.Cm = s->Cm;
+  a.t_n = s->t;
+  a.dt = dt;
+  a.threshold = s->opt.act_threshold;
+  a.act = s->act_on ? s->d_act : nullptr;
+  a.flags = s->d_flags;
+  a.eps = s->opt.eps;
+  a.ell_wmax = s->ell_wmax;
+  a.safety = s->opt.safety;
+  a.rho_S_min = s->opt.rho_S_min;
+  if (s->opt.rho_every == EMRKC_RHO_FIXED) {
+    a.fixed = 1;
+    a.rho_F_fixed = s->opt.rho_F;
+    a.rho_S_fixed = s->opt.rho_S;
+  } else {
+    a.due = (s->opt.rho_every == EMRKC_RHO_ONCE) ? !s->rho_done : (s->steps % s->opt.rho_every == 0);
+  }
+  PowerFusedArgs& p = a.pw;
+  p.n = s->n;
+  p.ld = s->ld;
+  p.V = s->d_V[s->cur];
+  p.Vhi = s->d_V32[s->cur];
+  p.Vlo = s->d_Vlo[s->cur];
+  p.Z = s->d_Z[s->cur];
+  p.vF[0] = s->d_vF;
+  p.vF[1] = s->d_vF2;
+  p.vS[0] = s->d_vS;
+  p.vS[1] = s->d_vS2;
+  p.fy = s->d_fy;
+  p.mask = s->d_mask;
+  p.Cm = s->Cm;
+  p.f_inv_Cm = (float)(1.0 / s->Cm);
+  p.eps = s->opt.pow_eps;
+  p.tol = s->opt.pow_tol;
+  p.max_iter = s->opt.pow_max_iter;
+  p.tol_cold = s->opt.pow_tol_cold;
+  p.max_iter_cold = s->opt.pow_max_iter_cold;
+  p.part = s->d_ppart;
+  p.flags = s->d_flags;
+  a.state = s->d_fstate;
+  cudaError_t e = cudaSuccess;
+  s->launch(EMRKC_PHASE_STAGE, [&] { e = s->ks.step_fused(a, s->ell, s->fcluster, s->stream); });
+  if (e != cudaSuccess) return s->cuda_fail(e, "device-resident step launch");
+  if (a.due) s->rho_done = true;
+  s->cur = (s->cur + 1) % 3;
+  s->t += dt;
+  s->steps += 1;
+  s->fstate_stale = true;
+  return EMRKC_OK;
+}
+
 int do_step(emrkc_solver* s, double dt) {
   if (s->method == EMRKC_METHOD_EXEX_RL || s->method == EMRKC_METHOD_IMEX_RL) return do_step_rl(s, dt);
   if (s->method == EMRKC_METHOD_MRKC) return do_step_mrkc(s, dt);
+  if (s->fcluster > 0) {
+    // fixed radii whose stage counts exceed the device-resident step's
+    // limit take the host-driven step (estimated radii cannot be checked
+    // before the launch: the kernel then flags the step, bit 4)
+    bool fits = true;
+    if (s->opt.rho_every == EMRKC_RHO_FIXED) {
+      double l_s = 0.0;
+      const int S = stages_for(dt, s->opt.rho_S, s->opt.eps, &l_s);
+      const int Mi = stages_for(2.0 * dt / l_s, s->opt.rho_F, s->opt.eps, nullptr);
+      fits = S <= kFusedMaxStages && Mi <= kFusedMaxStages;
+    }
+    if (fits) return do_step_fused(s, dt);
+    const int rc = fused_pull(s);
+    if (rc) return rc;
+  }
   double rhoF, rhoS;
   int rc = step_rho(s, &rhoF, &rhoS);
   if (rc) return rc;
@@ -1015,9 +1167,34 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
     s->pcluster = s->ks.power_cluster_size ? s->ks.power_cluster_size(s->device) : 0;
     const char* no_cluster = std::getenv("EMRKC_NO_CLUSTER");
     if (no_cluster && no_cluster[0] == '1') s->pcluster = 0;
+    // device-resident steps for problems one cluster holds (at most 4 nodes
+    // per thread), by default for mixed precision with rho estimated every
+    // step: there the step saves the host round trip of every power
+    // iteration.  With rho known after the first step the host-driven step
+    // is faster (its stage kernels, chained by programmatic dependent launch,
+    // take about 3 us each against about 5 us for a stage inside the
+    // cluster), and FP64 is bound by the FP64 pipe, which the separate
+    // launches spread over more SMs than one cluster has.
+    // EMRKC_FUSED_STEP=0 / 1 turns the device-resident step off / on.
+    const char* fused_env = std::getenv("EMRKC_FUSED_STEP");
+    const bool want = fused_env && (fused_env[0] == '0' || fused_env[0] == '1')
+                          ? fused_env[0] == '1'
+                          : (s->precision == EMRKC_PREC_MIXED && o.rho_every == 1);
+    if (want && s->pcluster > 0 && s->pfused_grid >= 16 && s->ks.step_fused_cluster_size) {
+      const int cl = s->ks.step_fused_cluster_size(s->device);
+      if (cl > 0 && s->n <= (int64_t)4 * cl * s->ks.step_fused_block()) s->fcluster = cl;
+    }
     if (s->pfused_grid > 0) {
       fail |= dalloc(&s->d_ppart, 8 * (int64_t)s->pfused_grid) != cudaSuccess;
       fail |= dalloc(&s->d_pbar, 2) != cudaSuccess;
+    }
+    if (s->fcluster > 0) {
+      if (cudaMalloc(&s->d_fstate, sizeof(FusedStepState)) != cudaSuccess) {
+        s->d_fstate = nullptr;
+        fail = true;
+      } else {
+        fail |= cudaMemsetAsync(s->d_fstate, 0, sizeof(FusedStepState), s->stream) != cudaSuccess;
+      }
     }
   }
   fail |= dalloc(&s->rs.partials, kReduceMaxBlocks) != cudaSuccess;
@@ -1319,6 +1496,8 @@ int emrkc_set_time(emrkc_solver* s, double t, int64_t steps) {
 int emrkc_get_stats(emrkc_solver* s, emrkc_stats* out) {
   if (!s || !out) return EMRKC_ERR_ARG;
   cudaSetDevice(s->device);
+  int rc = fused_pull(s);
+  if (rc) return rc;
   s->harvest();
   std::memset(out, 0, sizeof(*out));
   out->t = s->t;

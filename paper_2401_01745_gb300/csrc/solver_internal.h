@@ -12,22 +12,13 @@
 
 #include "emrkc.h"
 #include "launch.h"
+#include "rkc_coeffs.h"
 
 namespace emrkc {
 
-// ---- Algorithm 1 on the host (FP64) -----------------------------------------
-// get_stages: smallest s >= 1 with beta s^2 >= dt rho, beta = 2 - 4 eps / 3.
-inline int stages_for(double dt, double rho, double eps, double* l_s) {
-  const double beta = 2.0 - 4.0 * eps / 3.0;
-  double s_real = std::ceil(std::sqrt(dt * rho / beta));
-  int s = (s_real < 1.0 || !(s_real == s_real)) ? 1 : (int)s_real;
-  if (s < 1) s = 1;
-  if (l_s) *l_s = beta * (double)s * (double)s;
-  return s;
-}
+// ---- Algorithm 1 (FP64): the shared definition of rkc_coeffs.h -------------
+inline int stages_for(double dt, double rho, double eps, double* l_s) { return rkc_stages(dt, rho, eps, l_s); }
 
-// get_coeffs: Chebyshev T_j(w0) by the three-term recurrence and
-// T_s'(w0) = s U_{s-1}(w0) with U by its own recurrence.
 struct Coeffs {
   std::vector<double> mu, nu, kappa, c;
 };
@@ -38,29 +29,7 @@ inline Coeffs make_coeffs(int s, double eps) {
   co.nu.assign(s + 1, 0.0);
   co.kappa.assign(s + 1, 0.0);
   co.c.assign(s + 1, 0.0);
-  const double w0 = 1.0 + eps / ((double)s * (double)s);
-  std::vector<double> T(s + 1), U(s + 1);
-  T[0] = 1.0;
-  U[0] = 1.0;
-  if (s >= 1) {
-    T[1] = w0;
-    U[1] = 2.0 * w0;
-  }
-  for (int j = 1; j < s; ++j) {
-    T[j + 1] = 2.0 * w0 * T[j] - T[j - 1];
-    U[j + 1] = 2.0 * w0 * U[j] - U[j - 1];
-  }
-  const double dTs = (double)s * U[s - 1];
-  const double w1 = T[s] / dTs;
-  co.mu[1] = w1 / w0;
-  co.c[1] = co.mu[1];
-  for (int j = 2; j <= s; ++j) {
-    // b_j = 1 / T_j(w0)
-    co.mu[j] = 2.0 * w1 * T[j - 1] / T[j];
-    co.nu[j] = 2.0 * w0 * T[j - 1] / T[j];
-    co.kappa[j] = -T[j - 2] / T[j];
-    co.c[j] = co.nu[j] * co.c[j - 1] + co.kappa[j] * co.c[j - 2] + co.mu[j];
-  }
+  rkc_coeffs(s, eps, co.mu.data(), co.nu.data(), co.kappa.data(), co.c.data());
   return co;
 }
 
@@ -185,6 +154,13 @@ struct emrkc_solver {
   emrkc::MrkcKernels mk{};
   double* d_Um[3] = {nullptr, nullptr, nullptr};  // inner stages, stiff-gate part
   int ell_wmax = 0;  // widest sliced-ELL slice
+  // device-resident step (emRKC on problems one cluster holds): cluster
+  // size (0: off), the device state, its host copy, and whether the host's
+  // rho, iteration and stage-count fields are behind the device's
+  int fcluster = 0;
+  emrkc::FusedStepState* d_fstate = nullptr;
+  emrkc::FusedStepState h_fstate{};
+  bool fstate_stale = false;
   bool act_on = false;
   double phase_ms[EMRKC_NUM_PHASES] = {0};
   int64_t phase_launches[EMRKC_NUM_PHASES] = {0};

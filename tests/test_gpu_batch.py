@@ -69,12 +69,12 @@ def test_batch_equals_solo_rho_once():
 
 
 @pytest.mark.parametrize("rF,rS,sm_expected", [(3000.0, 60.0, (2, 5)), (1000.0, 60.0, (2, 3)),
-                                                (1000.0, 300.0, (3, 2))])
+                                                (1000.0, 300.0, (3, 2)), (250.0, 10.0, (1, 3))])
 def test_batch_equals_solo_many_stages(rF, rS, sm_expected):
     """Fixed rho sets (s, m): the phase chain of the persistent kernel covers
     outer and inner three-term recurrences, with buffers written once per
-    launch (s <= 2, m <= 3: loads through L1) and rewritten within a launch
-    (s = 3 or m = 5: loads through L2)."""
+    launch (s = 1, m = 3: loads through L1) and rewritten within a launch
+    (s >= 2 with m >= 2, s = 3 or m = 5: loads through L2)."""
     dt, steps = 0.05, 30
     ws = [make_workload(n, h=h) for n, h in WORKLOADS[:3]]
     b = pkg.Batch(rho_every=pkg.RHO_FIXED, rho_F=rF, rho_S=rS)
