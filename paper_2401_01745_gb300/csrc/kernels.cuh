@@ -1339,28 +1339,50 @@ __device__ __forceinline__ PowerResult power_fused_body(const PowerFusedArgs& a,
     VT* vn = vF[curF ^ 1];
     VT acc = 0;
     const float qf = (float)q;
-    for (int64_t i = i0; i < a.n; i += stride) {
-      const int64_t b = i >> 5;
-      const int w = __ldg(A.width + b);
-      int64_t p = __ldg(A.slice_ptr + b) + (i & 31);
-      VT wv;
-      if constexpr (MIXED) {
-        // q L v in FP32: f_F is linear, so f_F(V + q v) - f_F(V) = q L v
-        const float vi = __ldcg(vo + i);
-        float s32 = 0.0f;
-        for (int k = 0; k < w; ++k, p += 32) s32 += __ldg(A.val32 + p) * (__ldcg(vo + __ldg(A.col + p)) - vi);
-        wv = qf * s32;
+    if constexpr (MIXED) {
+      if (a.ell_wmax <= 8) {
+        // rows of at most 8 entries: the row's columns and values, then all
+        // of its gathers, are issued at once (three dependent loads per node
+        // instead of two per entry); same sum in the same order
+#pragma unroll 2
+        for (int64_t i = i0; i < a.n; i += stride) {
+          int32_t c[8];
+          float lv[8], xv[8];
+          const int w = ell_row<8>(A, i, c, lv);
+          ell_gather_x<8, true>(c, w, vo, xv);
+          const float wv = qf * ell_reduce<8>(xv, lv, w, __ldcg(vo + i));
+          vn[i] = wv;
+          acc += wv * wv;
+        }
       } else {
+        for (int64_t i = i0; i < a.n; i += stride) {
+          const int64_t b = i >> 5;
+          const int w = __ldg(A.width + b);
+          int64_t p = __ldg(A.slice_ptr + b) + (i & 31);
+          // q L v in FP32: f_F is linear, so f_F(V + q v) - f_F(V) = q L v
+          const float vi = __ldcg(vo + i);
+          float s32 = 0.0f;
+          for (int k = 0; k < w; ++k, p += 32) s32 += __ldg(A.val32 + p) * (__ldcg(vo + __ldg(A.col + p)) - vi);
+          const float wv = qf * s32;
+          vn[i] = wv;
+          acc += wv * wv;
+        }
+      }
+    } else {
+      for (int64_t i = i0; i < a.n; i += stride) {
+        const int64_t b = i >> 5;
+        const int w = __ldg(A.width + b);
+        int64_t p = __ldg(A.slice_ptr + b) + (i & 31);
         double fz = 0.0, fy = 0.0;
         for (int k = 0; k < w; ++k, p += 32) {
           const int32_t c = __ldg(A.col + p);
           fz += __ldg(A.val + p) * (a.V[c] + q * __ldcg(vo + c));
           fy += __ldg(A.val + p) * a.V[c];
         }
-        wv = fz - fy;
+        const double wv = fz - fy;
+        vn[i] = wv;
+        acc += wv * wv;
       }
-      vn[i] = wv;
-      acc += wv * wv;
     }
     publish(1, acc, 0, 0, 0);
     if (!power_barrier<CLUSTER>(a)) return res;

@@ -165,6 +165,7 @@ struct PowerFusedArgs {
   const uint8_t* mask = nullptr;
   double stim = 0, Cm = 1;
   float f_inv_Cm = 1;                  // (float)(1 / Cm)
+  int ell_wmax = 1 << 30;              // widest sliced-ELL slice (rows of <= 8: split row loads)
   double eps = 1e-8, tol = 1e-2;
   int max_iter = 50;
   double tol_cold = 1e-4;        // a start with warm value 0 (no initial guess)

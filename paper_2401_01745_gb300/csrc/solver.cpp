@@ -393,6 +393,7 @@ int power_fused(emrkc_solver* s) {
   a.stim = stim_at(s, s->t);
   a.Cm = s->Cm;
   a.f_inv_Cm = (float)(1.0 / s->Cm);
+  a.ell_wmax = s->ell_wmax;
   a.eps = s->opt.pow_eps;
   a.tol = s->opt.pow_tol;
   a.max_iter = s->opt.pow_max_iter;
@@ -594,6 +595,7 @@ int do_step_fused(emrkc_solver* s, double dt) {
   p.mask = s->d_mask;
   p.Cm = s->Cm;
   p.f_inv_Cm = (float)(1.0 / s->Cm);
+  p.ell_wmax = s->ell_wmax;
   p.eps = s->opt.pow_eps;
   p.tol = s->opt.pow_tol;
   p.max_iter = s->opt.pow_max_iter;
