@@ -6,8 +6,9 @@ cudaMalloc).  For them the library keeps the reduction scratch of the f_F
 power iteration in a static device array; this test checks, through the C
 ABI, that the variant gives the rho_F and iteration count of
 emrkc_estimate_rho on two calls in a row (cold start, then warm start), in
-FP64 and in the mixed precision, and that it rejects a vector length that
-does not match the solver and every method other than emRKC.
+FP64 and in the mixed precision, that it agrees with the oracle's Algorithm
+5 from the same start vector, and that it rejects a vector length that does
+not match the solver and every method other than emRKC.
 
 It sits in a file of its own that pytest collects last, and it passes both
 alone in a fresh process and after the other GPU tests (the first call on a
@@ -62,6 +63,38 @@ def test_noalloc_rho_F_matches_estimate_rho(precision):
         sol.estimate_rho_F_noalloc(d_v.data_ptr(), d_w.data_ptr(), w.n + 1, 0.0)
     assert ei.value.code == 1
     ref.close()
+    sol.close()
+
+
+@pytest.mark.parametrize("precision", [pkg.PREC_FP64, pkg.PREC_MIXED])
+def test_noalloc_rho_F_matches_oracle(precision):
+    """The variant against the oracle's Algorithm 5 directly (not only
+    through emrkc_estimate_rho): from the same start vector at rest, a cold
+    start runs to the cold-start tolerance 1e-4; the estimate agrees with
+    the oracle's to 1e-9 in FP64 (the same differences of f_F; the iteration
+    counts are equal) and to the mixed path's 1e-4."""
+    import torch
+
+    from oracle.emrkc import Monodomain
+    from oracle.power import compute_rho, start_vector
+
+    pkg.build()
+    w = make_workload("slab23x9x5_ttp", h=0.01)
+    seed = 5
+    sol = pkg.Solver.from_workload(w, seed=seed, precision=precision)
+    v0 = start_vector(seed, w.n)
+    d_v = torch.tensor(v0, dtype=torch.float64, device="cuda")
+    d_w = torch.empty_like(d_v)
+    torch.cuda.synchronize()
+    r, it = sol.estimate_rho_F_noalloc(d_v.data_ptr(), d_w.data_ptr(), w.n, 0.0)
+    prob = Monodomain.from_workload(w)
+    _, ro, ito = compute_rho(0.0, prob.initial_state()[0], prob.rho_F_fn, v0, 0.0, tol=1e-4, max_iter=1000)
+    if precision == pkg.PREC_FP64:
+        assert it == ito
+        assert r == pytest.approx(ro, rel=1e-9)
+    else:
+        assert abs(it - ito) <= 2
+        assert r == pytest.approx(ro, rel=1e-4)
     sol.close()
 
 
