@@ -1295,36 +1295,66 @@ __device__ __forceinline__ PowerResult power_fused_body(const PowerFusedArgs& a,
   // or q J v (mixed path), rho = |v_new| / delta, until the relative change
   // of rho is below tol or max_iter iterations
   // no initial guess (warm value 0): the cold-start tolerance and cap
+  // Mixed path: these scalars in FP32 too (its iterates are FP32, and one
+  // thread's FP64 square roots and divisions cost about 0.4 us each on
+  // GB300's narrow FP64 pipe); FP64 path: in FP64.
   auto start = [&](double ny2, double nv2, double warm) {
     if (threadIdx.x == 0) {
-      const double ny = sqrt(ny2), nv = sqrt(nv2);
-      s_delta = ny > 0.0 ? ny * a.eps : a.eps;
       s_rho = warm;
       s_it = 0;
       s_tol = warm == 0.0 ? a.tol_cold : a.tol;
       s_maxit = warm == 0.0 ? a.max_iter_cold : a.max_iter;
-      if (nv == 0.0) {
-        s_rho = 0.0;
-        s_go = 0;
+      if constexpr (MIXED) {
+        const float ny = sqrtf((float)ny2), nv = sqrtf((float)nv2), e = (float)a.eps;
+        const float delta = ny > 0.0f ? ny * e : e;
+        s_delta = delta;
+        if (nv == 0.0f) {
+          s_rho = 0.0;
+          s_go = 0;
+        } else {
+          s_q = delta / nv;
+          s_go = (fabs(warm) >= s_tol * warm && s_maxit > 0) ? 1 : 0;
+        }
       } else {
-        s_q = s_delta / nv;
-        s_go = (fabs(warm) >= s_tol * warm && s_maxit > 0) ? 1 : 0;
+        const double ny = sqrt(ny2), nv = sqrt(nv2);
+        s_delta = ny > 0.0 ? ny * a.eps : a.eps;
+        if (nv == 0.0) {
+          s_rho = 0.0;
+          s_go = 0;
+        } else {
+          s_q = s_delta / nv;
+          s_go = (fabs(warm) >= s_tol * warm && s_maxit > 0) ? 1 : 0;
+        }
       }
     }
     __syncthreads();
   };
   auto advance = [&](double nv2) {
     if (threadIdx.x == 0) {
-      const double nv = sqrt(nv2);
       ++s_it;
-      if (nv == 0.0) {
-        s_rho = 0.0;
-        s_go = 0;
+      if constexpr (MIXED) {
+        const float nv = sqrtf((float)nv2);
+        if (nv == 0.0f) {
+          s_rho = 0.0;
+          s_go = 0;
+        } else {
+          const float rho_old = (float)s_rho, delta = (float)s_delta;
+          const float rho = nv / delta;
+          s_q = delta / nv;
+          s_rho = rho;
+          s_go = (fabsf(rho - rho_old) >= (float)s_tol * rho && s_it < s_maxit) ? 1 : 0;
+        }
       } else {
-        const double rho_old = s_rho;
-        s_q = s_delta / nv;
-        s_rho = nv / s_delta;
-        s_go = (fabs(s_rho - rho_old) >= s_tol * s_rho && s_it < s_maxit) ? 1 : 0;
+        const double nv = sqrt(nv2);
+        if (nv == 0.0) {
+          s_rho = 0.0;
+          s_go = 0;
+        } else {
+          const double rho_old = s_rho;
+          s_q = s_delta / nv;
+          s_rho = nv / s_delta;
+          s_go = (fabs(s_rho - rho_old) >= s_tol * s_rho && s_it < s_maxit) ? 1 : 0;
+        }
       }
     }
     __syncthreads();
@@ -1507,11 +1537,14 @@ __global__ void __launch_bounds__(FusedBlock<MR>::value, 1) step_fused_kernel(co
   __shared__ double s_ci[4][kFusedMaxStages + 1];  // inner mu', nu', kappa', c'
   __shared__ double s_eta;
   __shared__ int s_S, s_M;
-  // the scalars of the current phase, computed by thread 0 (GB300's FP64
-  // pipe is narrow: the divisions and conversions are done once per CTA,
-  // not once per thread)
-  __shared__ double s_pd[13];
-  __shared__ float s_pf[15];
+  // the scalars of every phase of the step (outer stage j at j - 1, inner
+  // stage k at k - 2), computed once per step, one thread per phase, with
+  // multiplications only (GB300's FP64 pipe is narrow, and a division or
+  // square root in one thread costs about 0.4 us)
+  __shared__ double s_sd[kFusedMaxStages][10];
+  __shared__ float s_sf[kFusedMaxStages][12];
+  __shared__ double s_id[kFusedMaxStages][3];
+  __shared__ float s_if[kFusedMaxStages][3];
   // launched with programmatic dependent launch: the next step's cluster
   // may be made resident now, and this one waits for the previous step
   pdl_trigger();
@@ -1564,21 +1597,20 @@ __global__ void __launch_bounds__(FusedBlock<MR>::value, 1) step_fused_kernel(co
     st->itF = st->itS = 0;
   }
 
-  // ---- Algorithm 1: stage counts and coefficients (the same in every CTA)
+  // ---- Algorithm 1: stage counts (the same in every CTA), coefficients
+  // from the host's tables
+  const int L = rkc_table_len(kFusedMaxStages);
+  const double* __restrict__ inv_ls = a.ctab + 4 * L;                        // 1 / (beta s^2)
+  const double* __restrict__ inv_mu1 = a.ctab + 4 * L + kFusedMaxStages + 1;  // 1 / mu_1 of s
   if (threadIdx.x == 0) {
     const double rhoF = a.fixed ? a.rho_F_fixed : a.safety * rF;
     const double rhoS = a.fixed ? a.rho_S_fixed : fmax(a.safety * rS, a.rho_S_min);
-    double l_s = 0.0;
-    const int S = rkc_stages(a.dt, rhoS, a.eps, &l_s);
-    const double eta = 2.0 * a.dt / l_s;
-    const int M = rkc_stages(eta, rhoF, a.eps, nullptr);
+    const int S = rkc_stages_mul(a.dt * rhoS, a.beta);
+    const double eta = S <= kFusedMaxStages ? a.two_dt * inv_ls[S] : 0.0;
+    const int M = S <= kFusedMaxStages ? rkc_stages_mul(eta * rhoF, a.beta) : 0;
     s_S = S;
     s_M = M;
     s_eta = eta;
-    if (S <= kFusedMaxStages && M <= kFusedMaxStages) {
-      rkc_coeffs(S, a.eps, s_co[0], s_co[1], s_co[2], s_co[3]);
-      rkc_coeffs(M, a.eps, s_ci[0], s_ci[1], s_ci[2], s_ci[3]);
-    }
     if (lead) {
       st->rhoF = rhoF;
       st->rhoS = rhoS;
@@ -1594,6 +1626,53 @@ __global__ void __launch_bounds__(FusedBlock<MR>::value, 1) step_fused_kernel(co
     cluster_sync_all();  // the power iteration's shared-memory reads are done
     return;
   }
+  for (int q = threadIdx.x; q < 4 * (S + 1); q += blockDim.x)
+    s_co[q / (S + 1)][q % (S + 1)] = a.ctab[(q / (S + 1)) * L + rkc_table_row(S) + q % (S + 1)];
+  for (int q = threadIdx.x; q < 4 * (M + 1); q += blockDim.x)
+    s_ci[q / (M + 1)][q % (M + 1)] = a.ctab[(q / (M + 1)) * L + rkc_table_row(M) + q % (M + 1)];
+  __syncthreads();
+  // every phase's scalars at once
+  for (int j = threadIdx.x + 1; j <= S; j += blockDim.x) {
+    const double eta = s_eta, mu1 = s_ci[0][1];
+    const double inv_eta = a.beta * (double)S * (double)S * a.inv_two_dt;
+    const double nu = j >= 2 ? s_co[1][j] : 1.0, kappa = j >= 2 ? s_co[2][j] : 0.0, mu_dt = s_co[0][j] * a.dt;
+    const double ts = __dadd_rn(a.t_n, __dmul_rn(s_co[3][j - 1], a.dt));
+    const double stim = (a.mask != nullptr && a.t_on <= ts && ts <= a.t_off) ? a.amp : 0.0;
+    double* sd = s_sd[j - 1];
+    float* sf = s_sf[j - 1];
+    sd[0] = nu;
+    sd[1] = kappa;
+    sd[2] = mu_dt;
+    sd[3] = eta;
+    sd[4] = s_ci[3][M];
+    sd[5] = mu1 * eta;
+    sd[6] = stim;
+    sd[7] = a.inv_Cm;
+    sd[8] = inv_eta;
+    sd[9] = mu1;
+    sf[0] = (float)nu;
+    sf[1] = (float)kappa;
+    sf[2] = (float)mu_dt;
+    sf[3] = (float)inv_eta;
+    sf[4] = (float)sd[4];
+    sf[5] = (float)mu1;
+    sf[6] = (float)sd[5];
+    sf[7] = (float)eta;
+    sf[8] = (float)stim;
+    sf[9] = (float)a.inv_Cm;
+    sf[10] = (float)a.threshold;
+    sf[11] = (float)(inv_eta * inv_mu1[M]);
+  }
+  for (int k = threadIdx.x + 2; k <= M; k += blockDim.x) {
+    const double mu_eta = s_ci[0][k] * s_eta;
+    s_id[k - 2][0] = s_ci[1][k];
+    s_id[k - 2][1] = s_ci[2][k];
+    s_id[k - 2][2] = mu_eta;
+    s_if[k - 2][0] = (float)s_ci[1][k];
+    s_if[k - 2][1] = (float)s_ci[2][k];
+    s_if[k - 2][2] = (float)mu_eta;
+  }
+  __syncthreads();
 
   // ---- the s outer stages, each followed by its m - 1 inner stages
   // Mixed path with one node per thread and rows of at most 8 entries: the
@@ -1612,63 +1691,34 @@ __global__ void __launch_bounds__(FusedBlock<MR>::value, 1) step_fused_kernel(co
   const bool l2 = S >= 3 || M >= 4 || (S >= 2 && M >= 2);
   for (int j = 1; j <= S; ++j) {
     const int bm1 = (b0 + rot * (j - 1)) % 3, bm2 = (b0 + rot * (j + 1)) % 3, bo = (b0 + rot * j) % 3;
-    // the phase's scalars (FP64 arithmetic, divisions, conversions) once
-    // per CTA; every thread then fills its arguments from them
-    if (threadIdx.x == 0) {
-      const double eta = s_eta, mu1 = s_ci[0][1];
-      const double nu = j >= 2 ? s_co[1][j] : 1.0, kappa = j >= 2 ? s_co[2][j] : 0.0, mu_dt = s_co[0][j] * a.dt;
-      const double ts = __dadd_rn(a.t_n, __dmul_rn(s_co[3][j - 1], a.dt));
-      const double stim = (a.mask != nullptr && a.t_on <= ts && ts <= a.t_off) ? a.amp : 0.0;
-      s_pd[0] = nu;
-      s_pd[1] = kappa;
-      s_pd[2] = mu_dt;
-      s_pd[3] = eta;
-      s_pd[4] = s_ci[3][M];
-      s_pd[5] = mu1 * eta;
-      s_pd[6] = stim;
-      s_pd[7] = 1.0 / a.Cm;
-      s_pd[8] = 1.0 / eta;
-      s_pd[9] = mu1;
-      s_pf[0] = (float)nu;
-      s_pf[1] = (float)kappa;
-      s_pf[2] = (float)mu_dt;
-      s_pf[3] = (float)s_pd[8];
-      s_pf[4] = (float)s_pd[4];
-      s_pf[5] = (float)mu1;
-      s_pf[6] = (float)s_pd[5];
-      s_pf[7] = (float)eta;
-      s_pf[8] = (float)stim;
-      s_pf[9] = (float)s_pd[7];
-      s_pf[10] = (float)a.threshold;
-      s_pf[11] = (float)(1.0 / s_pd[5]);
-    }
-    __syncthreads();
+    const double* sd = s_sd[j - 1];
+    const float* sf = s_sf[j - 1];
     StageArgs sa;
     sa.n = a.n;
     sa.ld = a.ld;
     sa.Zm1 = a.Z[bm1];
     sa.Zm2 = j >= 2 ? a.Z[bm2] : nullptr;
     sa.Zout = a.Z[bo];
-    sa.nu = s_pd[0];
-    sa.kappa = s_pd[1];
-    sa.mu_dt = s_pd[2];
-    sa.eta = s_pd[3];
-    sa.cm_inner = s_pd[4];
-    sa.mu1_eta = s_pd[5];
+    sa.nu = sd[0];
+    sa.kappa = sd[1];
+    sa.mu_dt = sd[2];
+    sa.eta = sd[3];
+    sa.cm_inner = sd[4];
+    sa.mu1_eta = sd[5];
     sa.m = M;
     sa.F = a.F;
     sa.mask = a.mask;
-    sa.stim = s_pd[6];
+    sa.stim = sd[6];
     sa.Cm = a.Cm;
-    sa.inv_Cm = s_pd[7];
+    sa.inv_Cm = sd[7];
     sa.final_stage = (j == S && M == 1) ? 1 : 0;
     sa.act = a.act;
     sa.t_n = a.t_n;
     sa.dt = a.dt;
     sa.threshold = a.threshold;
     sa.flags = a.flags;
-    sa.inv_eta = s_pd[8];
-    sa.mu1 = s_pd[9];
+    sa.inv_eta = sd[8];
+    sa.mu1 = sd[9];
     if constexpr (MIXED) {
       sa.V32m1 = a.Vhi[bm1];
       sa.V32out = a.Vhi[bo];
@@ -1678,19 +1728,19 @@ __global__ void __launch_bounds__(FusedBlock<MR>::value, 1) step_fused_kernel(co
       sa.Vlo_out = a.Vlo[bo];
       sa.Vn32 = (S <= 2) ? a.Vhi[b0] : a.Vn32;
       sa.Vn32_copy = (j == 1 && S >= 3) ? a.Vn32 : nullptr;
-      sa.f_th = s_pf[10];
+      sa.f_th = sf[10];
       sa.D1 = a.D[0];
       sa.LV = (M >= 4) ? a.LV : nullptr;
-      sa.f_nu = s_pf[0];
-      sa.f_kappa = s_pf[1];
-      sa.f_mudt = s_pf[2];
-      sa.f_inv_eta = s_pf[3];
-      sa.f_cm = s_pf[4];
-      sa.f_mu1 = s_pf[5];
-      sa.f_mu1eta = s_pf[6];
-      sa.f_eta = s_pf[7];
-      sa.f_stim = s_pf[8];
-      sa.f_inv_Cm = s_pf[9];
+      sa.f_nu = sf[0];
+      sa.f_kappa = sf[1];
+      sa.f_mudt = sf[2];
+      sa.f_inv_eta = sf[3];
+      sa.f_cm = sf[4];
+      sa.f_mu1 = sf[5];
+      sa.f_mu1eta = sf[6];
+      sa.f_eta = sf[7];
+      sa.f_stim = sf[8];
+      sa.f_inv_Cm = sf[9];
       sa.ell_wmax = a.ell_wmax;
       auto nodes = [&](auto cg_tag) {
         constexpr bool CG = decltype(cg_tag)::value;
@@ -1730,25 +1780,16 @@ __global__ void __launch_bounds__(FusedBlock<MR>::value, 1) step_fused_kernel(co
       if (l2) nodes(std::true_type{});
       else nodes(std::false_type{});
     }
-    // also the last read of this phase's scalars before thread 0 rewrites them
     cluster_sync_all();
     for (int k = 2; k <= M; ++k) {
-      if (threadIdx.x == 0) {
-        const double mu_eta = s_ci[0][k] * s_pd[3];
-        s_pd[10] = s_ci[1][k];
-        s_pd[11] = s_ci[2][k];
-        s_pd[12] = mu_eta;
-        s_pf[12] = (float)s_ci[1][k];
-        s_pf[13] = (float)s_ci[2][k];
-        s_pf[14] = (float)mu_eta;
-      }
-      __syncthreads();
+      const double* id = s_id[k - 2];
+      const float* ifl = s_if[k - 2];
       InnerArgs ib;
       ib.n = a.n;
       ib.F = a.F;
-      ib.nu = s_pd[10];
-      ib.kappa = s_pd[11];
-      ib.mu_eta = s_pd[12];
+      ib.nu = id[0];
+      ib.kappa = id[1];
+      ib.mu_eta = id[2];
       ib.last = (k == M) ? 1 : 0;
       ib.onu = sa.nu;
       ib.okappa = sa.kappa;
@@ -1767,7 +1808,7 @@ __global__ void __launch_bounds__(FusedBlock<MR>::value, 1) step_fused_kernel(co
         ib.dk = a.D[(k - 1) % 3];
         ib.LV = a.LV;
         ib.lf_src = (M >= 4) ? 0 : (k == 2 ? 1 : 2);
-        ib.f_inv_mu1eta = s_pf[11];
+        ib.f_inv_mu1eta = sf[11];
         ib.V32out = a.Vhi[bo];
         ib.Vhi1 = a.Vhi[bm1];
         ib.Vlo1 = a.Vlo[bm1];
@@ -1778,9 +1819,9 @@ __global__ void __launch_bounds__(FusedBlock<MR>::value, 1) step_fused_kernel(co
         ib.f_okappa = sa.f_kappa;
         ib.f_omu_dt = sa.f_mudt;
         ib.f_th = sa.f_th;
-        ib.f_nu = s_pf[12];
-        ib.f_kappa = s_pf[13];
-        ib.f_mueta = s_pf[14];
+        ib.f_nu = ifl[0];
+        ib.f_kappa = ifl[1];
+        ib.f_mueta = ifl[2];
         ib.f_inv_eta = sa.f_inv_eta;
         auto nodes = [&](auto cg_tag) {
           constexpr bool CG = decltype(cg_tag)::value;
@@ -1902,8 +1943,13 @@ struct Kernels {
     Ell Ac = A;
     if (grid < 0) {
       cudaLaunchConfig_t cfg = {};
+      // the device-resident step's CTA size where it fits (the smallest
+      // multiple of 32 that gives every node a thread): the same launch
+      // shape adds the norms' partial sums in the same order in both
+      const int64_t per = (a.n + (-grid) - 1) / (-grid);
+      const int block = (int)std::min<int64_t>(kReduceBlock, std::max<int64_t>(32, (per + 31) / 32 * 32));
       cfg.gridDim = dim3(-grid);
-      cfg.blockDim = dim3(kReduceBlock);
+      cfg.blockDim = dim3(block);
       cfg.stream = st;
       cudaLaunchAttribute at[1];
       at[0].id = cudaLaunchAttributeClusterDimension;

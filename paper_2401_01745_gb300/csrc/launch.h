@@ -218,6 +218,11 @@ struct FusedStepArgs {
   double safety = 1.05, rho_S_min = 0;
   PowerFusedArgs pw;                   // Algorithm 5: vF, vS in buffer order, scratch, tolerances
   FusedStepState* state = nullptr;
+  // Algorithm 1 without FP64 divisions on the device: the coefficient
+  // tables of rkc_coeffs.h for s = 1 .. kFusedMaxStages, and host-side
+  // reciprocals
+  const double* ctab = nullptr;
+  double beta = 2.0, two_dt = 0, inv_two_dt = 0, inv_Cm = 1;
 };
 
 struct Launchers;  // per precision mode

@@ -24,6 +24,29 @@ EMRKC_HD inline int rkc_stages(double dt, double rho, double eps, double* l_s) {
   return s;
 }
 
+// The same s without division or square root (for one device thread, whose
+// FP64 divisions and square roots are slow): the smallest s >= 1 with
+// beta s^2 >= x = dt rho, from an FP32 estimate corrected by exact FP64
+// comparisons.  x not finite or beyond 1e15 gives 1 << 24 (no step has that
+// many stages).
+EMRKC_HD inline int rkc_stages_mul(double x, double beta) {
+  if (!(x > beta)) return 1;  // also x NaN
+  if (!(x < 1e15)) return 1 << 24;
+  int s = (int)ceilf(sqrtf((float)x / (float)beta));
+  if (s < 1) s = 1;
+  while (s > 1 && beta * (double)(s - 1) * (double)(s - 1) >= x) --s;
+  while (beta * (double)s * (double)s < x) ++s;
+  return s;
+}
+
+// Coefficient tables for s = 1 .. smax in one array: four blocks (mu, nu,
+// kappa, c) of rkc_table_len(smax) entries, row s (s + 1 entries) at
+// rkc_table_row(s) of each block, then 1 / (beta s^2) and 1 / mu_1 for
+// s = 0 .. smax.
+EMRKC_HD inline int rkc_table_row(int s) { return (s - 1) * (s + 2) / 2; }
+EMRKC_HD inline int rkc_table_len(int smax) { return rkc_table_row(smax + 1); }
+EMRKC_HD inline int rkc_table_doubles(int smax) { return 4 * rkc_table_len(smax) + 2 * (smax + 1); }
+
 // get_coeffs into mu, nu, kappa, c [0 .. s]: Chebyshev T_j(w0) by the
 // three-term recurrence and T_s'(w0) = s U_{s-1}(w0), U by its own
 // recurrence (a first pass for T_s and U_{s-1}, a second for the stages).

@@ -52,7 +52,8 @@ void free_all(emrkc_solver* s) {
                   s->d_D[0], s->d_D[1], s->d_D[2], s->d_LV, s->d_Vlo[0], s->d_Vlo[1], s->d_Vlo[2],
                   s->d_Vn32, s->d_mass, s->d_cg[0], s->d_cg[1], s->d_cg[2], s->d_cg[3], s->d_cg[4],
                   s->d_cg[5], s->d_part, s->d_bar, s->d_iters, s->d_res, s->d_Um[0], s->d_Um[1], s->d_Um[2],
-                  s->d_ppart, s->d_pbar, s->d_mask_alt, s->d_stage[0], s->d_stage[1], s->d_fstate};
+                  s->d_ppart, s->d_pbar, s->d_mask_alt, s->d_stage[0], s->d_stage[1], s->d_fstate,
+                  s->d_ctab};
   if (s->copy_stream) cudaStreamSynchronize(s->copy_stream);
   if (s->h2d_stream) cudaStreamSynchronize(s->h2d_stream);
   for (void* p : ptrs)
@@ -604,6 +605,11 @@ int do_step_fused(emrkc_solver* s, double dt) {
   p.part = s->d_ppart;
   p.flags = s->d_flags;
   a.state = s->d_fstate;
+  a.ctab = s->d_ctab;
+  a.beta = 2.0 - 4.0 * s->opt.eps / 3.0;
+  a.two_dt = 2.0 * dt;
+  a.inv_two_dt = 1.0 / (2.0 * dt);
+  a.inv_Cm = 1.0 / s->Cm;
   cudaError_t e = cudaSuccess;
   s->launch(EMRKC_PHASE_STAGE, [&] { e = s->ks.step_fused(a, s->ell, s->fcluster, s->stream); });
   if (e != cudaSuccess) return s->cuda_fail(e, "device-resident step launch");
@@ -636,12 +642,17 @@ int do_step(emrkc_solver* s, double dt) {
   double rhoF, rhoS;
   int rc = step_rho(s, &rhoF, &rhoS);
   if (rc) return rc;
-  double l_s = 0.0;
-  const int S = stages_for(dt, rhoS, s->opt.eps, &l_s);
-  const double eta = 2.0 * dt / l_s;
-  const int Mi = stages_for(eta, rhoF, s->opt.eps, nullptr);
+  // Algorithm 1 in the device-resident step's own expressions (stage counts
+  // by comparison, eta and its reciprocals by multiplication), so that both
+  // step forms take the same coefficients to the last bit
+  const double beta = 2.0 - 4.0 * s->opt.eps / 3.0;
+  const int S = rkc_stages_mul(dt * rhoS, beta);
+  const double eta = (2.0 * dt) * (1.0 / (beta * (double)S * (double)S));
+  const int Mi = rkc_stages_mul(eta * rhoF, beta);
+  const double inv_eta = beta * (double)S * (double)S * (1.0 / (2.0 * dt));
   const Coeffs co = s->coeffs(S);
   const Coeffs ci = s->coeffs(Mi);
+  const float f_inv_mu1eta = (float)(inv_eta * (1.0 / ci.mu[1]));
   const int b0 = s->cur;
   // V_n for the activation test: buffer b0 survives the step while S <= 2
   // (stage j writes buffer b0 + j); a copy is kept for S >= 3
@@ -678,7 +689,7 @@ int do_step(emrkc_solver* s, double dt) {
     a.threshold = s->opt.act_threshold;
     a.flags = s->d_flags;
     a.Vn_copy = (j == 1 && S >= 3) ? s->d_Vn : nullptr;
-    a.inv_eta = 1.0 / eta;
+    a.inv_eta = inv_eta;
     a.mu1 = ci.mu[1];
     a.V32m1 = s->d_V32[bm1];
     a.V32out = s->d_V32[bo];
@@ -694,7 +705,7 @@ int do_step(emrkc_solver* s, double dt) {
     a.f_nu = (float)a.nu;
     a.f_kappa = (float)a.kappa;
     a.f_mudt = (float)a.mu_dt;
-    a.f_inv_eta = (float)(1.0 / eta);
+    a.f_inv_eta = (float)inv_eta;
     a.f_cm = (float)a.cm_inner;
     a.f_mu1 = (float)ci.mu[1];
     a.f_mu1eta = (float)(ci.mu[1] * eta);
@@ -732,13 +743,13 @@ int do_step(emrkc_solver* s, double dt) {
       b.dt = dt;
       b.threshold = s->opt.act_threshold;
       b.flags = s->d_flags;
-      b.inv_eta = 1.0 / eta;
+      b.inv_eta = inv_eta;
       b.d1 = s->d_D[(k - 2) % 3];
       b.d2 = (k - 2 == 0) ? nullptr : s->d_D[(k - 3) % 3];
       b.dk = s->d_D[(k - 1) % 3];
       b.LV = s->d_LV;
       b.lf_src = (Mi >= 4) ? 0 : (k == 2 ? 1 : 2);
-      b.f_inv_mu1eta = (float)(1.0 / (ci.mu[1] * eta));
+      b.f_inv_mu1eta = f_inv_mu1eta;
       b.V32out = s->d_V32[bo];
       b.Vhi1 = s->d_V32[bm1];
       b.Vlo1 = s->d_Vlo[bm1];
@@ -752,7 +763,7 @@ int do_step(emrkc_solver* s, double dt) {
       b.f_nu = (float)ci.nu[k];
       b.f_kappa = (float)ci.kappa[k];
       b.f_mueta = (float)(ci.mu[k] * eta);
-      b.f_inv_eta = (float)(1.0 / eta);
+      b.f_inv_eta = (float)inv_eta;
       b.ell_wmax = s->ell_wmax;
       b.pdl = s->pdl;
       s->launch(EMRKC_PHASE_INNER, [&] { s->ks.inner(b, s->ell, s->stream); });
@@ -1196,6 +1207,23 @@ int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_
         fail = true;
       } else {
         fail |= cudaMemsetAsync(s->d_fstate, 0, sizeof(FusedStepState), s->stream) != cudaSuccess;
+      }
+      // Algorithm 1's coefficients for every stage count the fused step
+      // can take, with 1 / (beta s^2) and 1 / mu_1 (rkc_coeffs.h layout)
+      const int L = rkc_table_len(kFusedMaxStages);
+      std::vector<double> tab(rkc_table_doubles(kFusedMaxStages), 0.0);
+      const double beta = 2.0 - 4.0 * s->opt.eps / 3.0;
+      for (int sc = 1; sc <= kFusedMaxStages; ++sc) {
+        const int r = rkc_table_row(sc);
+        rkc_coeffs(sc, s->opt.eps, &tab[r], &tab[L + r], &tab[2 * L + r], &tab[3 * L + r]);
+        tab[4 * L + sc] = 1.0 / (beta * (double)sc * (double)sc);
+        tab[4 * L + kFusedMaxStages + 1 + sc] = 1.0 / tab[r + 1];
+      }
+      if (cudaMalloc(&s->d_ctab, tab.size() * sizeof(double)) != cudaSuccess) {
+        s->d_ctab = nullptr;
+        fail = true;
+      } else {
+        fail |= cudaMemcpy(s->d_ctab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess;
       }
     }
   }

@@ -159,6 +159,7 @@ struct emrkc_solver {
   // rho, iteration and stage-count fields are behind the device's
   int fcluster = 0;
   emrkc::FusedStepState* d_fstate = nullptr;
+  double* d_ctab = nullptr;  // Algorithm 1 tables of the fused step (rkc_coeffs.h layout)
   emrkc::FusedStepState h_fstate{};
   bool fstate_stale = false;
   bool act_on = false;
