@@ -501,6 +501,7 @@ def batched_line(args, world, rank, local, dev):
                    "precision": MIXED_PRECISION_TEXT,
                    "persistent_launches_per_step": launches / args.steps,
                    "tile": tile, "block": block, "schedule": st["schedule"], "grid": st["grid"],
+                   "threads_per_sm": st["threads_per_sm"],
                    "items_per_step": st["items"],
                    "stage_counts": _stage_count_summary(b, specs),
                    "setup_s": setup_s, "device_gb": st["device_bytes"] / 1e9,

@@ -364,11 +364,16 @@ typedef struct {
   int schedule;         /* order of the work list: 0 whole phases,
                            1 / 2 at most 16 / 4 tiles per instance
                            in turn (chosen by the autotuner)       */
+  int threads_per_sm;   /* resident threads per SM the persistent
+                           kernel is compiled for: 1024, 1536 or
+                           2048, a register budget of 64, 40 or 32
+                           per thread (chosen by the autotuner)    */
 } emrkc_batch_stats;
 
 /* Options: device, cuda_stream, seed, act_threshold, rho_every (ONCE or
  * FIXED with rho_F/rho_S), use_graphs are used; precision is forced to MIXED.
- * opt may be NULL.  The batch starts with tile 1024 nodes, block 128. */
+ * opt may be NULL.  The batch starts with tile 1024 nodes, block 128, 1536
+ * threads per SM. */
 int emrkc_batch_create(const emrkc_options* opt, emrkc_batch** out);
 /* Add an instance (copies its inputs; same arguments as emrkc_create).
  * inst_opt (may be NULL: the batch's options) sets the instance's rho policy
@@ -394,7 +399,12 @@ int emrkc_batch_set_config(emrkc_batch* b, int tile, int block);
 /* Order of the work list: 0 (default) an instance's whole phase at a time,
  * 1 / 2 at most 16 / 4 tiles of an instance before the next ready one. */
 int emrkc_batch_set_schedule(emrkc_batch* b, int schedule);
-/* Time each (tile, block, work-list order) candidate over `reps` steps of size dt without
+/* Register budget of the persistent kernel, as resident threads per SM:
+ * 1024, 1536 (default) or 2048 (64, 40 or 32 registers per thread).  More
+ * threads hide more load latency; the heavier ionic models spill at the
+ * smaller budgets.  EMRKC_ERR_ARG for other values. */
+int emrkc_batch_set_occupancy(emrkc_batch* b, int threads_per_sm);
+/* Time each (tile, block, work-list order, register budget) candidate over `reps` steps of size dt without
  * advancing any instance (the candidates run with bookkeeping and
  * activation writes disabled) and keep the fastest.  Returns EMRKC_ERR_STATE
  * (configuration unchanged) if an instance has s >= 3, whose dry steps would

@@ -371,6 +371,9 @@ class Batch:
     def set_schedule(self, schedule):
         self._check(self._lib.emrkc_batch_set_schedule(self._h, schedule))
 
+    def set_occupancy(self, threads_per_sm):
+        self._check(self._lib.emrkc_batch_set_occupancy(self._h, threads_per_sm))
+
     def set_spin_limit(self, limit):
         self._check(self._lib.emrkc_batch_set_spin_limit(self._h, limit))
 

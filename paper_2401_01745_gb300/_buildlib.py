@@ -64,13 +64,16 @@ def build(verbose: bool = False, force: bool = False) -> str:
         # the mixed-precision unit uses approximate FP32 division/sqrt and
         # flush-to-zero (FP64 code in it is unaffected)
         fast = ["-use_fast_math"] if u in FAST_MATH_UNITS else []
-        cmd = [nvcc, *GENCODE, "-O3", "-lineinfo", "-std=c++17", *fast, "-Xcompiler", "-fPIC",
+        # a non-void function without a return is undefined behaviour that
+        # the optimiser turns into a function that never returns: an error
+        cmd = [nvcc, *GENCODE, "-O3", "-lineinfo", "-std=c++17", *fast, "--diag-error", "940",
+               "-Xcompiler", "-fPIC,-Werror=return-type",
                "-I", INCLUDE, "-I", CSRC, "-c", os.path.join(CSRC, u), "-o", obj]
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     for u in host_units:
         obj = os.path.join(BUILD_DIR, u + ".o")
         objs.append(obj)
-        cmd = ["g++", "-O3", "-std=c++17", "-fPIC", "-fopenmp", "-I", INCLUDE, "-I", CSRC,
+        cmd = ["g++", "-O3", "-std=c++17", "-fPIC", "-fopenmp", "-Werror=return-type", "-I", INCLUDE, "-I", CSRC,
                "-I", os.path.join(cuda, "include"), "-c", os.path.join(CSRC, u), "-o", obj]
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     failed = []

@@ -64,7 +64,7 @@ class BatchInfo(C.Structure):
 class BatchStats(C.Structure):
     _fields_ = [("instances", C.c_int), ("total_nodes", C.c_int64), ("items", C.c_int64),
                 ("tile", C.c_int), ("block", C.c_int), ("grid", C.c_int), ("launches", C.c_int64),
-                ("device_bytes", C.c_int64), ("schedule", C.c_int)]
+                ("device_bytes", C.c_int64), ("schedule", C.c_int), ("threads_per_sm", C.c_int)]
 
 
 _P = C.c_void_p
@@ -113,6 +113,7 @@ SIGNATURES = {
     "emrkc_batch_set_config": (C.c_int, [_P, C.c_int, C.c_int]),
     "emrkc_batch_set_spin_limit": (C.c_int, [_P, C.c_int64]),
     "emrkc_batch_set_schedule": (C.c_int, [_P, C.c_int]),
+    "emrkc_batch_set_occupancy": (C.c_int, [_P, C.c_int]),
     "emrkc_batch_autotune": (C.c_int, [_P, C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                        C.POINTER(C.c_double)]),
     "emrkc_batch_set_stimulus_async": (C.c_int, [_P, C.POINTER(C.c_uint8), C.c_int64]),

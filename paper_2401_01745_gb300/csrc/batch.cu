@@ -82,8 +82,12 @@ __device__ __forceinline__ void batch_stage_rows(const StageArgs& a, const Ell& 
   }
 }
 
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) batch_step_kernel(const BatchCtl c) {
+// TPS: resident threads per SM the kernel is compiled for (1024, 1536 or
+// 2048: a register budget of 64, 40 or 32 per thread).  The light models'
+// items are bound by load latency and gain from the occupancy; TTP06's spill
+// at the smaller budgets.  The autotuner chooses.
+template <int BLOCK, int TPS>
+__global__ void __launch_bounds__(BLOCK, TPS / BLOCK) batch_step_kernel(const BatchCtl c) {
   __shared__ unsigned int s_item;
   __shared__ int s_abort;
   // Thread 0 takes the next ticket while the CTA works on the current item
@@ -301,18 +305,30 @@ void launch_batch_scatter_mask(uint8_t* const* masks, const int64_t* off, int ni
   batch_scatter_mask_kernel<<<dim3(64, (unsigned)ni), 256, 0, st>>>(masks, off, src);
 }
 
-void launch_batch_step(const BatchCtl& c, int grid, int block, cudaStream_t st) {
-  if (block == 256) batch_step_kernel<256><<<grid, 256, 0, st>>>(c);
-  else batch_step_kernel<128><<<grid, 128, 0, st>>>(c);
+namespace {
+template <int BLOCK>
+void launch_tps(const BatchCtl& c, int grid, int tps, cudaStream_t st) {
+  if (tps == 2048) batch_step_kernel<BLOCK, 2048><<<grid, BLOCK, 0, st>>>(c);
+  else if (tps == 1536) batch_step_kernel<BLOCK, 1536><<<grid, BLOCK, 0, st>>>(c);
+  else batch_step_kernel<BLOCK, 1024><<<grid, BLOCK, 0, st>>>(c);
+}
+template <int BLOCK>
+int blocks_tps(int tps) {
+  int nb = 0;
+  if (tps == 2048) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_step_kernel<BLOCK, 2048>, BLOCK, 0);
+  else if (tps == 1536) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_step_kernel<BLOCK, 1536>, BLOCK, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_step_kernel<BLOCK, 1024>, BLOCK, 0);
+  return nb;
+}
+}  // namespace
+
+void launch_batch_step(const BatchCtl& c, int grid, int block, int tps, cudaStream_t st) {
+  if (block == 256) launch_tps<256>(c, grid, tps, st);
+  else launch_tps<128>(c, grid, tps, st);
 }
 
-int batch_blocks_per_sm(int block) {
-  int nb = 0;
-  if (block == 256)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_step_kernel<256>, 256, 0);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_step_kernel<128>, 128, 0);
-  return nb;
+int batch_blocks_per_sm(int block, int tps) {
+  return block == 256 ? blocks_tps<256>(tps) : blocks_tps<128>(tps);
 }
 
 }  // namespace emrkc

@@ -55,6 +55,7 @@ struct emrkc_batch {
   int* d_err = nullptr;
   int tile = 1024, block = 128, grid = 0;
   int sched = 0;  // order of the work list (rebuild)
+  int tps = 1536; // resident threads per SM of the persistent kernel (register budget)
   long long spin_limit = 1 << 24;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -245,7 +246,7 @@ int rebuild(emrkc_batch* b, double dt) {
   // items it depends on (deadlock-free in-order consumption).
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-  b->grid = std::max(1, sms * std::max(1, batch_blocks_per_sm(b->block)));
+  b->grid = std::max(1, sms * std::max(1, batch_blocks_per_sm(b->block, b->tps)));
   // Schedule 0 emits an instance's whole phase at once (the first ready
   // instance in index order); schedules 1 and 2 emit at most 16 or 4 tiles of
   // an instance before moving on to the next ready instance (cyclically), so
@@ -323,7 +324,7 @@ int enqueue_step(emrkc_batch* b, int dry) {
       if (e != cudaSuccess) return b->cuda_fail(e, "graph capture");
       cudaMemsetAsync(b->d_done, 0, ni * kBatchMaxPhases * sizeof(unsigned int), b->stream);
       cudaMemsetAsync(b->d_ticket, 0, sizeof(unsigned int), b->stream);
-      launch_batch_step(make_ctl(b, 0), b->grid, b->block, b->stream);
+      launch_batch_step(make_ctl(b, 0), b->grid, b->block, b->tps, b->stream);
       e = cudaStreamEndCapture(b->stream, &b->graph);
       if (e != cudaSuccess) return b->cuda_fail(e, "graph capture");
       e = cudaGraphInstantiate(&b->exec, b->graph, 0);
@@ -344,7 +345,7 @@ int enqueue_step(emrkc_batch* b, int dry) {
       }
       cudaEventRecord(pr.first, b->stream);
     }
-    launch_batch_step(make_ctl(b, dry), b->grid, b->block, b->stream);
+    launch_batch_step(make_ctl(b, dry), b->grid, b->block, b->tps, b->stream);
     e = cudaGetLastError();
     if (e != cudaSuccess) return b->cuda_fail(e, "batch launch");
     if (pr.second) {
@@ -610,6 +611,7 @@ int emrkc_batch_get_stats(emrkc_batch* b, emrkc_batch_stats* out) {
   out->grid = b->grid;
   out->launches = b->launches;
   out->schedule = b->sched;
+  out->threads_per_sm = b->tps;
   return EMRKC_OK;
 }
 
@@ -620,6 +622,17 @@ int emrkc_batch_set_config(emrkc_batch* b, int tile, int block) {
   if (tile != b->tile || block != b->block) {
     b->tile = tile;
     b->block = block;
+    b->dirty = true;
+  }
+  return EMRKC_OK;
+}
+
+int emrkc_batch_set_occupancy(emrkc_batch* b, int threads_per_sm) {
+  if (!b) return EMRKC_ERR_ARG;
+  if (threads_per_sm != 1024 && threads_per_sm != 1536 && threads_per_sm != 2048)
+    return b->fail(EMRKC_ERR_ARG, "threads per SM must be 1024, 1536 or 2048");
+  if (threads_per_sm != b->tps) {
+    b->tps = threads_per_sm;
     b->dirty = true;
   }
   return EMRKC_OK;
@@ -647,33 +660,39 @@ int emrkc_batch_autotune(emrkc_batch* b, double dt, int reps, int* tile_out, int
   const int tiles[] = {512, 1024, 2048, 4096, 8192};
   const int blocks[] = {128, 256};
   const int scheds[] = {0, 1, 2};
-  const int keep_tile = b->tile, keep_block = b->block, keep_sched = b->sched;
-  int best_tile = keep_tile, best_block = keep_block, best_sched = keep_sched;
+  const int tpss[] = {1024, 1536, 2048};
+  const int keep_tile = b->tile, keep_block = b->block, keep_sched = b->sched, keep_tps = b->tps;
+  int best_tile = keep_tile, best_block = keep_block, best_sched = keep_sched, best_tps = keep_tps;
   double best = 1e300;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (int sc : scheds) {
-    for (int tl : tiles) {
-      for (int bl : blocks) {
-        b->tile = tl;
-        b->block = bl;
-        b->sched = sc;
-        if ((rc = rebuild(b, dt))) break;
-        if ((rc = enqueue_step(b, 1))) break;
-        cudaEventRecord(e0, b->stream);
-        for (int r = 0; r < reps && !rc; ++r) rc = enqueue_step(b, 1);
-        cudaEventRecord(e1, b->stream);
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        const double per = ms / reps;
-        if (per < best) {
-          best = per;
-          best_tile = tl;
-          best_block = bl;
-          best_sched = sc;
+  for (int tp : tpss) {
+    for (int sc : scheds) {
+      for (int tl : tiles) {
+        for (int bl : blocks) {
+          b->tile = tl;
+          b->block = bl;
+          b->sched = sc;
+          b->tps = tp;
+          if ((rc = rebuild(b, dt))) break;
+          if ((rc = enqueue_step(b, 1))) break;
+          cudaEventRecord(e0, b->stream);
+          for (int r = 0; r < reps && !rc; ++r) rc = enqueue_step(b, 1);
+          cudaEventRecord(e1, b->stream);
+          cudaEventSynchronize(e1);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          const double per = ms / reps;
+          if (per < best) {
+            best = per;
+            best_tile = tl;
+            best_block = bl;
+            best_sched = sc;
+            best_tps = tp;
+          }
         }
+        if (rc) break;
       }
       if (rc) break;
     }
@@ -684,11 +703,13 @@ int emrkc_batch_autotune(emrkc_batch* b, double dt, int reps, int* tile_out, int
   b->tile = best_tile;
   b->block = best_block;
   b->sched = best_sched;
+  b->tps = best_tps;
   b->dirty = true;
   if (rc) {
     b->tile = keep_tile;
     b->block = keep_block;
     b->sched = keep_sched;
+    b->tps = keep_tps;
     return rc;
   }
   int err = 0;

@@ -418,8 +418,10 @@ struct BatchCtl {
 inline uint64_t batch_item(int inst, int phase, int tile) {
   return ((uint64_t)(uint32_t)inst << 40) | ((uint64_t)(uint32_t)phase << 32) | (uint32_t)tile;
 }
-void launch_batch_step(const BatchCtl& c, int grid, int block, cudaStream_t st);
-int batch_blocks_per_sm(int block);
+// tps: resident threads per SM the persistent kernel is compiled for (1024,
+// 1536 or 2048)
+void launch_batch_step(const BatchCtl& c, int grid, int block, int tps, cudaStream_t st);
+int batch_blocks_per_sm(int block, int tps);
 // Whole-batch host I/O: V of every instance (current state buffer, joined to
 // double) into out[off[k] ...]; node masks from src[off[k] ...] into each
 // instance's mask buffer.  ni instances, off has ni + 1 entries.

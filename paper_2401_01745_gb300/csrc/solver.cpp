@@ -649,6 +649,10 @@ int do_step(emrkc_solver* s, double dt) {
   const int S = rkc_stages_mul(dt * rhoS, beta);
   const double eta = (2.0 * dt) * (1.0 / (beta * (double)S * (double)S));
   const int Mi = rkc_stages_mul(eta * rhoF, beta);
+  // a radius that is not finite (or beyond any useful stage count) gives
+  // 1 << 24 stages: refuse the step instead of launching them
+  if (S >= (1 << 24) || Mi >= (1 << 24))
+    return s->fail(EMRKC_ERR_STATE, "spectral radius estimate not finite or too large for a step");
   const double inv_eta = beta * (double)S * (double)S * (1.0 / (2.0 * dt));
   const Coeffs co = s->coeffs(S);
   const Coeffs ci = s->coeffs(Mi);

@@ -264,3 +264,35 @@ def test_work_list_orders_give_identical_states(schedule):
         b.close()
     for x, y in zip(*out):
         np.testing.assert_array_equal(x, y)
+
+
+@pytest.mark.parametrize("tps", [1024, 2048])
+def test_register_budgets_give_identical_states(tps):
+    """The persistent kernel compiled for 1024, 1536 (default) or 2048
+    resident threads per SM (64, 40 or 32 registers per thread; the heavier
+    models spill at the smaller budgets) computes the same per-node
+    arithmetic: every instance's state is bit for bit the same.  Instances
+    with s = 2, m = 1 (HH), s = 1 and m = 2 (TTP06) and the inner-stage
+    recurrences of a fixed rho (s = 2, m = 3) are covered."""
+    dt, steps = 0.05, 12
+    ws = [make_workload(n, h=h) for n, h in WORKLOADS]
+    out = []
+    for t in (1536, tps):
+        b = pkg.Batch()
+        ids = [b.add_workload(w) for w in ws]
+        ids.append(b.add_workload(ws[1], rho_every=pkg.RHO_FIXED, rho_F=1000.0, rho_S=60.0))
+        b.set_occupancy(t)
+        for _ in range(steps):
+            b.step(dt)
+        b.sync()
+        assert b.stats()["threads_per_sm"] == t
+        out.append([b.get_state(i) for i in ids])
+        b.close()
+    for x, y in zip(*out):
+        np.testing.assert_array_equal(x, y)
+    with pytest.raises(pkg.EmrkcError):
+        b = pkg.Batch()
+        try:
+            b.set_occupancy(1000)
+        finally:
+            b.close()
