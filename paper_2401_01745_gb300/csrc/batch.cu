@@ -83,9 +83,10 @@ __device__ __forceinline__ void batch_stage_rows(const StageArgs& a, const Ell& 
 }
 
 // TPS: resident threads per SM the kernel is compiled for (1024, 1536 or
-// 2048: a register budget of 64, 40 or 32 per thread).  The light models'
-// items are bound by load latency and gain from the occupancy; TTP06's spill
-// at the smaller budgets.  The autotuner chooses.
+// 2048: a register budget of 64, 40 or 32 per thread).  The items are bound
+// by the latency of their global loads and gain from more resident warps;
+// the two smaller budgets spill some registers to local memory (mostly L1
+// hits).  The autotuner chooses.
 template <int BLOCK, int TPS>
 __global__ void __launch_bounds__(BLOCK, TPS / BLOCK) batch_step_kernel(const BatchCtl c) {
   __shared__ unsigned int s_item;
