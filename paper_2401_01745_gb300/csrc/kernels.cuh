@@ -145,24 +145,46 @@ __device__ __forceinline__ void step_epilogue_ff(int64_t i, float Vn, float Vnew
   }
 }
 
-// Exponential step (Algorithm 3, Exponential_Euler) and f_S at one node,
-// mixed path (FP32).  dz receives the gate increments y_E - y =
-// (e^{eta Lambda} - 1)(z - z_inf); f_S is evaluated at the gates y_E = z + dz.
-template <class Model>
-__device__ __forceinline__ void ionic_mixed(float eta, float V, const float* z, float* dz, float& Iion, float* gS) {
-  constexpr int NE = Model::NE;
-  using M = Math<float>;
+// Mixed path (FP32), one node of outer stage j: the exponential step of the
+// gates (Algorithm 3, Exponential_Euler), f_S at the gates y_E, and the z
+// rows of g_j = nu g_{j-1} + kappa g_{j-2} + mu dt f_bar with f_bar =
+// (y_E - y)/eta on the gates and c_m g_S on z_S (HAS_M2: j >= 2).  Each gate's
+// row is written as soon as its increment dz = y_E - y = (e^{eta Lambda} - 1)
+// (z - z_inf) is known, so that only y_E and z_S stay live through f_S.
+// Returns F = (I_stim - I_ion) / C_m.
+template <class Model, bool HAS_M2, bool CG>
+__device__ __forceinline__ float stage_rows_mixed(const StageArgs& a, const int64_t i, const float V, const float* z,
+                                                  const bool stim) {
+  constexpr int NE = Model::NE, NS = Model::NS, NZ = NE + NS;
+  const int64_t ld = a.ld;
+  const float* __restrict__ Zm2 = static_cast<const float*>(a.Zm2);
+  float* __restrict__ Zout = static_cast<float*>(a.Zout);
+  const float mudt_eta = a.f_mudt * a.f_inv_eta;
   float zE1[NE > 0 ? NE : 1];
-  if constexpr (NE > 0) {
-    float lam[NE], zinf[NE];
-    Model::gating(V, z, z + NE, lam, zinf);
+  Model::gating_each(V, z, z + NE, [&](int k, float lam, float zinf) {
+    const float dz = Math<float>::em1(a.f_eta * lam) * (z[k] - zinf);
+    zE1[k] = z[k] + dz;
+    const float mfbar = mudt_eta * dz;
+    float out;
+    if constexpr (HAS_M2) out = a.f_nu * z[k] + a.f_kappa * ldm<CG>(Zm2 + k * ld + i) + mfbar;
+    else out = z[k] + mfbar;
+    Zout[k * ld + i] = out;
+  });
+  float Iion;
+  float gS[NS > 0 ? NS : 1];
+  Model::currents(V, zE1, z + NE, Iion, gS);
+  if constexpr (NS > 0) {
 #pragma unroll
-    for (int k = 0; k < NE; ++k) {
-      dz[k] = M::em1(eta * lam[k]) * (z[k] - zinf[k]);
-      zE1[k] = z[k] + dz[k];
+    for (int k = NE; k < NZ; ++k) {
+      const float mfbar = a.f_mudt * (a.f_cm * gS[k - NE]);
+      float out;
+      if constexpr (HAS_M2) out = a.f_nu * z[k] + a.f_kappa * ldm<CG>(Zm2 + k * ld + i) + mfbar;
+      else out = z[k] + mfbar;
+      Zout[k * ld + i] = out;
     }
   }
-  Model::currents(V, zE1, z + NE, Iion, gS);
+  const float Istim = stim ? a.f_stim : 0.0f;
+  return (Istim - Iion) * a.f_inv_Cm;
 }
 
 // ---------------------------------------------------------------------------
@@ -244,10 +266,6 @@ template <class Model, bool HAS_M2, bool CG, bool SPLIT = false, bool ROW = fals
 __device__ __forceinline__ void stage_node_mixed_with(const StageArgs& a, const Ell& A, const int64_t i, const float V,
                                                       const float* z, const int32_t* rc = nullptr,
                                                       const float* rv = nullptr, const int rw = 0) {
-  constexpr int NE = Model::NE, NS = Model::NS, NZ = NE + NS;
-  const int64_t ld = a.ld;
-  const float* __restrict__ Zm2 = static_cast<const float*>(a.Zm2);
-  float* __restrict__ Zout = static_cast<float*>(a.Zout);
   // the neighbour gathers go out before the ionic model, so their latency
   // overlaps it; the row's values are read after it
   const bool split = SPLIT && a.ell_wmax <= 8;
@@ -267,25 +285,7 @@ __device__ __forceinline__ void stage_node_mixed_with(const StageArgs& a, const 
     for (int k = 0; k < 8; ++k)
       if (k < w) xv[k] = ldm<CG>(a.V32m1 + __ldg(A.col + p + 32 * k));
   }
-  float dz[NE > 0 ? NE : 1];
-  float Iion;
-  float gS[NS > 0 ? NS : 1];
-  ionic_mixed<Model>(a.f_eta, V, z, dz, Iion, gS);
-  const float mudt_eta = a.f_mudt * a.f_inv_eta;
-  const float Istim = (a.mask != nullptr && a.mask[i]) ? a.f_stim : 0.0f;
-  const float F = (Istim - Iion) * a.f_inv_Cm;
-
-  if constexpr (NZ > 0) {
-#pragma unroll
-    for (int k = 0; k < NZ; ++k) {
-      // mu dt f_bar: f_bar = (y_E - y) / eta on the gates, c_m g_S on z_S
-      const float mfbar = (k < NE) ? mudt_eta * dz[k < NE ? k : 0] : a.f_mudt * (a.f_cm * gS[k >= NE ? k - NE : 0]);
-      float out;
-      if constexpr (HAS_M2) out = a.f_nu * z[k] + a.f_kappa * ldm<CG>(Zm2 + k * ld + i) + mfbar;
-      else out = z[k] + mfbar;
-      Zout[k * ld + i] = out;
-    }
-  }
+  const float F = stage_rows_mixed<Model, HAS_M2, CG>(a, i, V, z, a.mask != nullptr && a.mask[i]);
   float LV = 0.0f;
   if constexpr (ROW) {
 #pragma unroll
@@ -421,28 +421,7 @@ __device__ __forceinline__ void stage_node_core(const StageArgs& a, const Ell& A
                                                 const float V, const unsigned char mk,
                                                 const float (&xv)[kTmaStageEllWidth], const int w, const float* sval,
                                                 const int base) {
-  constexpr int NE = Model::NE, NS = Model::NS, NZ = NE + NS;
-  float dz[NE > 0 ? NE : 1];
-  float Iion;
-  float gS[NS > 0 ? NS : 1];
-  ionic_mixed<Model>(a.f_eta, V, z, dz, Iion, gS);
-  const float mudt_eta = a.f_mudt * a.f_inv_eta;
-  const float Istim = mk ? a.f_stim : 0.0f;
-  const float F = (Istim - Iion) * a.f_inv_Cm;
-  float* __restrict__ Zout = static_cast<float*>(a.Zout);
-  const float* __restrict__ Zm2 = static_cast<const float*>(a.Zm2);
-  const int64_t ld = a.ld;
-  if constexpr (NZ > 0) {
-#pragma unroll
-    for (int k = 0; k < NZ; ++k) {
-      // mu dt f_bar: f_bar = (y_E - y) / eta on the gates, c_m g_S on z_S
-      const float mfbar = (k < NE) ? mudt_eta * dz[k < NE ? k : 0] : a.f_mudt * (a.f_cm * gS[k >= NE ? k - NE : 0]);
-      float out;
-      if constexpr (HAS_M2) out = a.f_nu * z[k] + a.f_kappa * __ldg(Zm2 + k * ld + i) + mfbar;
-      else out = z[k] + mfbar;
-      Zout[k * ld + i] = out;
-    }
-  }
+  const float F = stage_rows_mixed<Model, HAS_M2, false>(a, i, V, z, mk != 0);
   // sparse row: slot k of row i at base + 32 k in the staged tile
   float LV = 0.0f;
   if (sval == nullptr) {

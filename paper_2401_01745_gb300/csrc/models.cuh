@@ -2,11 +2,14 @@
 //
 // Each model exposes, per node and templated on the arithmetic type R
 // (double for the FP64 path, float for the mixed path):
-//   gating(V, zE, zS, lam, zinf)  : Lambda_E (<= 0) and z_inf of every gate, so
-//                                   that g_E = Lambda_E (zE - z_inf).  Gates in
+//   gating_each(V, zE, zS, cb)    : calls cb(k, Lambda_k, z_inf_k) for every gate k
+//                                   as soon as both are known, so that a caller
+//                                   can consume a gate while the next is computed;
+//                                   g_E = Lambda_E (zE - z_inf).  Gates in
 //                                   alpha/beta form use Lambda = -(alpha+beta),
 //                                   z_inf = alpha/(alpha+beta); tau-form gates use
 //                                   Lambda = -1/tau.
+//   gating(V, zE, zS, lam, zinf)  : the same into arrays.
 //   currents(V, zE, zS, Iion, gS) : total ionic current (uA/cm^2 at 1 uF/cm^2) and
 //                                   the right-hand side g_S of the non-gating
 //                                   variables (Eq. mono_in_FSE).
@@ -65,6 +68,8 @@ template <> struct Math<float> {
 // Pure diffusion: V only.
 template <typename R> struct ModelNone {
   static constexpr int NE = 0, NS = 0;
+  template <class CB>
+  static __device__ __forceinline__ void gating_each(R, const R*, const R*, CB&&) {}
   static __device__ __forceinline__ void gating(R, const R*, const R*, R*, R*) {}
   static __device__ __forceinline__ void currents(R, const R*, const R*, R& I, R*) { I = R(0); }
   static __host__ __device__ constexpr double rest(int) { return 0.0; }
@@ -75,9 +80,15 @@ template <typename R> struct ModelNone {
 // one auxiliary c with g_S = -k_c c.  All three components are decoupled.
 template <typename R> struct ModelPassive {
   static constexpr int NE = 1, NS = 1;
-  static __device__ __forceinline__ void gating(R, const R*, const R*, R* lam, R* zinf) {
-    lam[0] = -(R(20) + R(30));
-    zinf[0] = R(20) / (R(20) + R(30));
+  template <class CB>
+  static __device__ __forceinline__ void gating_each(R, const R*, const R*, CB&& cb) {
+    cb(0, -(R(20) + R(30)), R(20) / (R(20) + R(30)));
+  }
+  static __device__ __forceinline__ void gating(R V, const R* zE, const R* zS, R* lam, R* zinf) {
+    gating_each(V, zE, zS, [&](int k, R l, R zi) {
+      lam[k] = l;
+      zinf[k] = zi;
+    });
   }
   static __device__ __forceinline__ void currents(R V, const R*, const R* zS, R& I, R* gS) {
     I = R(0.5) * V;
@@ -104,14 +115,18 @@ template <typename R> struct ModelHH {
     a[2] = R(0.1) * M::x_em1((R(10.0) - v) * R(1.0 / 10.0));  // alpha_n = 0.01(10-v)/(e^{(10-v)/10}-1)
     b[2] = R(0.125) * M::ex(-v * R(1.0 / 80.0));          // beta_n
   }
-  static __device__ __forceinline__ void gating(R V, const R*, const R*, R* lam, R* zinf) {
+  template <class CB>
+  static __device__ __forceinline__ void gating_each(R V, const R*, const R*, CB&& cb) {
     R a[3], b[3];
     rates(V, a, b);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      lam[k] = -(a[k] + b[k]);
-      zinf[k] = a[k] / (a[k] + b[k]);
-    }
+    for (int k = 0; k < 3; ++k) cb(k, -(a[k] + b[k]), a[k] / (a[k] + b[k]));
+  }
+  static __device__ __forceinline__ void gating(R V, const R* zE, const R* zS, R* lam, R* zinf) {
+    gating_each(V, zE, zS, [&](int k, R l, R zi) {
+      lam[k] = l;
+      zinf[k] = zi;
+    });
   }
   static __device__ __forceinline__ void currents(R V, const R* zE, const R*, R& I, R*) {
     const R m = zE[0], h = zE[1], n = zE[2];
@@ -138,75 +153,80 @@ template <typename R> struct ModelTTP06 {
   // 1 / (1 + e^{s (V - c)})
   static __device__ __forceinline__ R sg(R V, double c, double s) { return R(1) / (R(1) + M::ex_aff(V, c, s)); }
 
-  static __device__ __forceinline__ void gating(R V, const R*, const R* zS, R* lam, R* zinf) {
+  template <class CB>
+  static __device__ __forceinline__ void gating_each(R V, const R*, const R* zS, CB&& cb) {
     const R CaSS = zS[5];
     // I_Na gates
     {
       const R s = sg(V, -56.86, -(1.0 / 9.03));
-      zinf[0] = s * s;
       const R am = sg(V, -60.0, -(1.0 / 5.0));
       const R bm = R(0.1) * sg(V, -35.0, 1.0 / 5.0) + R(0.10) * sg(V, 50.0, 1.0 / 200.0);
-      lam[0] = -R(1) / (am * bm);
+      cb(0, -R(1) / (am * bm), s * s);
     }
     const R hs = sg(V, -71.55, 1.0 / 7.43);
-    zinf[1] = hs * hs;
-    zinf[2] = hs * hs;
     if (V >= R(-40.0)) {
       const R bh = R(0.77) / (R(0.13) * (R(1) + M::ex_aff(V, -10.66, -(1.0 / 11.1))));
-      lam[1] = -bh;  // alpha_h = 0
+      cb(1, -bh, hs * hs);  // alpha_h = 0
       const R bj = R(0.6) * M::ex_aff(V, 0.0, 0.057) / (R(1) + M::ex_aff(V, -32.0, -0.1));
-      lam[2] = -bj;  // alpha_j = 0
+      cb(2, -bj, hs * hs);  // alpha_j = 0
     } else {
       const R ah = R(0.057) * M::ex_aff(V, -80.0, -(1.0 / 6.8));
       const R bh = R(2.7) * M::ex_aff(V, 0.0, 0.079) + R(3.1e5) * M::ex_aff(V, 0.0, 0.3485);
-      lam[1] = -(ah + bh);
+      cb(1, -(ah + bh), hs * hs);
       const R aj = (R(-2.5428e4) * M::ex_aff(V, 0.0, 0.2444) - R(6.948e-6) * M::ex_aff(V, 0.0, -0.04391)) *
                    (V + R(37.78)) / (R(1) + M::ex_aff(V, -79.23, 0.311));
       const R bj = R(0.02424) * M::ex_aff(V, 0.0, -0.01052) / (R(1) + M::ex_aff(V, -40.14, -0.1378));
-      lam[2] = -(aj + bj);
+      cb(2, -(aj + bj), hs * hs);
     }
     // I_Kr gates
-    zinf[3] = sg(V, -26.0, -(1.0 / 7.0));
-    lam[3] = -R(1) / ((R(450.0) * sg(V, -45.0, -(1.0 / 10.0))) * (R(6.0) * sg(V, -30.0, 1.0 / 11.5)));
-    zinf[4] = sg(V, -88.0, 1.0 / 24.0);
-    lam[4] = -R(1) / ((R(3.0) * sg(V, -60.0, -(1.0 / 20.0))) * (R(1.12) * sg(V, 60.0, 1.0 / 20.0)));
+    cb(3, -R(1) / ((R(450.0) * sg(V, -45.0, -(1.0 / 10.0))) * (R(6.0) * sg(V, -30.0, 1.0 / 11.5))),
+       sg(V, -26.0, -(1.0 / 7.0)));
+    cb(4, -R(1) / ((R(3.0) * sg(V, -60.0, -(1.0 / 20.0))) * (R(1.12) * sg(V, 60.0, 1.0 / 20.0))),
+       sg(V, -88.0, 1.0 / 24.0));
     // I_Ks gate
-    zinf[5] = sg(V, -5.0, -(1.0 / 14.0));
-    lam[5] = -R(1) / ((R(1400.0) / M::sq(R(1) + M::ex_aff(V, 5.0, -(1.0 / 6.0)))) * sg(V, 35.0, 1.0 / 15.0) +
-                      R(80.0));
+    cb(5,
+       -R(1) / ((R(1400.0) / M::sq(R(1) + M::ex_aff(V, 5.0, -(1.0 / 6.0)))) * sg(V, 35.0, 1.0 / 15.0) + R(80.0)),
+       sg(V, -5.0, -(1.0 / 14.0)));
     // I_to gates (epicardial s)
-    zinf[6] = sg(V, 20.0, -(1.0 / 6.0));
     {
       const R d40 = V + R(40.0);
-      lam[6] = -R(1) / (R(9.5) * M::ex(-(d40 * d40) * R(1.0 / 1800.0)) + R(0.8));
+      cb(6, -R(1) / (R(9.5) * M::ex(-(d40 * d40) * R(1.0 / 1800.0)) + R(0.8)), sg(V, 20.0, -(1.0 / 6.0)));
     }
-    zinf[7] = sg(V, -20.0, 1.0 / 5.0);
     {
       const R d45 = V + R(45.0);
-      lam[7] = -R(1) / (R(85.0) * M::ex(-(d45 * d45) * R(1.0 / 320.0)) + R(5.0) * sg(V, 20.0, 1.0 / 5.0) + R(3.0));
+      cb(7, -R(1) / (R(85.0) * M::ex(-(d45 * d45) * R(1.0 / 320.0)) + R(5.0) * sg(V, 20.0, 1.0 / 5.0) + R(3.0)),
+         sg(V, -20.0, 1.0 / 5.0));
     }
     // I_CaL gates
-    zinf[8] = sg(V, -8.0, -(1.0 / 7.5));
-    lam[8] = -R(1) / ((R(1.4) * sg(V, -35.0, -(1.0 / 13.0)) + R(0.25)) * (R(1.4) * sg(V, -5.0, 1.0 / 5.0)) +
-                      sg(V, 50.0, -(1.0 / 20.0)));
-    zinf[9] = sg(V, -20.0, 1.0 / 7.0);
+    cb(8,
+       -R(1) / ((R(1.4) * sg(V, -35.0, -(1.0 / 13.0)) + R(0.25)) * (R(1.4) * sg(V, -5.0, 1.0 / 5.0)) +
+                sg(V, 50.0, -(1.0 / 20.0))),
+       sg(V, -8.0, -(1.0 / 7.5)));
     {
       const R d27 = V + R(27.0);
-      lam[9] = -R(1) / (R(1102.5) * M::ex(-(d27 * d27) * R(1.0 / 225.0)) + R(200.0) * sg(V, 13.0, -(1.0 / 10.0)) +
-                        R(180.0) * sg(V, -30.0, 1.0 / 10.0) + R(20.0));
+      cb(9,
+         -R(1) / (R(1102.5) * M::ex(-(d27 * d27) * R(1.0 / 225.0)) + R(200.0) * sg(V, 13.0, -(1.0 / 10.0)) +
+                  R(180.0) * sg(V, -30.0, 1.0 / 10.0) + R(20.0)),
+         sg(V, -20.0, 1.0 / 7.0));
     }
-    zinf[10] = R(0.67) * sg(V, -35.0, 1.0 / 7.0) + R(0.33);
     {
       const R d25 = V + R(25.0);
-      lam[10] = -R(1) / (R(600.0) * M::ex(-(d25 * d25) * R(1.0 / 170.0)) + R(31.0) * sg(V, 25.0, -(1.0 / 10.0)) +
-                         R(16.0) * sg(V, -30.0, 1.0 / 10.0));
+      cb(10,
+         -R(1) / (R(600.0) * M::ex(-(d25 * d25) * R(1.0 / 170.0)) + R(31.0) * sg(V, 25.0, -(1.0 / 10.0)) +
+                  R(16.0) * sg(V, -30.0, 1.0 / 10.0)),
+         R(0.67) * sg(V, -35.0, 1.0 / 7.0) + R(0.33));
     }
     {
       const R c = CaSS * R(1.0 / 0.05);
       const R q = R(1) + c * c;
-      zinf[11] = R(0.6) / q + R(0.4);
-      lam[11] = -R(1) / (R(80.0) / q + R(2.0));
+      cb(11, -R(1) / (R(80.0) / q + R(2.0)), R(0.6) / q + R(0.4));
     }
+  }
+  static __device__ __forceinline__ void gating(R V, const R* zE, const R* zS, R* lam, R* zinf) {
+    gating_each(V, zE, zS, [&](int k, R l, R zi) {
+      lam[k] = l;
+      zinf[k] = zi;
+    });
   }
 
   static __device__ __forceinline__ void currents(R V, const R* zE, const R* zS, R& Iion, R* gS) {
