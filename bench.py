@@ -47,10 +47,10 @@ import numpy as np  # noqa: E402
 # command is in profiles/stage_kernel_mixed_tma_pf_slab_ttp.md).  Reported only
 # while the kernel sources hash to the captured state.
 NCU_TRAFFIC = {"kernel": "stage_kernel_mixed_tma_pf<ModelTTP06<float>, false>", "workload": "slab_ttp",
-               "bytes_per_launch": 55202816 + 1882880,
+               "bytes_per_launch": 55213824 + 1949184,
                "sources": ("paper_2401_01745_gb300/csrc/kernels.cuh", "paper_2401_01745_gb300/csrc/models.cuh",
                            "paper_2401_01745_gb300/csrc/kernels_mixed.cu"),
-               "sha256": "285376c43bd783704d2d98124bd2f8a99c46226ae7667b8f479d918256ee1d31"}
+               "sha256": "da739140793334712781c681125641805b77b220066bda35e61cae750859dc9b"}
 
 
 def _sources_sha256(paths):
@@ -432,11 +432,11 @@ def _batched_bytes(b, specs):
 # scaled to the full batch by the algorithmic bytes (the traffic of a launch
 # grows with the work it does).  Reported only while the kernel sources hash
 # to the captured state.
-NCU_BATCH_TRAFFIC = {"instances": 48, "bytes_per_launch": 771398912 + 292239360,
+NCU_BATCH_TRAFFIC = {"instances": 48, "threads_per_sm": 1536, "bytes_per_launch": 749352192 + 268642816,
                      "algorithmic_bytes_per_launch": 1040028606.0,
                      "sources": ("paper_2401_01745_gb300/csrc/kernels.cuh", "paper_2401_01745_gb300/csrc/models.cuh",
                                  "paper_2401_01745_gb300/csrc/batch.cu"),
-                     "sha256": "afd6148f2ba675dd3d902181570f780a28bb43cb488301005d9b36b13b0e540d"}
+                     "sha256": "b67c0704be81cca79d00aa3c31a6e33451f8814f8d9d3cfe2eeb0eb10e737d47"}
 
 
 def batched_line(args, world, rank, local, dev):
@@ -461,6 +461,10 @@ def batched_line(args, world, rank, local, dev):
             b.step(0.05)
     b.sync()
     tile, block, tune_ms = b.autotune(0.05, reps=3)
+    if args.threads_per_sm:
+        # a fixed register budget (for a profiler capture of one build); the
+        # autotuner's tile, block and schedule are kept
+        b.set_occupancy(args.threads_per_sm)
     bytes_step = _batched_bytes(b, specs)
     torch.cuda.synchronize()
     _barrier(world)
@@ -490,7 +494,8 @@ def batched_line(args, world, rank, local, dev):
     avg_launch_ms = kms / max(kn, 1)
     achieved = bytes_step / (avg_launch_ms / 1e3) / 1e9
     traffic = None
-    if NCU_BATCH_TRAFFIC["sha256"] == _sources_sha256(NCU_BATCH_TRAFFIC["sources"]):
+    if (NCU_BATCH_TRAFFIC["sha256"] == _sources_sha256(NCU_BATCH_TRAFFIC["sources"])
+            and st["threads_per_sm"] == NCU_BATCH_TRAFFIC["threads_per_sm"]):
         traffic = NCU_BATCH_TRAFFIC["bytes_per_launch"] * bytes_step / NCU_BATCH_TRAFFIC["algorithmic_bytes_per_launch"]
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -514,9 +519,10 @@ def batched_line(args, world, rank, local, dev):
                      "algorithmic_bytes_per_launch": bytes_step, "avg_launch_us": avg_launch_ms * 1e3,
                      "launches_timed": kn, "traffic": traffic,
                      "traffic_note": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch over the "
-                                      f"first {NCU_BATCH_TRAFFIC['instances']} instances, scaled to the full batch "
-                                      "by algorithmic bytes") if traffic is not None else
-                     "no ncu capture of the current kernel sources"},
+                                      f"first {NCU_BATCH_TRAFFIC['instances']} instances at "
+                                      f"{NCU_BATCH_TRAFFIC['threads_per_sm']} resident threads per SM, scaled to "
+                                      "the full batch by algorithmic bytes") if traffic is not None else
+                     "no ncu capture of the current kernel sources at this register budget"},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
@@ -1509,6 +1515,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--instances", type=int, default=256, help="instances of the batched workload")
+    ap.add_argument("--threads-per-sm", type=int, default=0, choices=[0, 1024, 1536, 2048],
+                    help="batched line: resident threads per SM after autotuning (0: the autotuner's choice)")
     ap.add_argument("--accuracy-instances", type=int, default=16)
     ap.add_argument("--accuracy-T", type=float, default=50.0)
     ap.add_argument("--no-fp64-all", dest="fp64_all", action="store_false",
