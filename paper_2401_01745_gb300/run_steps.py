@@ -32,6 +32,7 @@ def main(argv=None):
     ap.add_argument("--h", type=float, default=None, help="mesh size for parametrised workload names")
     ap.add_argument("--method", default="emrkc", choices=["emrkc", "exex", "imex", "mrkc"])
     ap.add_argument("--dt", type=float, default=None)
+    ap.add_argument("--rho-s-min", type=float, default=0.0, help="lower bound on rho_S (known stiffness, Sec. 3.1)")
     a = ap.parse_args(argv)
     pkg.build()
     kw = {} if a.h is None else {"h": a.h}
@@ -40,7 +41,7 @@ def main(argv=None):
     method = {"emrkc": pkg.METHOD_EMRKC, "exex": pkg.METHOD_EXEX_RL, "imex": pkg.METHOD_IMEX_RL,
               "mrkc": pkg.METHOD_MRKC}[a.method]
     dt = w.dt if a.dt is None else a.dt
-    sol = pkg.Solver.from_workload(w, precision=prec, rho_every=a.rho_every, method=method)
+    sol = pkg.Solver.from_workload(w, precision=prec, rho_every=a.rho_every, method=method, rho_S_min=a.rho_s_min)
     t0 = time.perf_counter()
     for _ in range(a.steps):
         sol.step(dt)
