@@ -208,6 +208,27 @@ int emrkc_num_vars(int ionic_model);
 /* Number of gating variables nE of an ionic model, or -1. */
 int emrkc_num_gates(int ionic_model);
 
+/* Algorithm 1, get_stages: the stage count s >= 1 of the damped RKC method
+ * (damping eps) for a step dt and a spectral radius rho, i.e. the smallest
+ * s with beta s^2 >= dt rho, beta = 2 - 4 eps / 3, so that dt times the
+ * spectrum lies in the stability interval [-beta s^2, 0] (Sec. 3.1).  Every
+ * path of the library takes its counts from this definition: the outer
+ * stages from dt and rho_S, the inner stages from eta = 2 dt / (beta s^2)
+ * and rho_F (Algorithm 3).  Writes *s and, if l_s is not NULL, the interval
+ * length beta s^2.  Host routine: no device is needed.  Errors:
+ * EMRKC_ERR_ARG for a NULL s; dt, rho or eps negative or not finite;
+ * eps >= 1.5 (beta <= 0); or dt rho >= 1e15 (s beyond the library's limits). */
+int emrkc_rkc_stages(double dt, double rho, double eps, int* s, double* l_s);
+
+/* Algorithm 1, get_coeffs: the coefficients of the s-stage damped RKC
+ * method from the Chebyshev polynomials at omega_0 = 1 + eps / s^2:
+ * mu_j, nu_j, kappa_j for j = 1..s (entry 0 is 0; nu_1 = kappa_1 = 0) and the
+ * internal times c_j for j = 0..s (c_0 = 0, c_s = 1).  mu, nu, kappa and c
+ * are caller-owned host arrays of s + 1 doubles.  Host routine: no device
+ * is needed.  Errors: EMRKC_ERR_ARG for s < 1 or s > 2^20, eps negative or
+ * not finite, or a NULL array. */
+int emrkc_rkc_coeffs(int s, double eps, double* mu, double* nu, double* kappa, double* c);
+
 /* P1 stiffness K and row-sum lumped mass of a simplex mesh (Sec. 2.1).
  * dim in {1, 2, 3}; xyz: n_nodes*dim doubles (node-major); cells:
  * n_cells*(dim+1) node indices; D_per_cell: n_cells*dim*dim doubles, the

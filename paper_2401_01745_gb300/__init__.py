@@ -48,6 +48,26 @@ def num_gates(model: int) -> int:
     return lib().emrkc_num_gates(model)
 
 
+def rkc_stages(dt, rho, eps=0.05):
+    """Algorithm 1 stage count s and interval length beta s^2 (host routine)."""
+    s, ls = C.c_int(), C.c_double()
+    rc = lib().emrkc_rkc_stages(dt, rho, eps, C.byref(s), C.byref(ls))
+    if rc != 0:
+        raise EmrkcError(rc, "rkc_stages: invalid arguments")
+    return s.value, ls.value
+
+
+def rkc_coeffs(s, eps=0.05):
+    """Algorithm 1 coefficients mu, nu, kappa, c of the s-stage method (host routine)."""
+    if s < 1:
+        raise EmrkcError(1, "rkc_coeffs: s must be >= 1")
+    arrs = [np.zeros(s + 1) for _ in range(4)]
+    rc = lib().emrkc_rkc_coeffs(s, eps, *[_dp(a) for a in arrs])
+    if rc != 0:
+        raise EmrkcError(rc, "rkc_coeffs: invalid arguments")
+    return tuple(arrs)
+
+
 def assemble_p1(coords, cells, D):
     """P1 stiffness K (CSR arrays) and lumped mass by the library's host assembler."""
     coords = np.ascontiguousarray(coords, dtype=np.float64)

@@ -74,6 +74,9 @@ SIGNATURES = {
     "emrkc_default_options": (C.c_int, [C.POINTER(Options)]),
     "emrkc_num_vars": (C.c_int, [C.c_int]),
     "emrkc_num_gates": (C.c_int, [C.c_int]),
+    "emrkc_rkc_stages": (C.c_int, [C.c_double, C.c_double, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "emrkc_rkc_coeffs": (C.c_int, [C.c_int, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                   C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "emrkc_assemble_p1": (C.c_int, [C.c_int, C.c_int64, _PD, C.c_int64, C.POINTER(C.c_int64), _PD,
                                     C.POINTER(OwnedMatrix)]),
     "emrkc_free_matrix": (None, [C.POINTER(OwnedMatrix)]),

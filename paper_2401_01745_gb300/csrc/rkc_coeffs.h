@@ -13,22 +13,11 @@
 
 namespace emrkc {
 
-// get_stages: smallest s >= 1 with beta s^2 >= dt rho, beta = 2 - 4 eps / 3;
-// l_s = beta s^2 (the length of the stability interval).
-EMRKC_HD inline int rkc_stages(double dt, double rho, double eps, double* l_s) {
-  const double beta = 2.0 - 4.0 * eps / 3.0;
-  const double s_real = ceil(sqrt(dt * rho / beta));
-  int s = (s_real < 1.0 || !(s_real == s_real)) ? 1 : (int)s_real;
-  if (s < 1) s = 1;
-  if (l_s) *l_s = beta * (double)s * (double)s;
-  return s;
-}
-
-// The same s without division or square root (for one device thread, whose
-// FP64 divisions and square roots are slow): the smallest s >= 1 with
-// beta s^2 >= x = dt rho, from an FP32 estimate corrected by exact FP64
-// comparisons.  x not finite or beyond 1e15 gives 1 << 24 (no step has that
-// many stages).
+// get_stages without division or square root (one device thread's FP64
+// divisions and square roots are slow): the smallest s >= 1 with
+// beta s^2 >= x = dt rho, from an FP32 estimate corrected by FP64
+// comparisons of beta s^2 with x.  x not finite or beyond 1e15 gives 1 << 24
+// (no step has that many stages).
 EMRKC_HD inline int rkc_stages_mul(double x, double beta) {
   if (!(x > beta)) return 1;  // also x NaN
   if (!(x < 1e15)) return 1 << 24;
@@ -36,6 +25,17 @@ EMRKC_HD inline int rkc_stages_mul(double x, double beta) {
   if (s < 1) s = 1;
   while (s > 1 && beta * (double)(s - 1) * (double)(s - 1) >= x) --s;
   while (beta * (double)s * (double)s < x) ++s;
+  return s;
+}
+
+// get_stages: smallest s >= 1 with beta s^2 >= dt rho, beta = 2 - 4 eps / 3;
+// l_s = beta s^2 (the length of the stability interval).  Every path takes
+// its stage counts from this definition (the device-resident step calls
+// rkc_stages_mul with beta computed once).
+EMRKC_HD inline int rkc_stages(double dt, double rho, double eps, double* l_s) {
+  const double beta = 2.0 - 4.0 * eps / 3.0;
+  const int s = rkc_stages_mul(dt * rho, beta);
+  if (l_s) *l_s = beta * (double)s * (double)s;
   return s;
 }
 

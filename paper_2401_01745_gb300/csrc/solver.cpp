@@ -1031,6 +1031,23 @@ int emrkc_num_gates(int model) {
   }
 }
 
+int emrkc_rkc_stages(double dt, double rho, double eps, int* s, double* l_s) {
+  if (!s) return EMRKC_ERR_ARG;
+  if (!(dt >= 0.0) || !(rho >= 0.0) || !(eps >= 0.0) || !std::isfinite(dt) || !std::isfinite(rho) ||
+      !std::isfinite(eps) || !(eps < 1.5))
+    return EMRKC_ERR_ARG;
+  if (!(dt * rho < 1e15)) return EMRKC_ERR_ARG;
+  *s = emrkc::stages_for(dt, rho, eps, l_s);
+  return EMRKC_OK;
+}
+
+int emrkc_rkc_coeffs(int s, double eps, double* mu, double* nu, double* kappa, double* c) {
+  if (s < 1 || s > (1 << 20) || !(eps >= 0.0) || !std::isfinite(eps) || !mu || !nu || !kappa || !c)
+    return EMRKC_ERR_ARG;
+  emrkc::rkc_coeffs(s, eps, mu, nu, kappa, c);
+  return EMRKC_OK;
+}
+
 int emrkc_create(const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_model, const emrkc_stimulus* stim,
                  const emrkc_options* opt, emrkc_solver** out) {
   if (!out) {
