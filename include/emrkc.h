@@ -403,33 +403,55 @@ int emrkc_batch_create(const emrkc_options* opt, emrkc_batch** out);
  * batch-unique id.  Takes effect at the next step. */
 int emrkc_batch_add(emrkc_batch* b, const emrkc_matrix* mat, const emrkc_tissue* tissue, int ionic_model,
                     const emrkc_stimulus* stim, const emrkc_options* inst_opt, int* id_out);
-/* Remove an instance and free its device memory. */
+/* Remove an instance and free its device memory, after waiting for the
+ * batch's stream; the work plan is rebuilt at the next step.  Errors:
+ * EMRKC_ERR_ARG (unknown id). */
 int emrkc_batch_remove(emrkc_batch* b, int id);
-/* One emRKC step of size dt for every instance: one persistent launch. */
+/* One emRKC step (Algorithm 3) of size dt (ms) for every instance: one
+ * persistent launch, enqueued on the batch's stream (the call does not wait
+ * for it).  After instances joined or left, or when dt changes, the work
+ * plan is rebuilt first: Algorithm 5 runs for instances that have no
+ * estimate yet (EMRKC_RHO_ONCE), Algorithm 1 sets each instance's s and m,
+ * and the call waits for the plan's upload.  Errors: EMRKC_ERR_ARG (dt not
+ * positive and finite, or an instance's stage counts beyond s, m <= 32,
+ * s * m <= 64), EMRKC_ERR_OOM, EMRKC_ERR_CUDA, and the power iteration's
+ * errors. */
 int emrkc_batch_step(emrkc_batch* b, double dt);
 /* Wait for enqueued steps; EMRKC_ERR_NONFINITE if an instance produced a
  * non-finite V, EMRKC_ERR_TIMEOUT if a dependency wait gave up. */
 int emrkc_batch_sync(emrkc_batch* b);
+/* As emrkc_get_state, emrkc_set_state and emrkc_get_activation_times for
+ * the instance id (same arguments, layouts and waits).  Errors:
+ * EMRKC_ERR_ARG for an unknown id, then those of the solver call. */
 int emrkc_batch_get_state(emrkc_batch* b, int id, int var, double* host_out, int64_t len);
 int emrkc_batch_set_state(emrkc_batch* b, int id, int var, const double* host_in, int64_t len);
 int emrkc_batch_get_activation_times(emrkc_batch* b, int id, double* host_out, int64_t n);
+/* Sizes, stage counts, time and device bytes of one instance (*out, host);
+ * EMRKC_ERR_ARG for a NULL out or an unknown id. */
 int emrkc_batch_get_info(emrkc_batch* b, int id, emrkc_batch_info* out);
+/* Totals and the launch configuration in use (*out, host); EMRKC_ERR_ARG
+ * for a NULL out. */
 int emrkc_batch_get_stats(emrkc_batch* b, emrkc_batch_stats* out);
-/* Launch configuration: tile in {256, 512, ..., 8192} nodes, block 128 or 256. */
+/* Launch configuration: tile in {256, 512, ..., 8192} nodes, block 128 or
+ * 256 (takes effect at the next step).  EMRKC_ERR_ARG for other values. */
 int emrkc_batch_set_config(emrkc_batch* b, int tile, int block);
 /* Order of the work list: 0 (default) an instance's whole phase at a time,
- * 1 / 2 at most 16 / 4 tiles of an instance before the next ready one. */
+ * 1 / 2 at most 16 / 4 tiles of an instance before the next ready one.
+ * Every order gives the same results.  EMRKC_ERR_ARG for other values. */
 int emrkc_batch_set_schedule(emrkc_batch* b, int schedule);
 /* Register budget of the persistent kernel, as resident threads per SM:
  * 1024, 1536 (default) or 2048 (64, 40 or 32 registers per thread).  More
- * threads hide more load latency; the heavier ionic models spill at the
- * smaller budgets.  EMRKC_ERR_ARG for other values. */
+ * resident threads hide more load latency; the two smaller budgets spill
+ * some registers to local memory.  Every budget gives the same results.
+ * Takes effect at the next step.  EMRKC_ERR_ARG for other values. */
 int emrkc_batch_set_occupancy(emrkc_batch* b, int threads_per_sm);
-/* Time each (tile, block, work-list order, register budget) candidate over `reps` steps of size dt without
- * advancing any instance (the candidates run with bookkeeping and
- * activation writes disabled) and keep the fastest.  Returns EMRKC_ERR_STATE
- * (configuration unchanged) if an instance has s >= 3, whose dry steps would
- * overwrite its current state buffer.  Outputs may be NULL. */
+/* Time each (tile, block, work-list order, register budget) candidate over
+ * `reps` steps of size dt without advancing any instance (the candidates
+ * run with bookkeeping and activation writes disabled) and keep the
+ * fastest.  Returns EMRKC_ERR_STATE (configuration unchanged) if an
+ * instance has s >= 3, whose dry steps would overwrite its current state
+ * buffer, and EMRKC_ERR_TIMEOUT if a dependency wait gave up.  Outputs
+ * (the chosen tile and block, the best time per step in ms) may be NULL. */
 int emrkc_batch_autotune(emrkc_batch* b, double dt, int reps, int* tile_out, int* block_out, double* ms_out);
 /* Diagnostics: polls of a dependency wait before the persistent kernel gives
  * up, records EMRKC_ERR_TIMEOUT (reported by emrkc_batch_sync) and returns;
